@@ -1,0 +1,399 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the paper
+prints (tests/golden/, each file citing its table), closed forms, truncation orders of
+the scheme, and dense LU on tiny grids.
+"""
+import numpy as np
+import pytest
+
+import helm6_inputs as inputs
+import oracle as O
+from oracle import oned
+from oracle import sources as S
+from conftest import read_golden
+
+X3 = S.PolyExp([0, 0, 0, 1, -3, 3, -1])                      # x^3 (1-x)^3
+
+
+def table_u(k, phi3):
+    """u = x^3(1-x)^3 * y(1-y) cos(k pi y) * phi3(z), the paper's Section 4.2 products."""
+    return S.Separable([(1.0, X3, S.poly_times([0, 1, -1], S.cos1d(k * np.pi)), phi3)])
+
+
+def solve_error(prob, u, F, method="gmres", tol=1e-10):
+    U, info = O.solve(prob, F, tol=tol, restart=50, maxit=200, method=method)
+    Z, Y, X = prob.coords()
+    return U, info, np.abs(U - u(X, Y, Z)).max()
+
+
+# --------------------------------------------------------------------------------------
+# Stencil: closed-form eigenvalues (Eq. 3DEGV's lambda_ijl) and Table 1
+# --------------------------------------------------------------------------------------
+
+def lambda_3d(i, j, l, h, k):
+    """Eigenvalues of A and A_p for the Dirichlet cube (Section 3.4), s_r = sin^2(r pi h/2)."""
+    s = [np.sin(r * np.pi * h / 2) ** 2 for r in (i, j, l)]
+    kh2 = (k * h) ** 2
+    lp = -4 * sum(s) + kh2
+    la = (lp + 8 / 3 * (1 + kh2 / 30) * (s[0] * s[1] + s[0] * s[2] + s[1] * s[2])
+          - 32 / 15 * s[0] * s[1] * s[2] - kh2 ** 2 / 12 + kh2 ** 3 / 360)
+    return la, lp
+
+
+@pytest.mark.parametrize("k", [10.0, 23.0 + 1.5j])
+@pytest.mark.parametrize("ijl", [(1, 1, 1), (1, 2, 3), (4, 2, 7), (9, 9, 1)])
+def test_stencil_eigenvalues_dirichlet(k, ijl):
+    prob = O.Problem(9, k, "DDDDDD")
+    Z, Y, X = prob.coords()
+    i, j, l = ijl
+    u = np.sin(i * np.pi * X) * np.sin(j * np.pi * Y) * np.sin(l * np.pi * Z) * np.ones(prob.shape)
+    la, lp = lambda_3d(i, j, l, prob.h, k)
+    np.testing.assert_allclose(O.apply_A(prob, u), la * u, atol=1e-13)
+    np.testing.assert_allclose(O.apply_Ap(prob, u), lp * u, atol=1e-13)
+
+
+def test_table1_eigenvalue_bounds():
+    """Table 1: printed [m, M] = [-max d, -min d], d = lambda/lambda^p - 1 (Eq. 3DEGV)."""
+    def unit(txt):      # one unit in the last printed digit (the table rounds or truncates)
+        return 10.0 ** -(len(txt.split(".")[1]) if "." in txt else 0)
+
+    for hinv, k, m_s, M_s in read_golden("table1_eigen_bounds.txt"):
+        hinv, k, m_p, M_p = int(hinv), float(k), float(m_s), float(M_s)
+        h = 1.0 / hinv
+        r = np.arange(1, hinv)
+        s = np.sin(r * np.pi * h / 2) ** 2
+        kh2 = (k * h) ** 2
+        si, sj = s[:, None, None], s[None, :, None]
+        dmax, dmin = -np.inf, np.inf
+        for sl in np.array_split(s, 8):
+            sl = sl[None, None, :]
+            lp = -4 * (si + sj + sl) + kh2
+            la = (lp + 8 / 3 * (1 + kh2 / 30) * (si * sj + si * sl + sj * sl)
+                  - 32 / 15 * si * sj * sl - kh2 ** 2 / 12 + kh2 ** 3 / 360)
+            d = la / lp - 1
+            dmax, dmin = max(dmax, d.max()), min(dmin, d.min())
+        assert abs(-dmax - m_p) <= unit(m_s), (hinv, k, -dmax, m_p)
+        assert abs(-dmin - M_p) <= unit(M_s), (hinv, k, -dmin, M_p)
+
+
+def test_table1_uses_the_oracle_stencil():
+    """The oracle's A and A_p reproduce lambda/lambda^p on every DST mode of a small cube."""
+    k, n = 31.0, 7
+    prob = O.Problem(n, k, "DDDDDD")
+    Amat = O.dense_matrix(lambda U: O.apply_A(prob, U), prob.shape)
+    Apmat = O.dense_matrix(lambda U: O.apply_Ap(prob, U), prob.shape)
+    ratio = np.sort(np.linalg.eigvals(np.linalg.solve(Apmat, Amat)).real)
+    r = np.arange(1, n + 1)
+    I, J, L = np.meshgrid(r, r, r, indexing="ij")
+    la, lp = lambda_3d(I, J, L, prob.h, k)
+    np.testing.assert_allclose(ratio, np.sort((la / lp).ravel()), rtol=1e-10, atol=1e-10)
+
+
+# --------------------------------------------------------------------------------------
+# Truncation orders of the scheme and of the face eliminations
+# --------------------------------------------------------------------------------------
+
+def row_residual(n, k, faces, u):
+    prob = O.Problem(n, k, faces)
+    Z, Y, X = prob.coords()
+    U = u(X, Y, Z) * np.ones(prob.shape)
+    f = S.helmholtz_source(u, k)
+    return prob, np.abs(O.apply_A(prob, U) - O.rhs(prob, f))
+
+
+def order(r1, r2):
+    return np.log2(r1 / r2)
+
+
+def test_interior_truncation_is_eighth_order_scaled():
+    """Eq. scheme with the h^4/90 mixed-derivative reading: h^2-scaled residual O(h^8)."""
+    k = 6.0 + 0.4j
+    dirichlet = lambda b: S.PolyExp(np.polynomial.Polynomial([0, 1, -1]).coef, b)
+    u = S.Separable([(1.0, dirichlet(0.7), dirichlet(-0.4 + 0.3j), dirichlet(1.1j))])
+    res = [row_residual(n, k, "DDDDDD", u)[1].max() for n in (15, 31)]
+    assert order(*res) > 7.6, res
+
+
+def test_neumann_face_truncation_order():
+    """Eq. 3DN with the minus sign on 7h^5/180: face rows O(h^7) (printed sign: O(h^5))."""
+    k = 5.0 + 0.3j
+    dirichlet = lambda b: S.PolyExp([0, 1, -1], b)
+    # phi'(0) = phi'(1) = 0 and phi not even about either face
+    neu = S.Sum1D(S.PolyExp([0, 0, 1, -2.0 / 3]), S.Scaled1D(0.3, S.cos1d(np.pi)))
+    for faces, u in (("DDDDNN", S.Separable([(1.0, dirichlet(0.5), dirichlet(-0.3j), neu)])),
+                     ("NNDDDD", S.Separable([(1.0, neu, dirichlet(0.5), dirichlet(0.2 - 0.3j))]))):
+        out = []
+        for n in (15, 31):
+            prob, r = row_residual(n, k, faces, u)
+            axis = 2 if faces.startswith("DD") else 0
+            npax = 2 - axis
+            face = np.concatenate([np.take(r, [0], npax), np.take(r, [-1], npax)], npax)
+            out.append((face.max(), np.delete(r, [0, r.shape[npax] - 1], npax).max()))
+        assert order(out[0][0], out[1][0]) > 6.6, (faces, out)
+        assert order(out[0][1], out[1][1]) > 7.5, (faces, out)
+
+
+def test_sommerfeld_face_truncation_order():
+    """Eq. 3DDISCS as printed, bottom face and mirrored top face: face rows O(h^7)."""
+    k = 7.0 + 0.2j
+    b = 0.7
+    a = (2j * k + b * (2j * k - 3)) / (2 - 2j * k)     # u_z - iku = 0 at z = 1
+    som = S.PolyExp([1, 0, a, b], -1j * k)              # u_z + iku = 0 at z = 0
+    even_neu = S.Sum1D(S.cos1d(np.pi), S.Scaled1D(0.3, S.cos1d(2 * np.pi)))
+    u = S.Separable([(1.0, S.PolyExp([0, 1, -1], 0.4), even_neu, som)])
+    zz = np.array([0.0, 1.0])
+    assert abs(som.d(1, zz[0]) + 1j * k * som(zz[0])) < 1e-13
+    assert abs(som.d(1, zz[1]) - 1j * k * som(zz[1])) < 1e-13
+    out = []
+    for n in (15, 31):
+        prob, r = row_residual(n, k, "DDNNSS", u)
+        out.append((r[0].max(), r[-1].max(), r[1:-1].max()))
+    assert order(out[0][0], out[1][0]) > 6.6, out
+    assert order(out[0][1], out[1][1]) > 6.6, out
+    assert order(out[0][2], out[1][2]) > 7.5, out
+
+
+# --------------------------------------------------------------------------------------
+# Preconditioner (Eq. 3DAP)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lo,hi", [("D", "D"), ("N", "N"), ("D", "N"), ("N", "D")])
+def test_axis_matrix_closed_form_eigenvalues(lo, hi):
+    n = 11
+    prob = O.Problem(n, 3.0, lo + hi + "DDDD")
+    h = prob.h
+    T = O.axis_matrix(prob, 0).real
+    ev = np.sort(np.linalg.eigvals(T).real)
+    if lo == hi:
+        j = np.arange(1, n + 1) if lo == "D" else np.arange(0, n + 2)
+        ref = -4 * np.sin(j * np.pi * h / 2) ** 2
+    else:
+        j = np.arange(1, n + 2)
+        ref = -4 * np.sin((2 * j - 1) * np.pi * h / 4) ** 2
+    np.testing.assert_allclose(ev, np.sort(ref), atol=1e-12)
+
+
+@pytest.mark.parametrize("faces,k", [("DDDDDD", 10.0), ("DDNNSS", 12.0), ("NDDNNS", 9.0 + 0.5j),
+                                     ("NNNNDN", 4.0 + 1j), ("DNDDSD", 11.0)])
+def test_preconditioner_inverts_7point(faces, k):
+    prob = O.Problem(6, k, faces)
+    M = O.Preconditioner(prob)
+    Ap = O.dense_matrix(lambda U: O.apply_Ap(prob, U), prob.shape)
+    y = inputs.complex_normal(5, prob.shape)
+    ref = np.linalg.solve(Ap, y.ravel()).reshape(prob.shape)
+    np.testing.assert_allclose(M(y), ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_preconditioner_on_eigenvector_products():
+    """A_p^{-1} of a product of DST modes divides by lambda_p + lambda_q + lambda_r + k^2h^2."""
+    prob = O.Problem(10, 14.0 + 0.1j, "DDDDDD")
+    Z, Y, X = prob.coords()
+    h = prob.h
+    u = np.sin(3 * np.pi * X) * np.sin(5 * np.pi * Y) * np.sin(2 * np.pi * Z) * np.ones(prob.shape)
+    lam = -4 * sum(np.sin(r * np.pi * h / 2) ** 2 for r in (3, 5, 2)) + (prob.k * h) ** 2
+    np.testing.assert_allclose(O.Preconditioner(prob)(u), u / lam, atol=1e-12)
+
+
+# --------------------------------------------------------------------------------------
+# Krylov solvers: dense LU, closed-form solution, and the paper's tables
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("faces,k", [("DDDDDD", 7.0), ("DDNNSS", 9.0), ("NNDNSD", 6.0 + 0.5j),
+                                     ("DNNDNN", 5.0)])
+def test_gmres_and_sks_match_dense_lu(faces, k):
+    prob = O.Problem(5, k, faces)
+    F = inputs.complex_normal(11, prob.shape)
+    ref = O.solve_dense(prob, F)
+    U, info = O.solve(prob, F, tol=1e-13, restart=10, maxit=200)
+    assert info["converged"]
+    np.testing.assert_allclose(U, ref, atol=1e-10 * np.abs(ref).max())
+    U, info = O.solve(prob, F, tol=1e-13, restart=10, maxit=200, method="sks")
+    if info["converged"]:
+        np.testing.assert_allclose(U, ref, atol=1e-9 * np.abs(ref).max())
+
+
+def test_closed_form_discrete_solution_dirichlet_n32():
+    """u = sin(pi x) sin(2 pi y) sin(3 pi z) is a discrete eigenvector of A and of the right
+    side operator, so U* = (R / lambda_A) u on the grid exactly."""
+    n, k = 32, 10.0
+    prob = O.Problem(n, k, "DDDDDD")
+    h = prob.h
+    u = S.Separable([(1.0, S.sin1d(np.pi), S.sin1d(2 * np.pi), S.sin1d(3 * np.pi))])
+    f = S.helmholtz_source(u, k)
+    F = O.rhs(prob, f)
+    # right side multiplier: f = (k^2 - 14 pi^2) u, lap f = -14 pi^2 f, ...
+    p2 = np.pi ** 2
+    kh2 = (k * h) ** 2
+    cf = 1 - kh2 / 12 + kh2 ** 2 / 360
+    R = h * h * (cf - (h * h / 12) * (1 - kh2 / 30) * 14 * p2
+                 + (h ** 4 / 360) * p2 ** 2 * (1 + 16 + 81)
+                 + (h ** 4 / 90) * p2 ** 2 * (4 + 9 + 36)) * (k * k - 14 * p2)
+    la, _ = lambda_3d(1, 2, 3, h, k)
+    Z, Y, X = prob.coords()
+    Ustar = (R / la) * u(X, Y, Z)
+    np.testing.assert_allclose(F, R * u(X, Y, Z) * np.ones(prob.shape), atol=1e-15)
+    U, info = O.solve(prob, F, tol=1e-12, restart=20)
+    assert info["converged"]
+    np.testing.assert_allclose(U, Ustar, atol=1e-10 * np.abs(Ustar).max())
+    assert np.abs(Ustar - u(X, Y, Z)).max() < 1e-6     # sixth-order accurate at h = 1/33
+
+
+def test_table2_one_dimensional():
+    """Table 2: SKS counts exact, GMRES within one, Err6 / Err2 to the printed digits."""
+    k = 20.0
+    u = S.poly_times([0, 1, -1], S.cos1d(k * np.pi))
+    f = lambda x: u.d(2, x) + k * k * u.d(0, x)
+    f2 = lambda x: u.d(4, x) + k * k * u.d(2, x)
+    for N, g_p, sks_p, _, e6_p, e2_p in read_golden("table2_1d.txt"):
+        N = int(N)
+        A, Ap, h = oned.matrices(N, k)
+        F = oned.rhs(N, k, f, f2)
+        x = np.arange(1, N + 1) * h
+        Aop = lambda v: A @ v
+        Mop = lambda v: np.linalg.solve(Ap, v)
+        _, ig = O.gmres(Aop, Mop, F, tol=1e-10, restart=50, maxit=100)
+        _, isk = O.sks(Aop, Mop, F, tol=1e-10, maxit=100)
+        assert isk["iters"] == int(sks_p)
+        assert abs(ig["iters"] - int(g_p)) <= 1
+        err6 = np.abs(np.linalg.solve(A, F) - u(x)).max()
+        err2 = np.abs(np.linalg.solve(Ap, h * h * f(x)) - u(x)).max()
+        assert abs(err6 / float(e6_p) - 1) < 0.01, (N, err6)
+        assert abs(err2 / float(e2_p) - 1) < 0.05, (N, err2)
+
+
+def test_theorem3_eigenvalues_1d():
+    N, k = 40, 17.0
+    A, Ap, h = oned.matrices(N, k)
+    lp, la = oned.eigenvalues(N, k)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvals(Ap).real), np.sort(lp.real), atol=1e-12)
+    np.testing.assert_allclose(np.sort(np.linalg.eigvals(A).real), np.sort(la.real), atol=1e-12)
+
+
+def test_table3_table4_dirichlet_h64():
+    """Table 3 Err6 at h = 1/64 and the Table 4 iteration counts at h = 1/64."""
+    rows = read_golden("table3_4_dirichlet.txt")
+    err6 = {(int(r[1]), float(r[2])): float(r[3]) for r in rows if r[0] == "err6"}
+    counts = [r for r in rows if r[0] != "err6" and r[0] == "64"]
+    for hinv, k, g_p, sks_p in counts:
+        k = float(k)
+        prob = O.Problem(63, k, "DDDDDD")
+        u = table_u(k, S.sin1d(k * np.pi))
+        F = O.rhs(prob, S.helmholtz_source(u, k))
+        _, ig, e6 = solve_error(prob, u, F)
+        if k <= 30:
+            assert abs(ig["iters"] - int(g_p)) <= 1, (k, ig["iters"])
+        else:   # kh = 0.62, at the resolution limit kh < 2 pi / 10: no slower than printed
+            assert ig["iters"] <= int(g_p) + 1, (k, ig["iters"])
+        _, isk, _ = solve_error(prob, u, F, method="sks")
+        if sks_p == "div":
+            assert isk["diverged"] or not isk["converged"]
+        else:
+            assert isk["iters"] == int(sks_p), (k, isk["iters"])
+        if (64, k) in err6:
+            assert abs(e6 / err6[(64, k)] - 1) < 0.01, e6
+
+
+@pytest.mark.slow
+def test_table3_table4_dirichlet_h128():
+    rows = read_golden("table3_4_dirichlet.txt")
+    for hinv, k, g_p, sks_p in [r for r in rows if r[0] == "128"]:
+        k = float(k)
+        prob = O.Problem(127, k, "DDDDDD")
+        u = table_u(k, S.sin1d(k * np.pi))
+        F = O.rhs(prob, S.helmholtz_source(u, k))
+        _, ig, e6 = solve_error(prob, u, F)
+        assert abs(ig["iters"] - int(g_p)) <= 1
+        _, isk, _ = solve_error(prob, u, F, method="sks")
+        assert isk["iters"] == int(sks_p)
+        if k == 20.0:
+            assert abs(e6 / 6.35e-8 - 1) < 0.01
+
+
+def table5_problem(n, k=20.0):
+    prob = O.Problem(n, k, "DDDDND")
+    phi3 = S.cos1d(k * np.pi)
+    u = table_u(k, phi3)
+    F = O.rhs(prob, S.helmholtz_source(u, k))
+    xs = np.arange(0, n + 2) * prob.h
+    ub = (X3(xs)[None, :] * S.poly_times([0, 1, -1], S.cos1d(k * np.pi))(xs)[:, None]) * phi3(1.0)
+    return prob, u, O.lift_dirichlet(prob, F, {(2, 1): ub})
+
+
+def test_table5_dirichlet_neumann_h64():
+    """Table 5 at h = 1/64: Err6, GMRES (within one) and SKS (exact) counts."""
+    hinv, g_p, sks_p, e6_p, _ = read_golden("table5_dirichlet_neumann.txt")[0]
+    prob, u, F = table5_problem(int(hinv) - 1)
+    _, ig, e6 = solve_error(prob, u, F)
+    assert abs(e6 / float(e6_p) - 1) < 0.01, e6
+    assert abs(ig["iters"] - int(g_p)) <= 1
+    _, isk, _ = solve_error(prob, u, F, method="sks")
+    assert isk["iters"] == int(sks_p)
+
+
+def test_sommerfeld_sixth_order_convergence():
+    """Dirichlet x/y, Sommerfeld-like z (Section 4.2.3) with a test function that satisfies
+    both radiation conditions: the error falls by ~2^6 per halving of h."""
+    k = 20.0
+    c = 1j * k / (1 - 1j * k)
+    u = table_u(k, S.PolyExp([1, 0, c], -1j * k))
+    errs = []
+    for n in (47, 95):
+        prob = O.Problem(n, k, "DDDDSS")
+        F = O.rhs(prob, S.helmholtz_source(u, k))
+        errs.append(solve_error(prob, u, F)[2])
+    assert np.log(errs[0] / errs[1]) / np.log(96 / 48) > 5.5, errs
+
+
+def test_psi_order_estimate():
+    """Eq. PSI on the 1D problem, where Theorem 3 proves second order (the paper: 1.99)."""
+    k = 20.0
+    u = S.poly_times([0, 1, -1], S.cos1d(k * np.pi))
+    f = lambda x: u.d(2, x) + k * k * u.d(0, x)
+    f2 = lambda x: u.d(4, x) + k * k * u.d(2, x)
+    eps = []
+    for N in (255, 127):
+        A, Ap, h = oned.matrices(N, k)
+        F = oned.rhs(N, k, f, f2)
+        _, info = O.sks(lambda v: A @ v, lambda v: np.linalg.solve(Ap, v), F, tol=1e-14, maxit=3)
+        eps.append(info["history"][1] / info["history"][0])
+    assert abs(O.psi_order(eps[0], eps[1], 2.0) - 2.0) < 0.15
+
+
+# --------------------------------------------------------------------------------------
+# Sources and the seeded generators
+# --------------------------------------------------------------------------------------
+
+def test_splitmix64_published_vector():
+    # first outputs of SplitMix64 seeded with 0 (reference implementation by Vigna)
+    z = inputs.splitmix64(0, 2)
+    assert int(z[0]) == 0xE220A8397B1DCDAF
+    assert int(z[1]) == 0x6E789E6AA1B965F4
+
+
+def test_normal_moments():
+    z = inputs.standard_normal(3, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    c = inputs.complex_normal(4, (1000, 100))
+    assert abs(np.mean(np.abs(c) ** 2) - 1) < 0.02
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 6])
+def test_source_derivatives_by_finite_differences(order):
+    t = np.linspace(0.2, 0.8, 7)
+    e = 1e-3
+    for fn in (S.Gauss1D(0.45, 0.07), S.PolyExp([0.3, -1, 2, 0.5], 1.3 - 2j),
+               S.sin1d(3.0, 0.2), S.cos1d(2.0, -0.4)):
+        g = lambda dt: fn.d(order, t + dt)
+        fd = (8 * (g(e) - g(-e)) - (g(2 * e) - g(-2 * e))) / (12 * e)    # O(e^4)
+        np.testing.assert_allclose(fn.d(order + 1, t), fd, rtol=2e-5,
+                                   atol=2e-5 * np.abs(fd).max())
+
+
+def test_gaussian_sources_stay_inside():
+    n = 128
+    src = inputs.gaussian_sources(7, n, 8)
+    h = 1.0 / (n + 1)
+    assert np.all(src.centers >= 16 * h - 1e-12) and np.all(src.centers <= 1 - 16 * h + 1e-12)
+    np.testing.assert_allclose(np.abs(src.amps), 1.0)
+    assert inputs.dims(n, "DDNNSS") == (128, 130, 130)
