@@ -1,0 +1,152 @@
+/*
+ * helm6 -- sixth-order compact 3D Helmholtz solver on one GB300 (sm_103a).
+ *
+ * Solves  laplacian(u) + k^2 u = f  on the cube [0, a]^3, h = a/(n+1), with complex k and
+ * per-face Dirichlet (u = 0), Neumann (u_n = 0) or Sommerfeld-like (u_n - i k u = 0)
+ * conditions (Gryazin, "Preconditioned Krylov subspace methods for sixth order compact
+ * approximations of the Helmholtz equation", Eq. problem and Eq. bc).  The discrete system
+ * is the 27-point sixth-order compact scheme (Eq. scheme) with the paper's explicit
+ * sixth-order Neumann (Eq. 3DN) and Sommerfeld-like (Eq. 3DDISCS) face eliminations; it is
+ * solved by right-preconditioned restarted GMRES (Eq. AAP) or the SKS iteration
+ * (Algorithm 1), preconditioned by the second-order 7-point operator (Eq. 3DAP) inverted
+ * directly: eigen-transforms in x and y, complex tridiagonal solves in z.
+ *
+ * Grid and unknowns.  Nodes are x_i = i h, i = 0..n+1.  A Dirichlet face's nodes are known
+ * (zero) and carry no unknown; a Neumann or Sommerfeld-like face's nodes are unknowns, so
+ * an axis has n + (number of its non-Dirichlet faces) unknowns (Section 3.3, N_z chosen so
+ * that h is equal in all directions).  Sommerfeld-like faces are accepted on z only (the
+ * preconditioner of Section 3.3 diagonalises x and y).
+ *
+ * Data at the boundary.  Every vector argument is a DEVICE pointer to complex128
+ * (interleaved re, im doubles), x fastest: element (i, j, l) at index (l*my + j)*mx + i
+ * with (mx, my, mz) from helm6_dims.  The caller owns these buffers; the library never
+ * frees or retains them.  The library owns its workspace (allocated in helm6_create,
+ * released in helm6_destroy).  All work is ordered on the stream given in the options
+ * (NULL: the legacy default stream); calls return after the work has been enqueued, except
+ * helm6_solve, which reads convergence scalars back and returns when the solve is done.
+ *
+ * Errors.  Functions return HELM6_OK (0) on success, a negative HELM6_ERR_* code on
+ * failure (nothing was written), or for helm6_solve a positive warning (u then holds the
+ * last iterate and the stats are filled in).  helm6_status_string names every code.
+ * A context is not thread-safe: one host thread at a time.
+ */
+#ifndef HELM6_H
+#define HELM6_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm6_ctx helm6_ctx;  /* opaque, library-owned */
+
+typedef enum { HELM6_DIRICHLET = 0, HELM6_NEUMANN = 1, HELM6_SOMMERFELD = 2 } helm6_bc;
+
+typedef struct { double re, im; } helm6_c64;
+
+/* precision */
+enum { HELM6_FP64 = 0,   /* everything in FP64 complex */
+       HELM6_MIXED = 1   /* FP32 complex Krylov bulk, BF16-split tensor-core x/y transforms
+                            accumulated in FP32, inside FP64 iterative refinement whose true
+                            residual F - A U and Givens least squares stay FP64 */ };
+
+/* method */
+enum { HELM6_GMRES = 0,  /* right-preconditioned GMRES(m): U += A_p^{-1}(V y) per cycle */
+       HELM6_FGMRES = 1, /* flexible GMRES(m): keeps Z_j = A_p^{-1} v_j, U += Z y */
+       HELM6_SKS = 2     /* Algorithm 1 (no inner products except the residual norm) */ };
+
+/* return codes */
+enum {
+  HELM6_OK = 0,
+  HELM6_NOT_CONVERGED = 1,  /* maxit reached above tol */
+  HELM6_DIVERGED = 2,       /* residual grew by more than 1e3 (SKS; Table 4 "div") */
+  HELM6_BREAKDOWN = 3,      /* zero pivot in a z-line solve or a GMRES breakdown */
+  HELM6_NONFINITE = 4,      /* NaN/Inf in F or in the iteration */
+  HELM6_ERR_INVALID = -1,   /* bad argument (sizes, faces, pointers, options) */
+  HELM6_ERR_NOMEM = -2,     /* device allocation failed */
+  HELM6_ERR_CUDA = -3,      /* a CUDA call failed; the context should be destroyed */
+  HELM6_ERR_UNSUPPORTED = -4
+};
+
+typedef struct {
+  int precision;     /* HELM6_FP64 (default) or HELM6_MIXED */
+  int method;        /* HELM6_GMRES (default), HELM6_FGMRES or HELM6_SKS */
+  int xform_terms;   /* MIXED only: BF16 split terms of the x/y transforms (1, 2 or 3;
+                        0 = default 3: hi*hi + hi*lo + lo*hi) */
+  int max_restart;   /* largest restart length helm6_solve will be asked for (0 = 30);
+                        sizes the Krylov workspace */
+  double inner_tol;  /* MIXED only: relative reduction asked of each FP32 inner solve
+                        (0 = default 1e-5) */
+  void* stream;      /* cudaStream_t; NULL = default stream */
+} helm6_opts;
+
+#define HELM6_MAX_HIST 1024
+
+typedef struct {
+  int iters;          /* Krylov (or SKS) iterations, summed over restarts and refinements */
+  int outer;          /* GMRES cycles (FP64) or FP64 refinement steps (MIXED) */
+  int status;         /* same value helm6_solve returns */
+  double relres;      /* final true relative residual ||F - A U||_2 / ||F||_2, FP64 */
+  double t_total_ms;  /* wall time of helm6_solve */
+  int nhist;          /* entries in hist */
+  double hist[HELM6_MAX_HIST];  /* relative residual after each iteration (estimates for
+                                   GMRES, true residuals for SKS and refinement steps) */
+} helm6_stats;
+
+/* Fill opts with the defaults listed above. */
+void helm6_opts_default(helm6_opts* opts);
+
+/* Create a solver for n interior nodes per side (1 <= n <= 4094), grid step h (h <= 0 means
+ * the unit cube, h = 1/(n+1)), wavenumber k and faces[6] = {x0, x1, y0, y1, z0, z1} of
+ * helm6_bc.  Builds the 1D eigenbases (closed forms, FP64 host arithmetic), uploads them
+ * and allocates the workspace.  opts may be NULL (defaults).  *out is set only on success.
+ * Errors: INVALID (n out of range, Sommerfeld-like face on x or y, bad option values),
+ * NOMEM, CUDA. */
+int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[6],
+                 const helm6_opts* opts);
+
+/* Unknowns per axis: dims = {mx, my, mz}. */
+int helm6_dims(const helm6_ctx* ctx, int64_t dims[3]);
+
+/* y = A x, the h^2-scaled sixth-order compact operator (Eq. scheme; face rows per Eq. 3DN
+ * with the ghost eliminated by even reflection, and Eq. 3DDISCS).  x and y are device
+ * complex128 arrays of mx*my*mz elements and must not overlap.  In MIXED precision the
+ * product is computed by the FP32 kernel (inputs rounded to FP32, result widened). */
+int helm6_apply_A(helm6_ctx* ctx, const void* x, void* y);
+
+/* y = A_p^{-1} x, the direct inverse of the 7-point preconditioner (Eq. 3DAP): forward x
+ * and y eigen-transforms, a tridiagonal solve along z for every (x, y) mode pair, inverse
+ * transforms.  FP64: FP64 transforms and Thomas; MIXED: BF16-split tensor-core
+ * transforms and FP32 Thomas.  x and y may alias.  Returns BREAKDOWN if a z-line pivot is
+ * exactly zero (y is then undefined). */
+int helm6_apply_Pinv(helm6_ctx* ctx, const void* x, void* y);
+
+/* Solve A u = F to ||F - A u||_2 / ||F||_2 <= tol (true residual, FP64), starting from
+ * the u passed in (in/out).  restart = m of GMRES(m) (1 <= m <= opts.max_restart; ignored
+ * by SKS), maxit = cap on iterations (summed).  stats may be NULL.  Returns OK or a
+ * positive warning; u holds the final iterate either way.  F must be finite (NONFINITE
+ * otherwise, u untouched).  F = 0 returns u = 0. */
+int helm6_solve(helm6_ctx* ctx, const void* F, void* u, double tol, int restart, int maxit,
+                helm6_stats* stats);
+
+/* Assemble the compact right side F (Eq. scheme right side, h^2-scaled, with the face data
+ * terms of Eq. 3DN and Eq. 3DDISCS) for f = sum_s amps[s] exp(-|x - c_s|^2 / (2 sigma^2))
+ * plus an optional noise field eta (no derivatives; enters as h^2 cf eta with
+ * cf = 1 - k^2h^2/12 + k^4h^4/360).  centers: HOST array of nsrc*3 doubles (x, y, z);
+ * amps: HOST array of nsrc helm6_c64; noise: DEVICE complex128 array of the grid's size
+ * or NULL; F: DEVICE complex128 output.  0 <= nsrc <= 4096, sigma > 0. */
+int helm6_rhs_gaussians(helm6_ctx* ctx, int nsrc, const double* centers,
+                        const helm6_c64* amps, double sigma, const void* noise, void* F);
+
+/* Release the workspace and the context (NULL is allowed).  Synchronises its stream. */
+void helm6_destroy(helm6_ctx* ctx);
+
+/* Static string naming a return code. */
+const char* helm6_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM6_H */

@@ -1,0 +1,624 @@
+// C-ABI entry points of the helm6 library and the host-side drivers of the solvers.
+//
+// The Krylov loops run on the host thread but keep every vector, the Hessenberg matrix
+// and the Givens rotations on the device; one FP64 scalar (the residual estimate) is read
+// back per iteration to decide convergence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "helm6_internal.h"
+
+using namespace helm6;
+
+struct helm6_ctx {
+  Geom g;
+  int n = 0;
+  double h = 0;
+  cd k;
+  helm6_opts opts;
+  cudaStream_t stream = nullptr;
+  StencilCoef coef;
+  c64d diag0, alpha;  // z-line diagonal -2 + k^2h^2 and Sommerfeld-like end term 2ikh
+  int mrest = 30;
+  int nred = 0;        // blocks of the reduction kernels
+  int nsten = 0;       // blocks of the stencil kernel (partials of its fused norm)
+  double last_beta = 0;  // ||F - A U|| after the last FP64 residual
+  // preconditioner tables (device): V, W = V^{-1} row-major m x m, eigenvalues
+  double *Vx64 = nullptr, *Wx64 = nullptr, *Vy64 = nullptr, *Wy64 = nullptr;
+  float *Vx32 = nullptr, *Wx32 = nullptr, *Vy32 = nullptr, *Wy32 = nullptr;
+  double *lamx = nullptr, *lamy = nullptr;
+  // FP64 vectors (2N doubles each)
+  double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
+  double *V64 = nullptr, *Z64 = nullptr, *w64 = nullptr, *zt64 = nullptr, *tA64 = nullptr,
+         *tB64 = nullptr, *cw64 = nullptr;
+  // FP32 vectors (MIXED)
+  float *V32 = nullptr, *Z32 = nullptr, *w32 = nullptr, *zt32 = nullptr, *tA32 = nullptr,
+        *tB32 = nullptr, *cw32 = nullptr;
+  // small device arrays
+  double *partial = nullptr, *spart = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr,
+         *gv = nullptr, *yv = nullptr, *h2 = nullptr, *scal = nullptr;
+  int* status = nullptr;
+  double* pinned = nullptr;  // host-pinned readback slots
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+constexpr int kDiverge = 1000;  // SKS: relative residual growth that counts as divergence
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) {                          \
+      fprintf(stderr, "helm6: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+      return HELM6_ERR_CUDA;                          \
+    }                                                 \
+  } while (0)
+
+template <typename T>
+int dalloc(helm6_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&q, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return HELM6_ERR_NOMEM;
+  }
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return HELM6_OK;
+}
+
+// ---- 1D eigenbases of the x and y second-difference matrices (closed forms) ----
+// D-D: nodes 1..n, modes j=1..n, V[l][j] = sin(j l t), t = pi/(n+1), lam = -4 sin^2(j t/2)
+// N-N: nodes 0..n+1, modes j=0..n+1, V[l][j] = cos(j l t), V^{-1}[j][l] = (2/(n+1)) w_j w_l cos(j l t)
+//      with end weights w = 1/2 at 0 and n+1
+// D-N: nodes 1..n+1, th_j = (2j-1) t/2, V[l][j] = sin(l th_j), V^{-1}[j][l] = (2/(n+1)) w_l sin(l th_j),
+//      w_{n+1} = 1/2, lam = -4 sin^2(th_j/2);  N-D: nodes 0..n, cos(l th_j), w_0 = 1/2.
+void basis(int n, int lo, int hi, std::vector<double>& V, std::vector<double>& W, std::vector<double>& lam) {
+  const double t = M_PI / (n + 1);
+  const bool nlo = lo != HELM6_DIRICHLET, nhi = hi != HELM6_DIRICHLET;
+  const int m = n + (nlo ? 1 : 0) + (nhi ? 1 : 0);
+  V.assign((size_t)m * m, 0.0);
+  W.assign((size_t)m * m, 0.0);
+  lam.assign(m, 0.0);
+  const double sc = 2.0 / (n + 1);
+  for (int jj = 0; jj < m; ++jj) {
+    for (int p = 0; p < m; ++p) {
+      double v, wv;
+      if (!nlo && !nhi) {
+        const int j = jj + 1, l = p + 1;
+        v = std::sin(j * l * t);
+        wv = sc * v;
+        lam[jj] = -4.0 * std::pow(std::sin(j * t / 2), 2);
+      } else if (nlo && nhi) {
+        const int j = jj, l = p;
+        const double wj = (j == 0 || j == n + 1) ? 0.5 : 1.0, wl = (l == 0 || l == n + 1) ? 0.5 : 1.0;
+        v = std::cos((double)j * l * t);
+        wv = sc * wj * wl * v;
+        lam[jj] = -4.0 * std::pow(std::sin(j * t / 2), 2);
+      } else if (!nlo && nhi) {
+        const int j = jj + 1, l = p + 1;
+        const double th = (2 * j - 1) * t / 2, wl = (l == n + 1) ? 0.5 : 1.0;
+        v = std::sin(l * th);
+        wv = sc * wl * v;
+        lam[jj] = -4.0 * std::pow(std::sin(th / 2), 2);
+      } else {
+        const int j = jj + 1, l = p;
+        const double th = (2 * j - 1) * t / 2, wl = (l == 0) ? 0.5 : 1.0;
+        v = std::cos(l * th);
+        wv = sc * wl * v;
+        lam[jj] = -4.0 * std::pow(std::sin(th / 2), 2);
+      }
+      V[(size_t)p * m + jj] = v;   // row = node p, column = mode jj
+      W[(size_t)jj * m + p] = wv;  // row = mode jj, column = node p
+    }
+  }
+}
+
+// ---- 27-point weights (Eq. scheme, Eq. 3DDISCS) ----
+void stencil_coefficients(cd k, double h, StencilCoef& c) {
+  const cd kh2 = k * k * h * h;
+  const cd a = (1.0 + kh2 / 30.0) / 6.0;
+  const double b = 1.0 / 30.0;
+  const cd kappa = kh2 * (1.0 - kh2 / 12.0 + kh2 * kh2 / 360.0);
+  // class weights of D_x+D_y+D_z + a(sum D D) + b DDD + kappa on the 27 points
+  const cd c0 = -6.0 + 12.0 * a - 8.0 * b + kappa;
+  const cd c1 = 1.0 - 4.0 * a + 4.0 * b;
+  const cd c2 = a - 2.0 * b;
+  const cd c3 = b;
+  RowWeights in{};
+  in.w[1][0] = to_pod(c0);
+  in.w[1][1] = to_pod(c1);
+  in.w[1][2] = to_pod(c2);
+  for (int dz : {0, 2}) {
+    in.w[dz][0] = to_pod(c1);
+    in.w[dz][1] = to_pod(c2);
+    in.w[dz][2] = to_pod(c3);
+  }
+  c.interior = in;
+  // Sommerfeld-like face: B U_{-1} -> G1 U_1 + G0 U_0,
+  // G1 = e2 mu3 [p (Dx+Dy) + DxDy/(30 mu3) + q I], G0 = e1 mu3 [r I - s (Dx+Dy)]
+  const cd I(0.0, 1.0), ik = I * k;
+  const cd mu3 = 1.0 / (1.0 + (2.0 * ik * h / 3.0) * (1.0 + 2.0 * kh2 / 15.0));
+  const cd mu1 = (ik * h / 90.0 + (1.0 + kh2 / 30.0) / (6.0 * mu3)) / (1.0 + 2.0 * ik * h / 3.0);
+  const cd e1 = std::exp(ik * h), e2 = std::exp(2.0 * ik * h);
+  const cd p = mu1 + (2.0 * ik * h / 3.0) * (1.0 / 60.0 - mu1);
+  const cd q = 1.0 - 2.0 * ik * h / 3.0 - 4.0 * ik * kh2 * h / 45.0;
+  const cd r = (4.0 * ik * h / 3.0) * (1.0 + 2.0 * kh2 / 15.0);
+  const cd s = (4.0 * ik * h / 3.0) * (1.0 / 60.0 - mu1);
+  const cd g1c = e2 * mu3 * (-4.0 * p + 4.0 / (30.0 * mu3) + q);
+  const cd g1n = e2 * mu3 * (p - 2.0 / (30.0 * mu3));
+  const cd g1d = e2 * mu3 / (30.0 * mu3);
+  const cd g0c = e1 * mu3 * (r + 4.0 * s);
+  const cd g0n = -e1 * mu3 * s;
+  RowWeights lo{};
+  lo.w[1][0] = to_pod(c0 + g0c);
+  lo.w[1][1] = to_pod(c1 + g0n);
+  lo.w[1][2] = to_pod(c2);
+  lo.w[2][0] = to_pod(c1 + g1c);
+  lo.w[2][1] = to_pod(c2 + g1n);
+  lo.w[2][2] = to_pod(c3 + g1d);
+  RowWeights hi{};
+  hi.w[1][0] = lo.w[1][0];
+  hi.w[1][1] = lo.w[1][1];
+  hi.w[1][2] = lo.w[1][2];
+  hi.w[0][0] = lo.w[2][0];
+  hi.w[0][1] = lo.w[2][1];
+  hi.w[0][2] = lo.w[2][2];
+  c.s_lo = lo;
+  c.s_hi = hi;
+}
+
+// ---- preconditioner: x/y forward transforms, z lines, inverse transforms ----
+// in -> tA (x fwd) -> tB (y fwd) -> tA (z) -> tB (y inv) -> out (x inv); out may alias in.
+template <typename T>
+void precond(helm6_ctx* c, const T* in, T* out, T* tA, T* tB, T* cw, const T* Vx, const T* Wx,
+             const T* Vy, const T* Wy) {
+  const Geom& g = c->g;
+  cudaStream_t s = c->stream;
+  const int64_t plane = (int64_t)g.mx * g.my;
+  launch_axis_gemm<T>(Wx, in, tA, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+  launch_axis_gemm<T>(Wy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  launch_ztri<T>(g, c->lamx, c->lamy, c->diag0, c->alpha, tB, tA, cw, c->status, s);
+  launch_axis_gemm<T>(Vy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  launch_axis_gemm<T>(Vx, tB, out, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+}
+
+void precond64(helm6_ctx* c, const double* in, double* out) {
+  precond<double>(c, in, out, c->tA64, c->tB64, c->cw64, c->Vx64, c->Wx64, c->Vy64, c->Wy64);
+}
+void precond32(helm6_ctx* c, const float* in, float* out) {
+  precond<float>(c, in, out, c->tA32, c->tB32, c->cw32, c->Vx32, c->Wx32, c->Vy32, c->Wy32);
+}
+
+// ---- norms ----
+template <typename T>
+int norm2(helm6_ctx* c, const T* x, double* out) {
+  launch_sumsq<T>(x, c->g.N, c->partial, c->nred, c->stream);
+  launch_reduce_sum(c->partial, c->nred, c->scal, c->stream);
+  CK(cudaMemcpyAsync(c->pinned, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *out = std::sqrt(c->pinned[0]);
+  return HELM6_OK;
+}
+
+// r = F - A U (FP64) and ||r||
+int residual64(helm6_ctx* c, double* beta) {
+  int nb = 0;
+  launch_stencil<double>(c->g, c->coef, c->U64, c->R64, c->F64, nullptr, 1, c->spart, &nb, c->stream);
+  launch_reduce_sum(c->spart, nb, c->scal, c->stream);
+  CK(cudaMemcpyAsync(c->pinned, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *beta = std::sqrt(c->pinned[0]);
+  c->last_beta = *beta;
+  return HELM6_OK;
+}
+
+// One Arnoldi cycle (CGS2 orthogonalisation, FP64 Givens) on V[0] = r/beta.  Stops at
+// m steps, when the estimate |g_{j+1}| <= abs_tol, or after maxsteps.  On return y holds
+// the least-squares coefficients of the steps taken (*jused).
+template <typename T>
+int arnoldi(helm6_ctx* c, T* V, T* Z, T* w, T* zt, int m, double beta, double abs_tol, int maxsteps,
+            bool flexible, void (*prec)(helm6_ctx*, const T*, T*), const StencilCoef& coef, int* jused,
+            double* est_out, helm6_stats* st) {
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.N, vs = 2 * N;
+  const int ldh = c->mrest + 1;
+  CK(cudaMemsetAsync(c->H, 0, sizeof(double) * 2 * ldh * c->mrest, s));
+  CK(cudaMemsetAsync(c->gv, 0, sizeof(double) * 2 * ldh, s));
+  launch_set_complex(c->gv, beta, 0.0, s);
+  int j = 0;
+  double est = beta;
+  for (j = 0; j < m && j < maxsteps; ++j) {
+    T* vj = V + (int64_t)j * vs;
+    T* zj = flexible ? Z + (int64_t)j * vs : zt;
+    prec(c, vj, zj);
+    launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
+    double* Hcol = c->H + 2 * (int64_t)j * ldh;
+    const int cnt = j + 1;
+    launch_mdot<T>(V, vs, cnt, w, N, c->partial, c->nred, s);
+    launch_reduce_cols(c->partial, c->nred, 2 * cnt, Hcol, 0, s);
+    launch_update<T>(w, V, vs, cnt, Hcol, N, s);
+    launch_mdot<T>(V, vs, cnt, w, N, c->partial, c->nred, s);
+    launch_reduce_cols_accum(c->partial, c->nred, 2 * cnt, c->h2, Hcol, s);
+    launch_update<T>(w, V, vs, cnt, c->h2, N, s);
+    launch_sumsq<T>(w, N, c->partial, c->nred, s);
+    launch_reduce_sum(c->partial, c->nred, c->scal, s);
+    launch_set_subdiag(c->H, ldh, j, c->scal, c->scal + 1, s);
+    if (j + 1 < m) launch_scale_copy<T>(w, V + (int64_t)(j + 1) * vs, N, c->scal + 1, 0.0, s);
+    launch_givens(c->H, ldh, j, c->cs, c->sn, c->gv, c->scal + 2, s);
+    CK(cudaMemcpyAsync(c->pinned, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    est = c->pinned[0];
+    if (st) {
+      st->iters++;
+      if (st->nhist < HELM6_MAX_HIST) st->hist[st->nhist++] = est;  // scaled by caller
+    }
+    if (!(est > abs_tol) || !std::isfinite(est)) {
+      ++j;
+      break;
+    }
+  }
+  *jused = j;
+  *est_out = est;
+  launch_backsolve(c->H, ldh, j, c->gv, c->yv, s);
+  CK(cudaGetLastError());
+  return HELM6_OK;
+}
+
+void fix_hist(helm6_stats* st, int from, double scale) {
+  if (!st) return;
+  for (int i = from; i < st->nhist; ++i) st->hist[i] *= scale;
+}
+
+void push_hist(helm6_stats* st, double v) {
+  if (st && st->nhist < HELM6_MAX_HIST) st->hist[st->nhist++] = v;
+}
+
+int check_status(helm6_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&c->pinned[4], c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memcpy(&st, &c->pinned[4], sizeof(int));
+  return st;
+}
+
+// FP64 restarted GMRES / FGMRES on U64 with right side F64.
+int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {
+  const bool flex = c->opts.method == HELM6_FGMRES;
+  double beta;
+  int rc = residual64(c, &beta);
+  if (rc) return rc;
+  push_hist(st, beta / normF);
+  int iters = 0;
+  while (true) {
+    if (!std::isfinite(beta)) return HELM6_NONFINITE;
+    if (beta <= tol * normF) return HELM6_OK;
+    if (iters >= maxit) return HELM6_NOT_CONVERGED;
+    launch_scale_copy<double>(c->R64, c->V64, c->g.N, nullptr, 1.0 / beta, c->stream);
+    int j = 0;
+    double est = 0;
+    const int h0 = st ? st->nhist : 0;
+    rc = arnoldi<double>(c, c->V64, c->Z64, c->w64, c->zt64, m, beta, tol * normF, maxit - iters, flex,
+                         precond64, c->coef, &j, &est, st);
+    if (rc) return rc;
+    fix_hist(st, h0, 1.0 / normF);
+    iters += j;
+    if (flex) {
+      launch_lincomb<double, double>(c->Z64, 2 * c->g.N, j, c->yv, 1.0, c->U64, c->g.N, 1, c->stream);
+    } else {
+      launch_lincomb<double, double>(c->V64, 2 * c->g.N, j, c->yv, 1.0, c->E64, c->g.N, 0, c->stream);
+      precond64(c, c->E64, c->E64);
+      launch_axpy<double, double>(c->E64, c->U64, c->g.N, 1.0, c->stream);
+    }
+    if (st) st->outer++;
+    rc = residual64(c, &beta);
+    if (rc) return rc;
+    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+  }
+}
+
+// MIXED: FP64 refinement around FP32 FGMRES with the FP32 preconditioner.
+int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {
+  double beta;
+  int rc = residual64(c, &beta);
+  if (rc) return rc;
+  push_hist(st, beta / normF);
+  int iters = 0;
+  const double inner = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-5;
+  while (true) {
+    if (!std::isfinite(beta)) return HELM6_NONFINITE;
+    if (beta <= tol * normF) return HELM6_OK;
+    if (iters >= maxit) return HELM6_NOT_CONVERGED;
+    launch_convert<double, float>(c->R64, c->V32, c->g.N, 1.0 / beta, c->stream);
+    const double itol = std::max(inner, 0.3 * tol * normF / beta);
+    int j = 0;
+    double est = 0;
+    const int h0 = st ? st->nhist : 0;
+    rc = arnoldi<float>(c, c->V32, c->Z32, c->w32, c->zt32, m, 1.0, itol, maxit - iters, true, precond32,
+                        c->coef, &j, &est, st);
+    if (rc) return rc;
+    fix_hist(st, h0, beta / normF);
+    iters += j;
+    launch_lincomb<float, double>(c->Z32, 2 * c->g.N, j, c->yv, beta, c->U64, c->g.N, 1, c->stream);
+    if (st) st->outer++;
+    rc = residual64(c, &beta);
+    if (rc) return rc;
+    if (st && st->nhist > 0) st->hist[st->nhist - 1] = beta / normF;  // true residual
+    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+  }
+}
+
+// SKS (Algorithm 1) in its equivalent defect-correction form U <- U + A_p^{-1}(F - A U),
+// the residual computed in FP64; MIXED applies A_p^{-1} in FP32 to r/||r||.
+int solve_sks(helm6_ctx* c, double normF, double tol, int maxit, helm6_stats* st) {
+  double beta;
+  int rc = residual64(c, &beta);
+  if (rc) return rc;
+  const double beta0 = beta;
+  int iters = 0;
+  while (true) {
+    if (!std::isfinite(beta)) return HELM6_NONFINITE;
+    if (beta <= tol * normF) return HELM6_OK;
+    if (beta > kDiverge * std::max(beta0, normF)) return HELM6_DIVERGED;
+    if (iters >= maxit) return HELM6_NOT_CONVERGED;
+    if (c->opts.precision == HELM6_FP64) {
+      precond64(c, c->R64, c->E64);
+      launch_axpy<double, double>(c->E64, c->U64, c->g.N, 1.0, c->stream);
+    } else {
+      launch_convert<double, float>(c->R64, c->w32, c->g.N, 1.0 / beta, c->stream);
+      precond32(c, c->w32, c->zt32);
+      launch_axpy<float, double>(c->zt32, c->U64, c->g.N, beta, c->stream);
+    }
+    ++iters;
+    rc = residual64(c, &beta);
+    if (rc) return rc;
+    if (st) {
+      st->iters++;
+      push_hist(st, beta / normF);
+    }
+    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+  }
+}
+
+bool valid_face(int f) { return f == HELM6_DIRICHLET || f == HELM6_NEUMANN || f == HELM6_SOMMERFELD; }
+
+}  // namespace
+
+extern "C" {
+
+void helm6_opts_default(helm6_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HELM6_FP64;
+  o->method = HELM6_GMRES;
+  o->xform_terms = 3;
+  o->max_restart = 30;
+  o->inner_tol = 1e-5;
+  o->stream = nullptr;
+}
+
+const char* helm6_status_string(int code) {
+  switch (code) {
+    case HELM6_OK: return "ok";
+    case HELM6_NOT_CONVERGED: return "not converged (maxit reached)";
+    case HELM6_DIVERGED: return "diverged";
+    case HELM6_BREAKDOWN: return "breakdown (zero pivot in a z-line solve)";
+    case HELM6_NONFINITE: return "non-finite value in the input or the iteration";
+    case HELM6_ERR_INVALID: return "invalid argument";
+    case HELM6_ERR_NOMEM: return "device allocation failed";
+    case HELM6_ERR_CUDA: return "CUDA error";
+    case HELM6_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+void helm6_destroy(helm6_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[6], const helm6_opts* opts) {
+  if (!out || !faces || n < 1 || n > 4094) return HELM6_ERR_INVALID;
+  for (int i = 0; i < 6; ++i)
+    if (!valid_face(faces[i])) return HELM6_ERR_INVALID;
+  for (int i = 0; i < 4; ++i)
+    if (faces[i] == HELM6_SOMMERFELD) return HELM6_ERR_INVALID;
+  helm6_opts o;
+  helm6_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.precision != HELM6_FP64 && o.precision != HELM6_MIXED) return HELM6_ERR_INVALID;
+  if (o.method < HELM6_GMRES || o.method > HELM6_SKS) return HELM6_ERR_INVALID;
+  if (o.xform_terms == 0) o.xform_terms = 3;
+  if (o.xform_terms < 1 || o.xform_terms > 3) return HELM6_ERR_INVALID;
+  if (o.max_restart == 0) o.max_restart = 30;
+  if (o.max_restart < 1 || o.max_restart > 64) return HELM6_ERR_INVALID;
+  if (o.inner_tol == 0) o.inner_tol = 1e-5;
+  if (!(o.inner_tol > 0 && o.inner_tol < 1)) return HELM6_ERR_INVALID;
+  if (!(std::isfinite(k.re) && std::isfinite(k.im))) return HELM6_ERR_INVALID;
+
+  helm6_ctx* c = new helm6_ctx();
+  c->n = n;
+  c->h = (h > 0) ? h : 1.0 / (n + 1);
+  c->k = cd(k.re, k.im);
+  c->opts = o;
+  c->stream = (cudaStream_t)o.stream;
+  c->mrest = o.max_restart;
+  for (int i = 0; i < 6; ++i) c->g.face[i] = faces[i];
+  auto cnt = [&](int a) { return n + (faces[2 * a] != HELM6_DIRICHLET) + (faces[2 * a + 1] != HELM6_DIRICHLET); };
+  c->g.mx = cnt(0);
+  c->g.my = cnt(1);
+  c->g.mz = cnt(2);
+  c->g.N = (int64_t)c->g.mx * c->g.my * c->g.mz;
+  stencil_coefficients(c->k, c->h, c->coef);
+  const cd I(0.0, 1.0);
+  c->diag0 = to_pod(-2.0 + c->k * c->k * c->h * c->h);
+  c->alpha = to_pod(2.0 * I * c->k * c->h);
+
+  int rc = HELM6_OK;
+  auto fail = [&](int code) {
+    helm6_destroy(c);
+    return code;
+  };
+  // bases
+  std::vector<double> Vx, Wx, lx, Vy, Wy, ly;
+  basis(n, faces[0], faces[1], Vx, Wx, lx);
+  basis(n, faces[2], faces[3], Vy, Wy, ly);
+  const size_t mx2 = (size_t)c->g.mx * c->g.mx, my2 = (size_t)c->g.my * c->g.my;
+  if ((rc = dalloc(c, &c->Vx64, mx2)) || (rc = dalloc(c, &c->Wx64, mx2)) || (rc = dalloc(c, &c->Vy64, my2)) ||
+      (rc = dalloc(c, &c->Wy64, my2)) || (rc = dalloc(c, &c->Vx32, mx2)) || (rc = dalloc(c, &c->Wx32, mx2)) ||
+      (rc = dalloc(c, &c->Vy32, my2)) || (rc = dalloc(c, &c->Wy32, my2)) ||
+      (rc = dalloc(c, &c->lamx, (size_t)c->g.mx)) || (rc = dalloc(c, &c->lamy, (size_t)c->g.my)))
+    return fail(rc);
+  auto up64 = [&](double* d, const std::vector<double>& h_) {
+    return cudaMemcpy(d, h_.data(), h_.size() * sizeof(double), cudaMemcpyHostToDevice);
+  };
+  auto up32 = [&](float* d, const std::vector<double>& h_) {
+    std::vector<float> f(h_.begin(), h_.end());
+    return cudaMemcpy(d, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+  };
+  if (up64(c->Vx64, Vx) || up64(c->Wx64, Wx) || up64(c->Vy64, Vy) || up64(c->Wy64, Wy) || up64(c->lamx, lx) ||
+      up64(c->lamy, ly) || up32(c->Vx32, Vx) || up32(c->Wx32, Wx) || up32(c->Vy32, Vy) || up32(c->Wy32, Wy))
+    return fail(HELM6_ERR_CUDA);
+
+  // workspace
+  const int64_t N = c->g.N;
+  const size_t v = (size_t)(2 * N);
+  const int m = c->mrest;
+  if ((rc = dalloc(c, &c->F64, v)) || (rc = dalloc(c, &c->U64, v)) || (rc = dalloc(c, &c->R64, v)) ||
+      (rc = dalloc(c, &c->E64, v)))
+    return fail(rc);
+  if (o.precision == HELM6_FP64) {
+    const bool needZ = o.method == HELM6_FGMRES;
+    const bool krylov = o.method != HELM6_SKS;
+    if (krylov && (rc = dalloc(c, &c->V64, v * (m + 1)))) return fail(rc);
+    if (needZ && (rc = dalloc(c, &c->Z64, v * m))) return fail(rc);
+    if ((rc = dalloc(c, &c->w64, v)) || (rc = dalloc(c, &c->zt64, v)) || (rc = dalloc(c, &c->tA64, v)) ||
+        (rc = dalloc(c, &c->tB64, v)) || (rc = dalloc(c, &c->cw64, v)))
+      return fail(rc);
+  } else {
+    const bool krylov = o.method != HELM6_SKS;
+    if (krylov && ((rc = dalloc(c, &c->V32, v * (m + 1))) || (rc = dalloc(c, &c->Z32, v * m)))) return fail(rc);
+    if ((rc = dalloc(c, &c->w32, v)) || (rc = dalloc(c, &c->zt32, v)) || (rc = dalloc(c, &c->tA32, v)) ||
+        (rc = dalloc(c, &c->tB32, v)) || (rc = dalloc(c, &c->cw32, v)))
+      return fail(rc);
+    // FP64 scratch used by apply_Pinv in FP64 layout conversions
+    if ((rc = dalloc(c, &c->tA64, v))) return fail(rc);
+  }
+  c->nred = std::max(1, device_sm_count() * 4);
+  c->nsten = stencil_blocks(c->g);
+  if ((rc = dalloc(c, &c->partial, (size_t)c->nred * 2 * (m + 1))) || (rc = dalloc(c, &c->spart, (size_t)c->nsten)) ||
+      (rc = dalloc(c, &c->H, (size_t)2 * (m + 1) * m)) || (rc = dalloc(c, &c->cs, (size_t)2 * (m + 1))) ||
+      (rc = dalloc(c, &c->sn, (size_t)2 * (m + 1))) || (rc = dalloc(c, &c->gv, (size_t)2 * (m + 1))) ||
+      (rc = dalloc(c, &c->yv, (size_t)2 * (m + 1))) || (rc = dalloc(c, &c->h2, (size_t)2 * (m + 1))) ||
+      (rc = dalloc(c, &c->scal, 8)) || (rc = dalloc(c, &c->status, 1)))
+    return fail(rc);
+  if (cudaMallocHost((void**)&c->pinned, 16 * sizeof(double)) != cudaSuccess) return fail(HELM6_ERR_NOMEM);
+  if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
+  *out = c;
+  return HELM6_OK;
+}
+
+int helm6_dims(const helm6_ctx* c, int64_t dims[3]) {
+  if (!c || !dims) return HELM6_ERR_INVALID;
+  dims[0] = c->g.mx;
+  dims[1] = c->g.my;
+  dims[2] = c->g.mz;
+  return HELM6_OK;
+}
+
+int helm6_apply_A(helm6_ctx* c, const void* x, void* y) {
+  if (!c || !x || !y) return HELM6_ERR_INVALID;
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.N;
+  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  if (c->opts.precision == HELM6_FP64) {
+    launch_stencil<double>(c->g, c->coef, c->R64, c->E64, nullptr, nullptr, 0, nullptr, nullptr, s);
+  } else {
+    launch_convert<double, float>(c->R64, c->w32, N, 1.0, s);
+    launch_stencil<float>(c->g, c->coef, c->w32, c->zt32, nullptr, nullptr, 0, nullptr, nullptr, s);
+    launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
+  }
+  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  CK(cudaGetLastError());
+  return HELM6_OK;
+}
+
+int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
+  if (!c || !x || !y) return HELM6_ERR_INVALID;
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.N;
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  if (c->opts.precision == HELM6_FP64) {
+    precond64(c, c->R64, c->E64);
+  } else {
+    launch_convert<double, float>(c->R64, c->w32, N, 1.0, s);
+    precond32(c, c->w32, c->zt32);
+    launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
+  }
+  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  CK(cudaGetLastError());
+  const int st = check_status(c);
+  return st == HELM6_BREAKDOWN ? HELM6_BREAKDOWN : HELM6_OK;
+}
+
+int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, int maxit, helm6_stats* st) {
+  if (!c || !F || !u || !(tol > 0) || maxit < 0) return HELM6_ERR_INVALID;
+  if (c->opts.method != HELM6_SKS && (restart < 1 || restart > c->mrest)) return HELM6_ERR_INVALID;
+  const auto t0 = std::chrono::steady_clock::now();
+  helm6_stats local;
+  helm6_stats* S = st ? st : &local;
+  std::memset(S, 0, sizeof(*S));
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.N;
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  launch_interleaved_to_planar((const double*)F, c->F64, N, s);
+  double normF = 0;
+  int rc = norm2<double>(c, c->F64, &normF);
+  if (rc) return rc;
+  int status;
+  if (!std::isfinite(normF)) {
+    status = HELM6_NONFINITE;
+  } else if (normF == 0.0) {
+    CK(cudaMemsetAsync(u, 0, sizeof(double) * 2 * N, s));
+    CK(cudaStreamSynchronize(s));
+    status = HELM6_OK;
+  } else {
+    launch_interleaved_to_planar((const double*)u, c->U64, N, s);
+    if (c->opts.method == HELM6_SKS)
+      status = solve_sks(c, normF, tol, maxit, S);
+    else if (c->opts.precision == HELM6_FP64)
+      status = solve_fp64(c, normF, tol, restart, maxit, S);
+    else
+      status = solve_mixed(c, normF, tol, restart, maxit, S);
+    if (status < 0) return status;
+    launch_planar_to_interleaved(c->U64, (double*)u, N, s);
+    S->relres = c->last_beta / normF;
+  }
+  CK(cudaStreamSynchronize(s));
+  S->status = status;
+  S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+int helm6_rhs_gaussians(helm6_ctx* c, int nsrc, const double* centers, const helm6_c64* amps, double sigma,
+                        const void* noise, void* F) {
+  if (!c || !F || nsrc < 0 || nsrc > 4096 || !(sigma > 0)) return HELM6_ERR_INVALID;
+  if (nsrc > 0 && (!centers || !amps)) return HELM6_ERR_INVALID;
+  return rhs_gaussians(c->g, c->h, c->k, nsrc, centers, (const double*)amps, sigma, (const double*)noise,
+                       (double*)F, c->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of the helm6 library (not part of the C-ABI).
+//
+// Vectors inside the library are "planar": a complex field of N = mx*my*mz points is a
+// real array of 2N elements, the real plane [0, N) then the imaginary plane [N, 2N), each
+// indexed (l*my + j)*mx + i with x fastest.  FP64 vectors are double, MIXED-precision
+// Krylov vectors are float.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <vector>
+
+#include "../../include/helm6.h"
+
+namespace helm6 {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------------------
+// Small complex type usable in device code.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct cpx {
+  T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> mk(T r, T i) { return cpx<T>{r, i}; }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+// a + w * s  (complex fused multiply-add)
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> cfma(cpx<T> w, cpx<T> s, cpx<T> a) {
+  a.re = fma(w.re, s.re, a.re);
+  a.re = fma(-w.im, s.im, a.re);
+  a.im = fma(w.re, s.im, a.im);
+  a.im = fma(w.im, s.re, a.im);
+  return a;
+}
+
+struct c64d {  // plain-old-data complex double for kernel parameters
+  double re, im;
+};
+inline c64d to_pod(cd z) { return c64d{z.real(), z.imag()}; }
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> cast(c64d z) { return cpx<T>{(T)z.re, (T)z.im}; }
+
+// ---------------------------------------------------------------------------------------
+// Geometry and the scheme's coefficients.
+// ---------------------------------------------------------------------------------------
+struct Geom {
+  int mx, my, mz;       // unknowns per axis
+  int64_t N;            // mx*my*mz
+  int face[6];          // helm6_bc per face x0 x1 y0 y1 z0 z1
+};
+
+// Weights of one row type of the 27-point operator, per z-plane offset dz = -1, 0, +1:
+// w[dz+1][0] centre of that plane, [1] its 4 in-plane neighbours, [2] its 4 diagonals.
+struct RowWeights {
+  c64d w[3][3];
+};
+
+struct StencilCoef {
+  RowWeights interior;  // Eq. scheme
+  RowWeights s_lo;      // z = 0 Sommerfeld-like face row (Eq. 3DDISCS)
+  RowWeights s_hi;      // z = top face row, mirrored
+};
+
+// ---------------------------------------------------------------------------------------
+// Kernel launchers (stream-ordered).  Defined in the .cu files.
+// ---------------------------------------------------------------------------------------
+
+// y = A x  (mode 0);  y = f - A x (mode 1);  r = f - A x, y += r (mode 2, SKS-style).
+// sumsq (nullable): per-block partial sums of |result|^2 (mode 0/1: |y|^2, mode 2: |r|^2),
+// nblk entries written, reduced by reduce_sum.
+template <typename T>
+void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const T* f, T* r,
+                    int mode, double* sumsq, int* nblk, cudaStream_t s);
+
+// Number of blocks (and fused-norm partials) of launch_stencil for this geometry.
+int stencil_blocks(const Geom& g);
+
+// Batched strided real GEMM on planar data, C = A * B per batch:
+//  along_x = true : B(k, n) = B[b*bstride + n*ld + k], C(p, n) = C[b*bstride + n*ld + p]
+//  along_x = false: B(k, n) = B[b*bstride + k*ld + n], C(p, n) = C[b*bstride + p*ld + n]
+// A is P x K row-major (P = K = the axis length m).
+template <typename T>
+void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, int64_t bstride,
+                      int nbatch, bool along_x, cudaStream_t s);
+
+// Tridiagonal solve along z for every (x, y) mode pair, Thomas algorithm started at the
+// Sommerfeld-like end (if any).  x: input (destroyed), y: output, cw: scratch of 2N T.
+template <typename T>
+void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha,
+                 const T* x, T* y, T* cw, int* status, cudaStream_t s);
+
+// BLAS-1 style kernels on planar complex vectors of N points.
+template <typename T>
+void launch_mdot(const T* V, int64_t vstride, int count, const T* w, int64_t N, double* partial,
+                 int nblocks, cudaStream_t s);  // partial[b][i] (complex double) = sum conj(V_i) w
+void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
+                        cudaStream_t s);  // out[i] (+)= sum_b partial[b][i], complex double
+template <typename T>
+void launch_update(T* w, const T* V, int64_t vstride, int count, const double* h, int64_t N,
+                   cudaStream_t s);  // w -= sum_i V_i h_i
+template <typename T>
+void launch_sumsq(const T* x, int64_t N, double* partial, int nblocks, cudaStream_t s);
+template <typename T>
+void launch_scale_copy(const T* x, T* y, int64_t N, const double* inv_scale_dev, double host_scale,
+                       cudaStream_t s);  // y = x * (host_scale or 1/(*dev))
+template <typename TI, typename TO>
+void launch_lincomb(const TI* V, int64_t vstride, int count, const double* y, double scale, TO* out,
+                    int64_t N, int accumulate, cudaStream_t s);  // out (+)= scale*sum V_i y_i
+template <typename TI, typename TO>
+void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s);  // planar
+void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cudaStream_t s);
+void launch_planar_to_interleaved(const double* in, double* zout, int64_t N, cudaStream_t s);
+void launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t s);  // one double
+
+// Givens update of Hessenberg column j on the device (single thread, FP64):
+// applies the j previous rotations to H[:, j], makes rotation j, updates g; writes
+// |g_{j+1}| to *res.  H column-major with leading dimension ldh, complex double.
+void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* res,
+                   cudaStream_t s);
+// H[j+1, j] = sqrt(*sumsq); inv = 1/that (0 if zero).
+void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* inv, cudaStream_t s);
+// Solve the j x j upper triangular system R y = g (complex double) on the device.
+void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s);
+
+// Compact right side for Gaussian sources (FP64, complex128 interleaved output F).
+// centers: host nsrc*3, amps: host nsrc*2 (re, im); noise: device complex128 or nullptr.
+int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
+                  double sigma, const double* noise, double* F, cudaStream_t s);
+
+// Reduce partial columns into out and also add them into accum.
+void launch_reduce_cols_accum(const double* partial, int nblocks, int ncols, double* out,
+                              double* accum, cudaStream_t s);
+
+// y += alpha x (planar, 2N reals), mixed input/output precision.
+template <typename TI, typename TO>
+void launch_axpy(const TI* x, TO* y, int64_t N, double alpha, cudaStream_t s);
+// p[0] = re, p[1] = im on the device (stream-ordered).
+void launch_set_complex(double* p, double re, double im, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace helm6

@@ -1,0 +1,182 @@
+// Direct inverse of the 7-point preconditioner A_p (Eq. 3DAP) by separation of variables:
+//   X^ = (W_y (x) W_x) X           forward eigen-transforms along x and y (W = V^{-1})
+//   (T_z + (lam_p + lam_q) I) U^_pq = X^_pq   for every mode pair (p, q)
+//   U  = (V_y (x) V_x) U^          inverse transforms
+// This file holds the SIMT pieces: a batched strided real GEMM for the transforms (used
+// in FP64, and in FP32 where the tensor-core path is not used) and the batched complex
+// Thomas solver for the z lines.
+#include "helm6_internal.h"
+
+namespace helm6 {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+// C(p, n) = sum_k A[p*m + k] B(k, n), one 64 x 64 tile of C per block, 4 x 4 per thread.
+template <typename T, bool ALONG_X>
+__global__ void __launch_bounds__(256)
+    axis_gemm_kernel(const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ C, int m,
+                     int ncols, int ld, int64_t bstride) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int p0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const T* Bb = B + (int64_t)blockIdx.z * bstride;
+  T* Cb = C + (int64_t)blockIdx.z * bstride;
+  // along x the output is contiguous in p: let consecutive threads walk p
+  const int tp = ALONG_X ? (tid & 15) : (tid >> 4);
+  const int tn = ALONG_X ? (tid >> 4) : (tid & 15);
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+
+  for (int k0 = 0; k0 < m; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      const int pp = e / BK, kk = e - pp * BK;
+      const int gp = p0 + pp, gk = k0 + kk;
+      As[kk][pp] = (gp < m && gk < m) ? A[(int64_t)gp * m + gk] : T(0);
+    }
+    if (ALONG_X) {
+      for (int e = tid; e < BN * BK; e += 256) {
+        const int nn = e / BK, kk = e - nn * BK;
+        const int gn = n0 + nn, gk = k0 + kk;
+        Bs[kk][nn] = (gn < ncols && gk < m) ? Bb[(int64_t)gn * ld + gk] : T(0);
+      }
+    } else {
+      for (int e = tid; e < BN * BK; e += 256) {
+        const int kk = e / BN, nn = e - kk * BN;
+        const int gn = n0 + nn, gk = k0 + kk;
+        Bs[kk][nn] = (gn < ncols && gk < m) ? Bb[(int64_t)gk * ld + gn] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][tp + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tn + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int gp = p0 + tp + 16 * a;
+    if (gp >= m) continue;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int gn = n0 + tn + 16 * b;
+      if (gn >= ncols) continue;
+      if (ALONG_X)
+        Cb[(int64_t)gn * ld + gp] = acc[a][b];
+      else
+        Cb[(int64_t)gp * ld + gn] = acc[a][b];
+    }
+  }
+}
+
+// One thread per (p, q) line along z.  Rows of T_z + sigma I in the natural order l:
+//   a_l U_{l-1} + d_l U_l + c_l U_{l+1},  a = c = 1 except the corner entries 2 at a
+//   Neumann / Sommerfeld-like end (beta = 1), d_l = -2 + k^2h^2 + sigma (+ 2ikh at a
+//   Sommerfeld-like end).  Elimination starts at the Sommerfeld-like end when only the top
+//   face is one (there the pivots keep a positive imaginary part).
+template <typename T>
+__global__ void ztri_kernel(Geom g, const double* __restrict__ lamx, const double* __restrict__ lamy,
+                            c64d diag0, c64d alpha, const T* __restrict__ x, T* __restrict__ y,
+                            T* __restrict__ cw, int* status) {
+  const int64_t plane = (int64_t)g.mx * g.my;
+  const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= plane) return;
+  const int p = (int)(pq % g.mx), q = (int)(pq / g.mx);
+  const double sig = lamx[p] + lamy[q];
+  const int m = g.mz;
+  const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
+  const T c_lo = (g.face[4] != HELM6_DIRICHLET) ? T(2) : T(1);
+  const T a_hi = (g.face[5] != HELM6_DIRICHLET) ? T(2) : T(1);
+  const bool rev = (!lo_s && hi_s);
+  const cpx<T> dint = mk((T)(diag0.re + sig), (T)diag0.im);
+  const cpx<T> al = cast<T>(alpha);
+  const int64_t N = g.N;
+
+  cpx<T> cprev = mk(T(0), T(0)), yprev = mk(T(0), T(0));
+  bool bad = false;
+  for (int r = 0; r < m; ++r) {
+    const int l = rev ? (m - 1 - r) : r;
+    // coefficients in elimination order: sub = towards the previous row, sup = next
+    T a_l = (l == m - 1) ? a_hi : T(1);
+    T c_l = (l == 0) ? c_lo : T(1);
+    if (l == 0) a_l = T(0);
+    if (l == m - 1) c_l = T(0);
+    const T sub = rev ? c_l : a_l;
+    const T sup = rev ? a_l : c_l;
+    cpx<T> d = dint;
+    if (l == 0 && lo_s) d = d + al;
+    if (l == m - 1 && hi_s) d = d + al;
+    const cpx<T> den = d - sub * cprev;
+    const T n2 = den.re * den.re + den.im * den.im;
+    if (!(n2 > T(0))) bad = true;
+    const T inv = T(1) / n2;
+    const cpx<T> rinv = mk(den.re * inv, -den.im * inv);
+    const int64_t idx = (int64_t)l * plane + pq;
+    const cpx<T> xv = mk(x[idx], x[N + idx]);
+    const cpx<T> cp = sup * rinv;
+    const cpx<T> yp = (xv - sub * yprev) * rinv;
+    cw[idx] = cp.re;
+    cw[N + idx] = cp.im;
+    y[idx] = yp.re;
+    y[N + idx] = yp.im;
+    cprev = cp;
+    yprev = yp;
+  }
+  cpx<T> next = mk(T(0), T(0));
+  for (int r = m - 1; r >= 0; --r) {
+    const int l = rev ? (m - 1 - r) : r;
+    const int64_t idx = (int64_t)l * plane + pq;
+    const cpx<T> cp = mk(cw[idx], cw[N + idx]);
+    const cpx<T> v = mk(y[idx], y[N + idx]) - cp * next;
+    y[idx] = v.re;
+    y[N + idx] = v.im;
+    next = v;
+  }
+  if (bad) atomicExch(status, (int)HELM6_BREAKDOWN);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, int64_t bstride,
+                      int nbatch, bool along_x, cudaStream_t s) {
+  dim3 grid((ncols + BN - 1) / BN, (m + BM - 1) / BM, nbatch);
+  if (along_x)
+    axis_gemm_kernel<T, true><<<grid, 256, 0, s>>>(A, B, C, m, ncols, ld, bstride);
+  else
+    axis_gemm_kernel<T, false><<<grid, 256, 0, s>>>(A, B, C, m, ncols, ld, bstride);
+}
+
+template <typename T>
+void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha,
+                 const T* x, T* y, T* cw, int* status, cudaStream_t s) {
+  const int64_t lines = (int64_t)g.mx * g.my;
+  const int bs = 128;
+  ztri_kernel<T><<<(unsigned)((lines + bs - 1) / bs), bs, 0, s>>>(g, lamx, lamy, diag0, alpha, x, y,
+                                                                  cw, status);
+}
+
+template void launch_axis_gemm<float>(const float*, const float*, float*, int, int, int, int64_t, int,
+                                      bool, cudaStream_t);
+template void launch_axis_gemm<double>(const double*, const double*, double*, int, int, int, int64_t,
+                                       int, bool, cudaStream_t);
+template void launch_ztri<float>(const Geom&, const double*, const double*, c64d, c64d, const float*,
+                                 float*, float*, int*, cudaStream_t);
+template void launch_ztri<double>(const Geom&, const double*, const double*, c64d, c64d,
+                                  const double*, double*, double*, int*, cudaStream_t);
+
+}  // namespace helm6

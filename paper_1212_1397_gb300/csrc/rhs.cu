@@ -1,0 +1,189 @@
+// Compact right side F of the sixth-order scheme for sums of Gaussian sources (FP64).
+//
+// Interior (Eq. scheme right side, h^2-scaled; the mixed fourth derivatives carry the
+// total weight h^4/90 that makes the scheme sixth order):
+//   F = h^2 [ cf f + q1 lap f + (h^4/360) sum_a f_aaaa + (h^4/90) sum_{a<b} f_aabb ] + h^2 cf eta
+//   cf = 1 - k^2h^2/12 + k^4h^4/360,  q1 = (h^2/12)(1 - k^2h^2/30).
+// Neumann face rows (Eq. 3DN, homogeneous data, minus sign on the 7h^5/180 term):
+//   F -= D_N,  D_N = dn1 f_n + dn3 f_nnn + dnm (f_ntt + f_nss)
+// Sommerfeld-like face rows (Eq. 3DDISCS), fbar = exp(ik n) f in the inward normal n:
+//   F -= D_S,  D_S = -e^{ikh} mu3 [ 2h Fbar + mu1 (h^5/3)(fbar_ntt + fbar_nss) ].
+// A Gaussian is separable, so each source contributes products of 1D derivatives
+// G_a^(m)(x_a), m = 0..4, tabulated per axis by the host.
+#include <algorithm>
+#include <cmath>
+
+#include "helm6_internal.h"
+
+namespace helm6 {
+
+namespace {
+
+struct RhsCoef {
+  double h;
+  c64d cf, q1;         // interior
+  c64d dn1;            // Neumann: coefficient of f_n
+  double dn3, dnm;     // Neumann: f_nnn and f_ntt + f_nss
+  c64d ik;             // Sommerfeld-like: i k
+  c64d a1, a2;         // Fbar = a1 fb_n + a2 fb_nn + a3 (fb_nnn - fb_ntt - fb_nss)
+  double a3;
+  c64d e1mu3, mu1h5;   // D_S = -e1mu3 (2h Fbar + mu1h5 (fb_ntt + fb_nss))
+};
+
+using Z = cpx<double>;
+
+__device__ __forceinline__ Z zc(c64d a) { return Z{a.re, a.im}; }
+
+// Source-summed derivative f^(ox, oy, oz) at node (i, j, l).
+__device__ __forceinline__ Z deriv(const double* tab, const double* amps, int nsrc, int mmax, int i, int j,
+                                   int l, int ox, int oy, int oz) {
+  Z s = Z{0.0, 0.0};
+  for (int k = 0; k < nsrc; ++k) {
+    const double* t = tab + (int64_t)k * 15 * mmax;
+    const double v = t[(0 * 5 + ox) * mmax + i] * t[(1 * 5 + oy) * mmax + j] * t[(2 * 5 + oz) * mmax + l];
+    s.re += amps[2 * k] * v;
+    s.im += amps[2 * k + 1] * v;
+  }
+  return s;
+}
+
+__global__ void rhs_kernel(Geom g, RhsCoef c, int nsrc, int mmax, const double* __restrict__ tab,
+                           const double* __restrict__ amps, const double* __restrict__ noise,
+                           double* __restrict__ F) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.N) return;
+  const int i = (int)(idx % g.mx);
+  const int j = (int)((idx / g.mx) % g.my);
+  const int l = (int)(idx / ((int64_t)g.mx * g.my));
+  Z S0{0, 0}, S1{0, 0}, S2{0, 0}, S3{0, 0};
+  for (int k = 0; k < nsrc; ++k) {
+    const double* t = tab + (int64_t)k * 15 * mmax;
+    double gx[5], gy[5], gz[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      gx[m] = t[(0 * 5 + m) * mmax + i];
+      gy[m] = t[(1 * 5 + m) * mmax + j];
+      gz[m] = t[(2 * 5 + m) * mmax + l];
+    }
+    const double f0 = gx[0] * gy[0] * gz[0];
+    const double lap = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2];
+    const double p4 = gx[4] * gy[0] * gz[0] + gx[0] * gy[4] * gz[0] + gx[0] * gy[0] * gz[4];
+    const double m4 = gx[2] * gy[2] * gz[0] + gx[2] * gy[0] * gz[2] + gx[0] * gy[2] * gz[2];
+    const Z a = Z{amps[2 * k], amps[2 * k + 1]};
+    S0 = S0 + f0 * a;
+    S1 = S1 + lap * a;
+    S2 = S2 + p4 * a;
+    S3 = S3 + m4 * a;
+  }
+  const double h = c.h, h2 = h * h, h4 = h2 * h2;
+  Z Fv = zc(c.cf) * S0 + zc(c.q1) * S1 + (h4 / 360.0) * S2 + (h4 / 90.0) * S3;
+  Fv = h2 * Fv;
+  if (noise) Fv = Fv + h2 * (zc(c.cf) * Z{noise[2 * idx], noise[2 * idx + 1]});
+
+  // face data terms
+  const int pos[3] = {i, j, l};
+  const int dimv[3] = {g.mx, g.my, g.mz};
+  for (int ax = 0; ax < 3; ++ax) {
+    for (int side = 0; side < 2; ++side) {
+      const int kind = g.face[2 * ax + side];
+      if (kind == HELM6_DIRICHLET) continue;
+      if (pos[ax] != (side == 0 ? 0 : dimv[ax] - 1)) continue;
+      const double sg = side == 0 ? 1.0 : -1.0;
+      const int t1 = (ax == 0) ? 1 : 0, t2 = (ax == 2) ? 1 : 2;
+      auto d = [&](int on, int o1, int o2) {
+        int o[3] = {0, 0, 0};
+        o[ax] = on;
+        o[t1] = o1;
+        o[t2] = o2;
+        Z v = deriv(tab, amps, nsrc, mmax, i, j, l, o[0], o[1], o[2]);
+        const double sgn = (on & 1) ? sg : 1.0;
+        return sgn * v;
+      };
+      if (kind == HELM6_NEUMANN) {
+        const Z DN = zc(c.dn1) * d(1, 0, 0) + c.dn3 * d(3, 0, 0) + c.dnm * (d(1, 2, 0) + d(1, 0, 2));
+        Fv = Fv - DN;
+      } else {
+        const Z ik = zc(c.ik), ik2 = ik * ik, ik3 = ik2 * ik;
+        const Z f0 = d(0, 0, 0), fn = d(1, 0, 0), fnn = d(2, 0, 0), fnnn = d(3, 0, 0);
+        const Z ftt = d(0, 2, 0), fss = d(0, 0, 2), fntt = d(1, 2, 0), fnss = d(1, 0, 2);
+        const Z fb_n = ik * f0 + fn;
+        const Z fb_nn = ik2 * f0 + 2.0 * (ik * fn) + fnn;
+        const Z fb_nnn = ik3 * f0 + 3.0 * (ik2 * fn) + 3.0 * (ik * fnn) + fnnn;
+        const Z fb_ntt = ik * ftt + fntt;
+        const Z fb_nss = ik * fss + fnss;
+        const Z Fbar = zc(c.a1) * fb_n + zc(c.a2) * fb_nn + c.a3 * (fb_nnn - fb_ntt - fb_nss);
+        const Z DS = Z{0.0, 0.0} - zc(c.e1mu3) * ((2.0 * h) * Fbar + zc(c.mu1h5) * (fb_ntt + fb_nss));
+        Fv = Fv - DS;
+      }
+    }
+  }
+  F[2 * idx] = Fv.re;
+  F[2 * idx + 1] = Fv.im;
+}
+
+}  // namespace
+
+// Host side: 1D derivative tables G^(m)(x) = (-1/sigma)^m He_m(t) exp(-t^2/2), t = (x-c)/sigma,
+// with He the probabilists' Hermite polynomials, at the unknown nodes of each axis.
+int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
+                  double sigma, const double* noise, double* F, cudaStream_t s) {
+  const int mmax = std::max(g.mx, std::max(g.my, g.mz));
+  const int mdim[3] = {g.mx, g.my, g.mz};
+  std::vector<double> tab((size_t)std::max(nsrc, 1) * 15 * mmax, 0.0);
+  for (int src = 0; src < nsrc; ++src) {
+    for (int ax = 0; ax < 3; ++ax) {
+      const int start = (g.face[2 * ax] == HELM6_DIRICHLET) ? 1 : 0;
+      for (int p = 0; p < mdim[ax]; ++p) {
+        const double x = (start + p) * h;
+        const double t = (x - centers[3 * src + ax]) / sigma;
+        const double e = std::exp(-0.5 * t * t);
+        double he[5];
+        he[0] = 1.0;
+        he[1] = t;
+        for (int m = 1; m < 4; ++m) he[m + 1] = t * he[m] - m * he[m - 1];
+        double sc = 1.0;
+        for (int m = 0; m < 5; ++m) {
+          tab[((size_t)src * 15 + ax * 5 + m) * mmax + p] = sc * he[m] * e;
+          sc *= -1.0 / sigma;
+        }
+      }
+    }
+  }
+  double *dtab = nullptr, *damps = nullptr;
+  if (cudaMallocAsync((void**)&dtab, tab.size() * sizeof(double), s) != cudaSuccess) return HELM6_ERR_NOMEM;
+  if (cudaMallocAsync((void**)&damps, (size_t)std::max(nsrc, 1) * 2 * sizeof(double), s) != cudaSuccess) {
+    cudaFreeAsync(dtab, s);
+    return HELM6_ERR_NOMEM;
+  }
+  cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (nsrc > 0)
+    cudaMemcpyAsync(damps, amps, (size_t)nsrc * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+
+  RhsCoef c;
+  const cd I(0.0, 1.0);
+  const cd kh2 = k * k * h * h;
+  const double h2 = h * h, h3 = h2 * h, h4 = h2 * h2, h5 = h4 * h;
+  c.h = h;
+  c.cf = to_pod(1.0 - kh2 / 12.0 + kh2 * kh2 / 360.0);
+  c.q1 = to_pod((h2 / 12.0) * (1.0 - kh2 / 30.0));
+  c.dn1 = to_pod(-(h3 / 3.0) * (1.0 - kh2 / 20.0));
+  c.dn3 = -h5 / 60.0;
+  c.dnm = -7.0 * h5 / 180.0;
+  const cd ik = I * k;
+  c.ik = to_pod(ik);
+  const cd mu3 = 1.0 / (1.0 + (2.0 * ik * h / 3.0) * (1.0 + 2.0 * kh2 / 15.0));
+  const cd mu1 = (ik * h / 90.0 + (1.0 + kh2 / 30.0) / (6.0 * mu3)) / (1.0 + 2.0 * ik * h / 3.0);
+  c.a1 = to_pod(h2 / 6.0 + k * k * h4 / 45.0);
+  c.a2 = to_pod(-ik * h4 / 90.0);
+  c.a3 = h4 / 120.0;
+  c.e1mu3 = to_pod(std::exp(ik * h) * mu3);
+  c.mu1h5 = to_pod(mu1 * h5 / 3.0);
+
+  const int bs = 256;
+  rhs_kernel<<<(unsigned)((g.N + bs - 1) / bs), bs, 0, s>>>(g, c, nsrc, mmax, dtab, damps, noise, F);
+  cudaFreeAsync(dtab, s);
+  cudaFreeAsync(damps, s);
+  return cudaGetLastError() == cudaSuccess ? HELM6_OK : HELM6_ERR_CUDA;
+}
+
+}  // namespace helm6

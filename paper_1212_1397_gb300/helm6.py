@@ -1,0 +1,187 @@
+"""Python binding of the helm6 C-ABI (ctypes; argument marshalling only).
+
+Every step of the solver runs in the CUDA library libhelm6.so; this module only turns
+torch tensors into device pointers and structs into ctypes.  Importing it does not need a
+GPU; opening the library does, and a missing library raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhelm6.so")
+
+DIRICHLET, NEUMANN, SOMMERFELD = 0, 1, 2
+FP64, MIXED = 0, 1
+GMRES, FGMRES, SKS = 0, 1, 2
+MAX_HIST = 1024
+
+STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "DIVERGED", 3: "BREAKDOWN", 4: "NONFINITE",
+          -1: "ERR_INVALID", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED"}
+
+_FACE_CODE = {"D": DIRICHLET, "N": NEUMANN, "S": SOMMERFELD}
+
+# every symbol declared in include/helm6.h
+EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", "helm6_apply_Pinv",
+           "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string")
+
+
+class C64(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("method", C.c_int), ("xform_terms", C.c_int),
+                ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
+                ("relres", C.c_double), ("t_total_ms", C.c_double), ("nhist", C.c_int),
+                ("hist", C.c_double * MAX_HIST)]
+
+    def to_dict(self):
+        return dict(iters=self.iters, outer=self.outer, status=STATUS.get(self.status, self.status),
+                    relres=self.relres, t_total_ms=self.t_total_ms,
+                    history=list(self.hist[: self.nhist]))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Open libhelm6.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1212_1397_gb300.build.build()")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    lib.helm6_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.helm6_opts_default.restype = None
+    lib.helm6_create.argtypes = [C.POINTER(P), I, D, C64, C.POINTER(C.c_int), C.POINTER(Opts)]
+    lib.helm6_create.restype = I
+    lib.helm6_dims.argtypes = [P, C.POINTER(C.c_int64)]
+    lib.helm6_dims.restype = I
+    lib.helm6_apply_A.argtypes = [P, P, P]
+    lib.helm6_apply_A.restype = I
+    lib.helm6_apply_Pinv.argtypes = [P, P, P]
+    lib.helm6_apply_Pinv.restype = I
+    lib.helm6_solve.argtypes = [P, P, P, D, I, I, C.POINTER(Stats)]
+    lib.helm6_solve.restype = I
+    lib.helm6_rhs_gaussians.argtypes = [P, I, C.POINTER(C.c_double), C.POINTER(C64), D, P, P]
+    lib.helm6_rhs_gaussians.restype = I
+    lib.helm6_destroy.argtypes = [P]
+    lib.helm6_destroy.restype = None
+    lib.helm6_status_string.argtypes = [I]
+    lib.helm6_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class Helm6Error(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc < 0:
+        msg = load().helm6_status_string(rc).decode()
+        raise Helm6Error(f"{what}: {msg} ({rc})")
+    return rc
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("expected a contiguous complex128 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One helm6 context: grid, wavenumber, faces and options fixed at construction.
+
+    faces: 6 letters 'x0 x1 y0 y1 z0 z1' over D (Dirichlet), N (Neumann), S (Sommerfeld-like).
+    Vectors are complex128 CUDA tensors of shape (mz, my, mx).
+    """
+
+    def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
+                 max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None):
+        lib = load()
+        self._lib = lib
+        o = Opts()
+        lib.helm6_opts_default(C.byref(o))
+        o.precision, o.method, o.max_restart = precision, method, max_restart
+        o.inner_tol, o.xform_terms = inner_tol, xform_terms
+        if stream is not None:
+            o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.stream = stream
+        f = (C.c_int * 6)(*[_FACE_CODE[ch] for ch in faces])
+        kk = complex(k)
+        ctx = C.c_void_p()
+        _check(lib.helm6_create(C.byref(ctx), int(n), float(h), C64(kk.real, kk.imag), f, C.byref(o)),
+               "helm6_create")
+        self._ctx = ctx
+        d = (C.c_int64 * 3)()
+        _check(lib.helm6_dims(ctx, d), "helm6_dims")
+        self.dims = (d[0], d[1], d[2])
+        self.shape = (d[2], d[1], d[0])
+        self.n, self.k, self.faces = n, kk, faces
+        self.h = h if h > 0 else 1.0 / (n + 1)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.helm6_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def empty(self):
+        import torch
+        return torch.zeros(self.shape, dtype=torch.complex128, device="cuda")
+
+    def apply_A(self, x, y=None):
+        y = self.empty() if y is None else y
+        _check(self._lib.helm6_apply_A(self._ctx, _ptr(x), _ptr(y)), "helm6_apply_A")
+        return y
+
+    def apply_Pinv(self, x, y=None):
+        y = self.empty() if y is None else y
+        rc = _check(self._lib.helm6_apply_Pinv(self._ctx, _ptr(x), _ptr(y)), "helm6_apply_Pinv")
+        if rc != 0:
+            raise Helm6Error(f"helm6_apply_Pinv: {STATUS.get(rc)}")
+        return y
+
+    def solve(self, F, u=None, tol=1e-8, restart=30, maxit=500):
+        """Solve A u = F (u in/out, zero if None).  Returns (u, stats dict)."""
+        u = self.empty() if u is None else u
+        st = Stats()
+        rc = _check(self._lib.helm6_solve(self._ctx, _ptr(F), _ptr(u), float(tol), int(restart),
+                                          int(maxit), C.byref(st)), "helm6_solve")
+        d = st.to_dict()
+        d["rc"] = rc
+        return u, d
+
+    def rhs_gaussians(self, sources, noise=None, F=None):
+        """Compact right side for helm6_inputs.GaussianSources (+ optional noise tensor)."""
+        F = self.empty() if F is None else F
+        ns = len(sources)
+        cen = (C.c_double * max(3 * ns, 1))(*sources.centers.ravel().tolist())
+        amps = (C64 * max(ns, 1))(*[C64(a.real, a.imag) for a in sources.amps])
+        nptr = _ptr(noise) if noise is not None else None
+        _check(self._lib.helm6_rhs_gaussians(self._ctx, ns, cen, amps, float(sources.sigma), nptr,
+                                             _ptr(F)), "helm6_rhs_gaussians")
+        return F
