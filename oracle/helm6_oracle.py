@@ -397,8 +397,8 @@ class Preconditioner:
         Vx, Vy = self.V
         lx, ly = self.lam
         Y = np.asarray(Y, dtype=np.complex128)
-        Yh = np.einsum("px,zyx->zyp", Wx, Y)
-        Yh = np.einsum("qy,zyp->zqp", Wy, Yh)
+        Yh = Y @ Wx.T          # Yh[z, y, p] = sum_x Wx[p, x] Y[z, y, x]
+        Yh = Wy @ Yh           # Yh[z, q, p] = sum_y Wy[q, y] Yh[z, y, p]
         Uh = np.empty_like(Yh)
         mz = Yh.shape[0]
         for q in range(Yh.shape[1]):
@@ -412,8 +412,8 @@ class Preconditioner:
                 if info != 0:
                     raise np.linalg.LinAlgError(f"singular z-line ({p},{q})")
                 Uh[:, q, p] = x
-        U = np.einsum("yq,zqp->zyp", Vy, Uh)
-        return np.einsum("xp,zyp->zyx", Vx, U)
+        U = Vy @ Uh            # U[z, y, p] = sum_q Vy[y, q] Uh[z, q, p]
+        return U @ Vx.T        # U[z, y, x] = sum_p Vx[x, p] U[z, y, p]
 
 
 # ======================================================================================
