@@ -139,6 +139,35 @@ int helm6_solve(helm6_ctx* ctx, const void* F, void* u, double tol, int restart,
 int helm6_rhs_gaussians(helm6_ctx* ctx, int nsrc, const double* centers,
                         const helm6_c64* amps, double sigma, const void* noise, void* F);
 
+/* ---- Measurement (not part of the method) ----
+ * Per-phase device time of helm6_solve / helm6_apply_* measured with CUDA events on the
+ * context's stream, and the number of kernels the library launched.  Off by default;
+ * enabling it resets the counters.  Phases: */
+enum {
+  HELM6_PH_STENCIL = 0,  /* 27-point operator in the Krylov precision */
+  HELM6_PH_XFWD = 1,     /* preconditioner x forward transform */
+  HELM6_PH_YFWD = 2,     /* y forward transform */
+  HELM6_PH_ZTRI = 3,     /* z tridiagonal lines */
+  HELM6_PH_YINV = 4,     /* y inverse transform */
+  HELM6_PH_XINV = 5,     /* x inverse transform */
+  HELM6_PH_ORTHO = 6,    /* CGS2 dot products, updates, norms, Givens */
+  HELM6_PH_RESID64 = 7,  /* FP64 true residual F - A U and its norm */
+  HELM6_PH_OTHER = 8,    /* conversions, solution updates */
+  HELM6_NPHASE = 9
+};
+
+typedef struct {
+  int64_t launches;              /* kernels launched by the library since enabling */
+  int64_t count[HELM6_NPHASE];   /* timed intervals per phase */
+  double ms[HELM6_NPHASE];       /* summed device milliseconds per phase */
+} helm6_profile;
+
+/* enable != 0 starts (and resets) measurement, 0 stops it.  INVALID if ctx is NULL. */
+int helm6_profile_enable(helm6_ctx* ctx, int enable);
+
+/* Copy the counters accumulated so far into *out (synchronises the stream). */
+int helm6_profile_read(helm6_ctx* ctx, helm6_profile* out);
+
 /* Release the workspace and the context (NULL is allowed).  Synchronises its stream. */
 void helm6_destroy(helm6_ctx* ctx);
 

@@ -47,6 +47,17 @@ struct helm6_ctx {
   int* status = nullptr;
   double* pinned = nullptr;  // host-pinned readback slots
   std::vector<void*> allocs;
+  // measurement (helm6_profile_enable)
+  struct Pending {
+    int ph;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool, ev_all;
+  std::vector<Pending> ev_pend;
+  int64_t prof_count[HELM6_NPHASE] = {};
+  double prof_ms[HELM6_NPHASE] = {};
+  long long prof_l0 = 0;
 };
 
 namespace {
@@ -73,6 +84,38 @@ int dalloc(helm6_ctx* c, T** p, size_t count) {
   c->allocs.push_back(q);
   *p = (T*)q;
   return HELM6_OK;
+}
+
+// ---- per-phase event timing (measurement only) ----
+void prof_flush(helm6_ctx* c) {
+  for (auto& p : c->ev_pend) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_count[p.ph] += 1;
+      c->prof_ms[p.ph] += ms;
+    }
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->ev_pend.clear();
+}
+
+cudaEvent_t prof_start(helm6_ctx* c) {
+  if (!c->prof_on) return nullptr;
+  if (c->ev_pool.size() < 2) prof_flush(c);
+  if (c->ev_pool.size() < 2) return nullptr;
+  cudaEvent_t a = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  cudaEventRecord(a, c->stream);
+  return a;
+}
+
+void prof_stop(helm6_ctx* c, int ph, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  cudaEventRecord(b, c->stream);
+  c->ev_pend.push_back({ph, a, b});
 }
 
 // ---- 1D eigenbases of the x and y second-difference matrices (closed forms) ----
@@ -184,11 +227,21 @@ void precond(helm6_ctx* c, const T* in, T* out, T* tA, T* tB, T* cw, const T* Vx
   const Geom& g = c->g;
   cudaStream_t s = c->stream;
   const int64_t plane = (int64_t)g.mx * g.my;
+  cudaEvent_t e = prof_start(c);
   launch_axis_gemm<T>(Wx, in, tA, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+  prof_stop(c, HELM6_PH_XFWD, e);
+  e = prof_start(c);
   launch_axis_gemm<T>(Wy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  prof_stop(c, HELM6_PH_YFWD, e);
+  e = prof_start(c);
   launch_ztri<T>(g, c->lamx, c->lamy, c->diag0, c->alpha, tB, tA, cw, c->status, s);
+  prof_stop(c, HELM6_PH_ZTRI, e);
+  e = prof_start(c);
   launch_axis_gemm<T>(Vy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  prof_stop(c, HELM6_PH_YINV, e);
+  e = prof_start(c);
   launch_axis_gemm<T>(Vx, tB, out, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+  prof_stop(c, HELM6_PH_XINV, e);
 }
 
 void precond64(helm6_ctx* c, const double* in, double* out) {
@@ -212,8 +265,10 @@ int norm2(helm6_ctx* c, const T* x, double* out) {
 // r = F - A U (FP64) and ||r||
 int residual64(helm6_ctx* c, double* beta) {
   int nb = 0;
+  cudaEvent_t e = prof_start(c);
   launch_stencil<double>(c->g, c->coef, c->U64, c->R64, c->F64, nullptr, 1, c->spart, &nb, c->stream);
   launch_reduce_sum(c->spart, nb, c->scal, c->stream);
+  prof_stop(c, HELM6_PH_RESID64, e);
   CK(cudaMemcpyAsync(c->pinned, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *beta = std::sqrt(c->pinned[0]);
@@ -240,7 +295,10 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* w, T* zt, int m, double beta, double ab
     T* vj = V + (int64_t)j * vs;
     T* zj = flexible ? Z + (int64_t)j * vs : zt;
     prec(c, vj, zj);
+    cudaEvent_t e = prof_start(c);
     launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
+    prof_stop(c, HELM6_PH_STENCIL, e);
+    e = prof_start(c);
     double* Hcol = c->H + 2 * (int64_t)j * ldh;
     const int cnt = j + 1;
     launch_mdot<T>(V, vs, cnt, w, N, c->partial, c->nred, s);
@@ -254,8 +312,10 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* w, T* zt, int m, double beta, double ab
     launch_set_subdiag(c->H, ldh, j, c->scal, c->scal + 1, s);
     if (j + 1 < m) launch_scale_copy<T>(w, V + (int64_t)(j + 1) * vs, N, c->scal + 1, 0.0, s);
     launch_givens(c->H, ldh, j, c->cs, c->sn, c->gv, c->scal + 2, s);
+    prof_stop(c, HELM6_PH_ORTHO, e);
     CK(cudaMemcpyAsync(c->pinned, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (c->prof_on) prof_flush(c);
     est = c->pinned[0];
     if (st) {
       st->iters++;
@@ -424,6 +484,7 @@ void helm6_destroy(helm6_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
@@ -611,6 +672,39 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
   S->status = status;
   S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
+}
+
+int helm6_profile_enable(helm6_ctx* c, int enable) {
+  if (!c) return HELM6_ERR_INVALID;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  prof_flush(c);
+  if (c->ev_all.empty()) {
+    for (int i = 0; i < 512; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      c->ev_all.push_back(e);
+      c->ev_pool.push_back(e);
+    }
+  }
+  c->prof_on = enable != 0;
+  for (int i = 0; i < HELM6_NPHASE; ++i) {
+    c->prof_count[i] = 0;
+    c->prof_ms[i] = 0.0;
+  }
+  c->prof_l0 = launch_total();
+  return HELM6_OK;
+}
+
+int helm6_profile_read(helm6_ctx* c, helm6_profile* out) {
+  if (!c || !out) return HELM6_ERR_INVALID;
+  CK(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  out->launches = launch_total() - c->prof_l0;
+  for (int i = 0; i < HELM6_NPHASE; ++i) {
+    out->count[i] = c->prof_count[i];
+    out->ms[i] = c->prof_ms[i];
+  }
+  return HELM6_OK;
 }
 
 int helm6_rhs_gaussians(helm6_ctx* c, int nsrc, const double* centers, const helm6_c64* amps, double sigma,

@@ -154,4 +154,8 @@ void launch_set_complex(double* p, double re, double im, cudaStream_t s);
 
 int device_sm_count();
 
+// Kernels launched by the library so far (process-wide counter, for measurement).
+void note_launch(int n = 1);
+long long launch_total();
+
 }  // namespace helm6

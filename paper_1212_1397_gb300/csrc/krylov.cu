@@ -2,6 +2,8 @@
 // norms, linear combinations, precision conversions, and the FP64 Givens least-squares
 // update of GMRES, all on the device.  Dot products accumulate per thread in the vector
 // precision and combine block partials in FP64.
+#include <atomic>
+
 #include "helm6_internal.h"
 
 namespace helm6 {
@@ -294,6 +296,10 @@ int grid_for(int64_t n, int bs) {
 
 }  // namespace
 
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
+
 int device_sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -304,78 +310,94 @@ int device_sm_count() {
 template <typename T>
 void launch_mdot(const T* V, int64_t vstride, int count, const T* w, int64_t N, double* partial,
                  int nblocks, cudaStream_t s) {
+  note_launch();
   mdot_kernel<T><<<nblocks, RB, 0, s>>>(V, vstride, count, w, N, partial);
 }
 
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
                         cudaStream_t s) {
+  note_launch();
   reduce_cols_kernel<<<ncols, RB, 0, s>>>(partial, nblocks, ncols, out, accumulate, nullptr);
 }
 
 void launch_reduce_cols_accum(const double* partial, int nblocks, int ncols, double* out,
                               double* accum, cudaStream_t s) {
+  note_launch();
   reduce_cols_kernel<<<ncols, RB, 0, s>>>(partial, nblocks, ncols, out, 0, accum);
 }
 
 template <typename T>
 void launch_update(T* w, const T* V, int64_t vstride, int count, const double* h, int64_t N,
                    cudaStream_t s) {
+  note_launch();
   update_kernel<T><<<grid_for(N, RB), RB, 0, s>>>(w, V, vstride, count, h, N);
 }
 
 template <typename T>
 void launch_sumsq(const T* x, int64_t N, double* partial, int nblocks, cudaStream_t s) {
+  note_launch();
   sumsq_kernel<T><<<nblocks, RB, 0, s>>>(x, N, partial);
 }
 
 template <typename T>
 void launch_scale_copy(const T* x, T* y, int64_t N, const double* inv_dev, double host_scale,
                        cudaStream_t s) {
+  note_launch();
   scale_copy_kernel<T><<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, inv_dev, host_scale);
 }
 
 template <typename TI, typename TO>
 void launch_lincomb(const TI* V, int64_t vstride, int count, const double* y, double scale, TO* out,
                     int64_t N, int accumulate, cudaStream_t s) {
+  note_launch();
   lincomb_kernel<TI, TO><<<grid_for(N, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
 }
 
 template <typename TI, typename TO>
 void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s) {
+  note_launch();
   convert_kernel<TI, TO><<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, scale);
 }
 
 void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cudaStream_t s) {
+  note_launch();
   inter_to_planar_kernel<<<grid_for(N, RB), RB, 0, s>>>((const double2*)zin, out, N);
 }
 
 void launch_planar_to_interleaved(const double* in, double* zout, int64_t N, cudaStream_t s) {
+  note_launch();
   planar_to_inter_kernel<<<grid_for(N, RB), RB, 0, s>>>(in, (double2*)zout, N);
 }
 
 void launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t s) {
+  note_launch();
   reduce_sum_kernel<<<1, RB, 0, s>>>(partial, n, out);
 }
 
 void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g, double* res,
                    cudaStream_t s) {
+  note_launch();
   givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, res);
 }
 
 void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* inv, cudaStream_t s) {
+  note_launch();
   set_subdiag_kernel<<<1, 32, 0, s>>>(H, ldh, j, sumsq, inv);
 }
 
 void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s) {
+  note_launch();
   backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y);
 }
 
 template <typename TI, typename TO>
 void launch_axpy(const TI* x, TO* y, int64_t N, double alpha, cudaStream_t s) {
+  note_launch();
   axpy_kernel<TI, TO><<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, alpha);
 }
 
 void launch_set_complex(double* p, double re, double im, cudaStream_t s) {
+  note_launch();
   set_complex_kernel<<<1, 32, 0, s>>>(p, re, im);
 }
 

@@ -155,6 +155,7 @@ template <typename T>
 void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, int64_t bstride,
                       int nbatch, bool along_x, cudaStream_t s) {
   dim3 grid((ncols + BN - 1) / BN, (m + BM - 1) / BM, nbatch);
+  note_launch();
   if (along_x)
     axis_gemm_kernel<T, true><<<grid, 256, 0, s>>>(A, B, C, m, ncols, ld, bstride);
   else
@@ -166,6 +167,7 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
                  const T* x, T* y, T* cw, int* status, cudaStream_t s) {
   const int64_t lines = (int64_t)g.mx * g.my;
   const int bs = 128;
+  note_launch();
   ztri_kernel<T><<<(unsigned)((lines + bs - 1) / bs), bs, 0, s>>>(g, lamx, lamy, diag0, alpha, x, y,
                                                                   cw, status);
 }

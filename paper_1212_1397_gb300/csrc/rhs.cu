@@ -180,6 +180,7 @@ int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers
   c.mu1h5 = to_pod(mu1 * h5 / 3.0);
 
   const int bs = 256;
+  note_launch();
   rhs_kernel<<<(unsigned)((g.N + bs - 1) / bs), bs, 0, s>>>(g, c, nsrc, mmax, dtab, damps, noise, F);
   cudaFreeAsync(dtab, s);
   cudaFreeAsync(damps, s);

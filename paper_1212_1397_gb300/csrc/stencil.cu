@@ -171,6 +171,7 @@ void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const
   dim3 block(TX, TY);
   dim3 grid((g.mx + TX - 1) / TX, (g.my + TY - 1) / TY, (g.mz + ZCH - 1) / ZCH);
   if (nblk) *nblk = (int)(grid.x * grid.y * grid.z);
+  note_launch();
   if (mode == 0)
     stencil_kernel<T, 0><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
   else

@@ -24,7 +24,11 @@ _FACE_CODE = {"D": DIRICHLET, "N": NEUMANN, "S": SOMMERFELD}
 
 # every symbol declared in include/helm6.h
 EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", "helm6_apply_Pinv",
-           "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string")
+           "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
+           "helm6_profile_enable", "helm6_profile_read")
+
+PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "ortho",
+          "resid64", "other")
 
 
 class C64(C.Structure):
@@ -45,6 +49,16 @@ class Stats(C.Structure):
         return dict(iters=self.iters, outer=self.outer, status=STATUS.get(self.status, self.status),
                     relres=self.relres, t_total_ms=self.t_total_ms,
                     history=list(self.hist[: self.nhist]))
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * len(PHASES)),
+                ("ms", C.c_double * len(PHASES))]
+
+    def to_dict(self):
+        return dict(launches=self.launches,
+                    phases={PHASES[i]: dict(count=self.count[i], ms=self.ms[i])
+                            for i in range(len(PHASES))})
 
 
 _lib = None
@@ -75,6 +89,10 @@ def load(path: str = LIB_PATH):
     lib.helm6_rhs_gaussians.restype = I
     lib.helm6_destroy.argtypes = [P]
     lib.helm6_destroy.restype = None
+    lib.helm6_profile_enable.argtypes = [P, I]
+    lib.helm6_profile_enable.restype = I
+    lib.helm6_profile_read.argtypes = [P, C.POINTER(Profile)]
+    lib.helm6_profile_read.restype = I
     lib.helm6_status_string.argtypes = [I]
     lib.helm6_status_string.restype = C.c_char_p
     _lib = lib
@@ -174,6 +192,15 @@ class Solver:
         d = st.to_dict()
         d["rc"] = rc
         return u, d
+
+    def profile(self, enable=True):
+        """Start (and reset) or stop per-phase event timing inside the library."""
+        _check(self._lib.helm6_profile_enable(self._ctx, int(bool(enable))), "helm6_profile_enable")
+
+    def profile_read(self):
+        p = Profile()
+        _check(self._lib.helm6_profile_read(self._ctx, C.byref(p)), "helm6_profile_read")
+        return p.to_dict()
 
     def rhs_gaussians(self, sources, noise=None, F=None):
         """Compact right side for helm6_inputs.GaussianSources (+ optional noise tensor)."""
