@@ -168,6 +168,35 @@ int helm6_profile_enable(helm6_ctx* ctx, int enable);
 /* Copy the counters accumulated so far into *out (synchronises the stream). */
 int helm6_profile_read(helm6_ctx* ctx, helm6_profile* out);
 
+/* ---- Residual without device allocation (the paper has no counterpart) ----
+ * r = F - A u for the sixth-order operator of helm6_apply_A, and *sumsq = ||r||_2^2, for
+ * callers that cannot call cudaMalloc: code that runs where allocation is not allowed or
+ * not possible -- a custom device allocator or memory pool that must not re-enter
+ * cudaMalloc, an embedding runtime that owns every byte of device memory, a real-time loop
+ * that must never block on the allocator, or a CUDA host callback (which may not make
+ * CUDA calls that allocate).  It takes the problem description instead of a context (a
+ * context allocates workspace), allocates nothing and calls no allocating routine.
+ *
+ * Its only scratch is a file-scope device array of HELM6_NOALLOC_MAX_BLOCKS doubles
+ * (512 KiB) that every GPU which loads the library holds until the process exits.  Sizes
+ * whose stencil grid needs more than HELM6_NOALLOC_MAX_BLOCKS thread blocks --
+ * ceil(mx/32) * ceil(my/8) * ceil(mz/16), about n > 510 for a cube -- are rejected with
+ * HELM6_ERR_INVALID before any device work.  The first call on each device looks up the
+ * array's device address with that device current (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call shares the array and leaves its partial sums
+ * there; each call writes every slot it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU (several streams, or several host threads on one device) race on it
+ * and must be serialised by the caller.
+ *
+ * n, h, k, faces: as helm6_create.  F, u, r: DEVICE complex128 arrays (layout as above),
+ * r must not overlap u.  sumsq: DEVICE pointer to one double.  stream: cudaStream_t or
+ * NULL.  Work is enqueued on the stream; the call returns without synchronising.
+ * Returns OK, INVALID (arguments, or grid too large), UNSUPPORTED (device ordinal >= 64)
+ * or CUDA. */
+#define HELM6_NOALLOC_MAX_BLOCKS 65536
+int helm6_residual_noalloc(int n, double h, helm6_c64 k, const int faces[6], const void* F,
+                           const void* u, void* r, double* sumsq, void* stream);
+
 /* Release the workspace and the context (NULL is allowed).  Synchronises its stream. */
 void helm6_destroy(helm6_ctx* ctx);
 

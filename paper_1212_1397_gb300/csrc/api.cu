@@ -165,8 +165,10 @@ void basis(int n, int lo, int hi, std::vector<double>& V, std::vector<double>& W
   }
 }
 
+}  // namespace
+
 // ---- 27-point weights (Eq. scheme, Eq. 3DDISCS) ----
-void stencil_coefficients(cd k, double h, StencilCoef& c) {
+void helm6::stencil_coefficients(cd k, double h, StencilCoef& c) {
   const cd kh2 = k * k * h * h;
   const cd a = (1.0 + kh2 / 30.0) / 6.0;
   const double b = 1.0 / 30.0;
@@ -218,6 +220,8 @@ void stencil_coefficients(cd k, double h, StencilCoef& c) {
   c.s_lo = lo;
   c.s_hi = hi;
 }
+
+namespace {
 
 // ---- preconditioner: x/y forward transforms, z lines, inverse transforms ----
 // in -> tA (x fwd) -> tB (y fwd) -> tA (z) -> tB (y inv) -> out (x inv); out may alias in.

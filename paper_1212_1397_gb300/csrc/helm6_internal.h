@@ -76,6 +76,10 @@ struct StencilCoef {
   RowWeights s_hi;      // z = top face row, mirrored
 };
 
+// Class weights of the interior rows and the Sommerfeld-like face rows for wavenumber k
+// and grid step h (host, FP64).
+void stencil_coefficients(cd k, double h, StencilCoef& c);
+
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (stream-ordered).  Defined in the .cu files.
 // ---------------------------------------------------------------------------------------

@@ -25,7 +25,7 @@ _FACE_CODE = {"D": DIRICHLET, "N": NEUMANN, "S": SOMMERFELD}
 # every symbol declared in include/helm6.h
 EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", "helm6_apply_Pinv",
            "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
-           "helm6_profile_enable", "helm6_profile_read")
+           "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "ortho",
           "resid64", "other")
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_profile_enable.restype = I
     lib.helm6_profile_read.argtypes = [P, C.POINTER(Profile)]
     lib.helm6_profile_read.restype = I
+    lib.helm6_residual_noalloc.argtypes = [I, D, C64, C.POINTER(C.c_int), P, P, P, P, P]
+    lib.helm6_residual_noalloc.restype = I
     lib.helm6_status_string.argtypes = [I]
     lib.helm6_status_string.restype = C.c_char_p
     _lib = lib
@@ -117,6 +119,25 @@ def _ptr(t):
     if t.dtype != torch.complex128 or not t.is_contiguous():
         raise TypeError("expected a contiguous complex128 tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def residual_noalloc(n, k, faces, F, u, r, sumsq, h=0.0, stream=None):
+    """r = F - A u and sumsq[0] = ||r||^2 through helm6_residual_noalloc (no allocation).
+
+    F, u, r: complex128 CUDA tensors of the grid's shape; sumsq: float64 CUDA tensor of one
+    element.  Returns the library's return code (raises on errors)."""
+    import torch
+    if not (isinstance(sumsq, torch.Tensor) and sumsq.is_cuda and sumsq.dtype == torch.float64):
+        raise TypeError("sumsq must be a float64 CUDA tensor")
+    lib = load()
+    f = (C.c_int * 6)(*[_FACE_CODE[ch] for ch in faces])
+    kk = complex(k)
+    s = None
+    if stream is not None:
+        s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    return _check(lib.helm6_residual_noalloc(int(n), float(h), C64(kk.real, kk.imag), f, _ptr(F),
+                                             _ptr(u), _ptr(r), C.c_void_p(sumsq.data_ptr()), s),
+                  "helm6_residual_noalloc")
 
 
 class Solver:
