@@ -34,6 +34,9 @@ struct helm6_ctx {
   double *Vx64 = nullptr, *Wx64 = nullptr, *Vy64 = nullptr, *Wy64 = nullptr;
   float *Vx32 = nullptr, *Wx32 = nullptr, *Vy32 = nullptr, *Wy32 = nullptr;
   double *lamx = nullptr, *lamy = nullptr;
+  // MIXED: BF16 hi/lo basis tiles for the tensor-core transforms (null: SIMT FP32 path)
+  uint8_t *Wx_tc = nullptr, *Wy_tc = nullptr, *Vx_tc = nullptr, *Vy_tc = nullptr;
+  int* tcerr = nullptr;
   // FP64 vectors (2N doubles each)
   double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
   double *V64 = nullptr, *Z64 = nullptr, *w64 = nullptr, *zt64 = nullptr, *tA64 = nullptr,
@@ -251,7 +254,36 @@ void precond(helm6_ctx* c, const T* in, T* out, T* tA, T* tB, T* cw, const T* Vx
 void precond64(helm6_ctx* c, const double* in, double* out) {
   precond<double>(c, in, out, c->tA64, c->tB64, c->cw64, c->Vx64, c->Wx64, c->Vy64, c->Wy64);
 }
+// Tensor-core path: x forward writes planes x-mode-major ([z][p][y]); y forward contracts
+// the now contiguous y; the z lines walk that order; y inverse writes [z][y][p] back;
+// x inverse restores [z][y][x].  in -> tA -> tB -> tA -> tB -> out.
+void precond_tc(helm6_ctx* c, const float* in, float* out) {
+  const Geom& g = c->g;
+  cudaStream_t s = c->stream;
+  const int terms = c->opts.xform_terms;
+  const int rows_x = 2 * g.mz * g.my, rows_y = 2 * g.mz * g.mx;
+  cudaEvent_t e = prof_start(c);
+  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s);
+  prof_stop(c, HELM6_PH_XFWD, e);
+  e = prof_start(c);
+  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s);
+  prof_stop(c, HELM6_PH_YFWD, e);
+  e = prof_start(c);
+  launch_ztri<float>(g, c->lamx, c->lamy, c->diag0, c->alpha, c->tB32, c->tA32, c->cw32, c->status, s, 1);
+  prof_stop(c, HELM6_PH_ZTRI, e);
+  e = prof_start(c);
+  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s);
+  prof_stop(c, HELM6_PH_YINV, e);
+  e = prof_start(c);
+  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s);
+  prof_stop(c, HELM6_PH_XINV, e);
+}
+
 void precond32(helm6_ctx* c, const float* in, float* out) {
+  if (c->Wx_tc) {
+    precond_tc(c, in, out);
+    return;
+  }
   precond<float>(c, in, out, c->tA32, c->tB32, c->cw32, c->Vx32, c->Wx32, c->Vy32, c->Wy32);
 }
 
@@ -346,11 +378,16 @@ void push_hist(helm6_stats* st, double v) {
   if (st && st->nhist < HELM6_MAX_HIST) st->hist[st->nhist++] = v;
 }
 
+// Device status words: z-line breakdown flag, and the tensor-core kernel's timeout flag
+// (a timed-out bounded wait is reported as a CUDA error).
 int check_status(helm6_ctx* c) {
-  int st = 0;
+  int st = 0, te = 0;
   CK(cudaMemcpyAsync(&c->pinned[4], c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&c->pinned[5], c->tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   std::memcpy(&st, &c->pinned[4], sizeof(int));
+  std::memcpy(&te, &c->pinned[5], sizeof(int));
+  if (te) return HELM6_ERR_CUDA;
   return st;
 }
 
@@ -385,7 +422,10 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
     if (st) st->outer++;
     rc = residual64(c, &beta);
     if (rc) return rc;
-    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+    {
+      const int cs = check_status(c);
+      if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
+    }
   }
 }
 
@@ -416,7 +456,10 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     rc = residual64(c, &beta);
     if (rc) return rc;
     if (st && st->nhist > 0) st->hist[st->nhist - 1] = beta / normF;  // true residual
-    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+    {
+      const int cs = check_status(c);
+      if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
+    }
   }
 }
 
@@ -448,7 +491,10 @@ int solve_sks(helm6_ctx* c, double normF, double tol, int maxit, helm6_stats* st
       st->iters++;
       push_hist(st, beta / normF);
     }
-    if (check_status(c) == HELM6_BREAKDOWN) return HELM6_BREAKDOWN;
+    {
+      const int cs = check_status(c);
+      if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
+    }
   }
 }
 
@@ -588,6 +634,22 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
       (rc = dalloc(c, &c->yv, (size_t)2 * (m + 1))) || (rc = dalloc(c, &c->h2, (size_t)2 * (m + 1))) ||
       (rc = dalloc(c, &c->scal, 8)) || (rc = dalloc(c, &c->status, 1)))
     return fail(rc);
+  if ((rc = dalloc(c, &c->tcerr, 1))) return fail(rc);
+  if (cudaMemset(c->tcerr, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+  if (o.precision == HELM6_MIXED && c->g.mx <= tc_max_axis() && c->g.my <= tc_max_axis()) {
+    if (tc_configure() != HELM6_OK) return fail(HELM6_ERR_CUDA);
+    std::vector<uint8_t> t;
+    auto upt = [&](uint8_t** d, const std::vector<double>& B, int m) -> int {
+      tc_prepare_basis(B, m, m, t);
+      int r2 = dalloc(c, d, t.size());
+      if (r2) return r2;
+      return cudaMemcpy(*d, t.data(), t.size(), cudaMemcpyHostToDevice) == cudaSuccess ? (int)HELM6_OK
+                                                                                      : (int)HELM6_ERR_CUDA;
+    };
+    if ((rc = upt(&c->Wx_tc, Wx, c->g.mx)) || (rc = upt(&c->Vx_tc, Vx, c->g.mx)) ||
+        (rc = upt(&c->Wy_tc, Wy, c->g.my)) || (rc = upt(&c->Vy_tc, Vy, c->g.my)))
+      return fail(rc);
+  }
   if (cudaMallocHost((void**)&c->pinned, 16 * sizeof(double)) != cudaSuccess) return fail(HELM6_ERR_NOMEM);
   if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
@@ -625,6 +687,7 @@ int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
   cudaStream_t s = c->stream;
   const int64_t N = c->g.N;
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
   launch_interleaved_to_planar((const double*)x, c->R64, N, s);
   if (c->opts.precision == HELM6_FP64) {
     precond64(c, c->R64, c->E64);
@@ -636,7 +699,7 @@ int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
   launch_planar_to_interleaved(c->E64, (double*)y, N, s);
   CK(cudaGetLastError());
   const int st = check_status(c);
-  return st == HELM6_BREAKDOWN ? HELM6_BREAKDOWN : HELM6_OK;
+  return (st == HELM6_BREAKDOWN || st < 0) ? st : HELM6_OK;
 }
 
 int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, int maxit, helm6_stats* st) {
@@ -649,6 +712,7 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
   cudaStream_t s = c->stream;
   const int64_t N = c->g.N;
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
   launch_interleaved_to_planar((const double*)F, c->F64, N, s);
   double normF = 0;
   int rc = norm2<double>(c, c->F64, &normF);

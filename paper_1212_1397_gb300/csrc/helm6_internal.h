@@ -102,11 +102,24 @@ template <typename T>
 void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, int64_t bstride,
                       int nbatch, bool along_x, cudaStream_t s);
 
+// Tensor-core (tcgen05) BF16-split transform along the contiguous axis of each row:
+// out(row, p) = sum_k in(row, k) B(p, k), rows of length K, M_total rows, P <= tc_max_axis().
+// W: tc_prepare_basis(B).  transposed = 0: out[row*P + p]; 1: out[(row/R)*R*P + p*R + row%R].
+// terms: 1 (hi*hi), 2 (+ lo*hi), 3 (+ hi*lo).  *err is set if a bounded wait timed out.
+int tc_npad(int P);
+int tc_nk(int K);
+int tc_max_axis();
+int tc_configure();
+void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out);
+void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
+                     int transposed, int R, int* err, cudaStream_t s);
+
 // Tridiagonal solve along z for every (x, y) mode pair, Thomas algorithm started at the
-// Sommerfeld-like end (if any).  x: input (destroyed), y: output, cw: scratch of 2N T.
+// Sommerfeld-like end (if any).  x: input, y: output (may alias x), cw: scratch of 2N T.
+// xmajor: planes stored x-mode-major (p*my + q) rather than y-major (q*mx + p).
 template <typename T>
 void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha,
-                 const T* x, T* y, T* cw, int* status, cudaStream_t s);
+                 const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor = 0);
 
 // BLAS-1 style kernels on planar complex vectors of N points.
 template <typename T>

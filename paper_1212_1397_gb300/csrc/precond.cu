@@ -88,14 +88,17 @@ __global__ void __launch_bounds__(256)
 //   Neumann / Sommerfeld-like end (beta = 1), d_l = -2 + k^2h^2 + sigma (+ 2ikh at a
 //   Sommerfeld-like end).  Elimination starts at the Sommerfeld-like end when only the top
 //   face is one (there the pivots keep a positive imaginary part).
+//   xmajor: the plane is stored x-mode-major (index p*my + q, the layout the tensor-core
+//   transforms produce) instead of y-major (q*mx + p).
 template <typename T>
 __global__ void ztri_kernel(Geom g, const double* __restrict__ lamx, const double* __restrict__ lamy,
                             c64d diag0, c64d alpha, const T* __restrict__ x, T* __restrict__ y,
-                            T* __restrict__ cw, int* status) {
+                            T* __restrict__ cw, int* status, int xmajor) {
   const int64_t plane = (int64_t)g.mx * g.my;
   const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pq >= plane) return;
-  const int p = (int)(pq % g.mx), q = (int)(pq / g.mx);
+  const int p = xmajor ? (int)(pq / g.my) : (int)(pq % g.mx);
+  const int q = xmajor ? (int)(pq % g.my) : (int)(pq / g.mx);
   const double sig = lamx[p] + lamy[q];
   const int m = g.mz;
   const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
@@ -164,12 +167,12 @@ void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, in
 
 template <typename T>
 void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha,
-                 const T* x, T* y, T* cw, int* status, cudaStream_t s) {
+                 const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor) {
   const int64_t lines = (int64_t)g.mx * g.my;
   const int bs = 128;
   note_launch();
   ztri_kernel<T><<<(unsigned)((lines + bs - 1) / bs), bs, 0, s>>>(g, lamx, lamy, diag0, alpha, x, y,
-                                                                  cw, status);
+                                                                  cw, status, xmajor);
 }
 
 template void launch_axis_gemm<float>(const float*, const float*, float*, int, int, int, int64_t, int,
@@ -177,8 +180,8 @@ template void launch_axis_gemm<float>(const float*, const float*, float*, int, i
 template void launch_axis_gemm<double>(const double*, const double*, double*, int, int, int, int64_t,
                                        int, bool, cudaStream_t);
 template void launch_ztri<float>(const Geom&, const double*, const double*, c64d, c64d, const float*,
-                                 float*, float*, int*, cudaStream_t);
+                                 float*, float*, int*, cudaStream_t, int);
 template void launch_ztri<double>(const Geom&, const double*, const double*, c64d, c64d,
-                                  const double*, double*, double*, int*, cudaStream_t);
+                                  const double*, double*, double*, int*, cudaStream_t, int);
 
 }  // namespace helm6
