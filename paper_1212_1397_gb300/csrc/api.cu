@@ -29,6 +29,12 @@ struct helm6_ctx {
   int mrest = 30;
   int nred = 0;        // blocks of the reduction kernels
   int nsten = 0;       // blocks of the stencil kernel (partials of its fused norm)
+  int ncgs = 0;        // blocks of the Gram-Schmidt update kernel
+  int ndot = 0;        // blocks of the Gram-Schmidt reduction kernel
+  double *Hr = nullptr, *Tm = nullptr, *red = nullptr, *coefv = nullptr, *qv = nullptr;
+  int* brk = nullptr;
+  double* u64 = nullptr;
+  float* u32 = nullptr;
   double last_beta = 0;  // ||F - A U|| after the last FP64 residual
   // preconditioner tables (device): V, W = V^{-1} row-major m x m, eigenvalues
   double *Vx64 = nullptr, *Wx64 = nullptr, *Vy64 = nullptr, *Wy64 = nullptr;
@@ -312,59 +318,66 @@ int residual64(helm6_ctx* c, double* beta) {
   return HELM6_OK;
 }
 
-// One Arnoldi cycle (CGS2 orthogonalisation, FP64 Givens) on V[0] = r/beta.  Stops at
-// m steps, when the estimate |g_{j+1}| <= abs_tol, or after maxsteps.  On return y holds
-// the least-squares coefficients of the steps taken (*jused).
+void push_hist(helm6_stats* st, double v);
+
+// One Arnoldi cycle with delayed classical Gram-Schmidt.  On entry u holds the starting
+// residual (any scale; g_0 = ||u||).  Step j applies the preconditioner and the operator
+// to u_j, reduces V^H u_j, V^H w, ||u_j||^2 and u_j^H w in one pass, completes column j-1
+// of the Hessenberg matrix (residual estimate |g_j|) and forms column j on the device, and
+// writes v_j and u_{j+1} in one update pass.  The cycle ends at m columns (a last reduction
+// of u_m completes column m-1), when the estimate of the last completed column is
+// <= abs_tol, at a breakdown, or after maxsteps operator applications.  On return y holds
+// the least-squares coefficients of its *kout columns and *beta = ||u_0||.
 template <typename T>
-int arnoldi(helm6_ctx* c, T* V, T* Z, T* w, T* zt, int m, double beta, double abs_tol, int maxsteps,
-            bool flexible, void (*prec)(helm6_ctx*, const T*, T*), const StencilCoef& coef, int* jused,
-            double* est_out, helm6_stats* st) {
+int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, int maxsteps, bool flexible,
+            void (*prec)(helm6_ctx*, const T*, T*), const StencilCoef& coef, int* kout, double* beta,
+            helm6_stats* st) {
   cudaStream_t s = c->stream;
   const int64_t N = c->g.N, vs = 2 * N;
   const int ldh = c->mrest + 1;
   CK(cudaMemsetAsync(c->H, 0, sizeof(double) * 2 * ldh * c->mrest, s));
+  CK(cudaMemsetAsync(c->Hr, 0, sizeof(double) * 2 * ldh * c->mrest, s));
   CK(cudaMemsetAsync(c->gv, 0, sizeof(double) * 2 * ldh, s));
-  launch_set_complex(c->gv, beta, 0.0, s);
-  int j = 0;
-  double est = beta;
-  for (j = 0; j < m && j < maxsteps; ++j) {
-    T* vj = V + (int64_t)j * vs;
-    T* zj = flexible ? Z + (int64_t)j * vs : zt;
-    prec(c, vj, zj);
+  if (flexible) CK(cudaMemsetAsync(c->Tm, 0, sizeof(double) * 2 * c->mrest * c->mrest, s));
+  int k = 0, applied = 0;
+  *beta = 0.0;
+  for (int j = 0;; ++j) {
+    const bool full = (j < m) && (applied < maxsteps);
+    if (full) {
+      T* zj = flexible ? Z + (int64_t)j * vs : zt;
+      prec(c, u, zj);
+      cudaEvent_t e = prof_start(c);
+      launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
+      prof_stop(c, HELM6_PH_STENCIL, e);
+      ++applied;
+    }
     cudaEvent_t e = prof_start(c);
-    launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
-    prof_stop(c, HELM6_PH_STENCIL, e);
-    e = prof_start(c);
-    double* Hcol = c->H + 2 * (int64_t)j * ldh;
-    const int cnt = j + 1;
-    launch_mdot<T>(V, vs, cnt, w, N, c->partial, c->nred, s);
-    launch_reduce_cols(c->partial, c->nred, 2 * cnt, Hcol, 0, s);
-    launch_update<T>(w, V, vs, cnt, Hcol, N, s);
-    launch_mdot<T>(V, vs, cnt, w, N, c->partial, c->nred, s);
-    launch_reduce_cols_accum(c->partial, c->nred, 2 * cnt, c->h2, Hcol, s);
-    launch_update<T>(w, V, vs, cnt, c->h2, N, s);
-    launch_sumsq<T>(w, N, c->partial, c->nred, s);
-    launch_reduce_sum(c->partial, c->nred, c->scal, s);
-    launch_set_subdiag(c->H, ldh, j, c->scal, c->scal + 1, s);
-    if (j + 1 < m) launch_scale_copy<T>(w, V + (int64_t)(j + 1) * vs, N, c->scal + 1, 0.0, s);
-    launch_givens(c->H, ldh, j, c->cs, c->sn, c->gv, c->scal + 2, s);
+    launch_dcgs_dot<T>(V, vs, j, u, full ? w : nullptr, N, c->partial, c->ndot, s);
+    launch_reduce_cols(c->partial, c->ndot, 4 * j + 3, c->red, 0, s);
+    launch_dcgs_step(j, full ? 1 : 0, c->red, c->Hr, c->H, ldh, flexible ? c->Tm : nullptr, c->mrest, c->cs, c->sn,
+                     c->gv, c->coefv, c->scal + 2, c->brk, s);
+    if (full) launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
     prof_stop(c, HELM6_PH_ORTHO, e);
     CK(cudaMemcpyAsync(c->pinned, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&c->pinned[6], c->brk, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (c->prof_on) prof_flush(c);
-    est = c->pinned[0];
-    if (st) {
-      st->iters++;
-      if (st->nhist < HELM6_MAX_HIST) st->hist[st->nhist++] = est;  // scaled by caller
+    const double est = c->pinned[0];
+    int brk = 0;
+    std::memcpy(&brk, &c->pinned[6], sizeof(int));
+    if (j == 0) {
+      *beta = est;
+      if (brk || !std::isfinite(est)) break;
+    } else {
+      k = j;
+      if (st) st->iters++;
+      push_hist(st, est);  // rescaled by the caller
+      if (!(est > abs_tol) || !std::isfinite(est) || brk) break;
     }
-    if (!(est > abs_tol) || !std::isfinite(est)) {
-      ++j;
-      break;
-    }
+    if (!full) break;
   }
-  *jused = j;
-  *est_out = est;
-  launch_backsolve(c->H, ldh, j, c->gv, c->yv, s);
+  *kout = k;
+  if (k > 0) launch_backsolve(c->H, ldh, k, c->gv, c->yv, s);
   CK(cudaGetLastError());
   return HELM6_OK;
 }
@@ -403,21 +416,24 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
     if (!std::isfinite(beta)) return HELM6_NONFINITE;
     if (beta <= tol * normF) return HELM6_OK;
     if (iters >= maxit) return HELM6_NOT_CONVERGED;
-    launch_scale_copy<double>(c->R64, c->V64, c->g.N, nullptr, 1.0 / beta, c->stream);
-    int j = 0;
-    double est = 0;
+    launch_scale_copy<double>(c->R64, c->u64, c->g.N, nullptr, 1.0, c->stream);
+    int k = 0;
+    double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    rc = arnoldi<double>(c, c->V64, c->Z64, c->w64, c->zt64, m, beta, tol * normF, maxit - iters, flex,
-                         precond64, c->coef, &j, &est, st);
+    rc = arnoldi<double>(c, c->V64, c->Z64, c->u64, c->w64, c->zt64, m, tol * normF, maxit - iters, flex, precond64,
+                         c->coef, &k, &b0, st);
     if (rc) return rc;
     fix_hist(st, h0, 1.0 / normF);
-    iters += j;
-    if (flex) {
-      launch_lincomb<double, double>(c->Z64, 2 * c->g.N, j, c->yv, 1.0, c->U64, c->g.N, 1, c->stream);
-    } else {
-      launch_lincomb<double, double>(c->V64, 2 * c->g.N, j, c->yv, 1.0, c->E64, c->g.N, 0, c->stream);
-      precond64(c, c->E64, c->E64);
-      launch_axpy<double, double>(c->E64, c->U64, c->g.N, 1.0, c->stream);
+    iters += k;
+    if (k > 0) {
+      if (flex) {
+        launch_tri_mul(c->Tm, c->mrest, k, c->yv, c->qv, c->stream);
+        launch_lincomb<double, double>(c->Z64, 2 * c->g.N, k, c->qv, 1.0, c->U64, c->g.N, 1, c->stream);
+      } else {
+        launch_lincomb<double, double>(c->V64, 2 * c->g.N, k, c->yv, 1.0, c->E64, c->g.N, 0, c->stream);
+        precond64(c, c->E64, c->E64);
+        launch_axpy<double, double>(c->E64, c->U64, c->g.N, 1.0, c->stream);
+      }
     }
     if (st) st->outer++;
     rc = residual64(c, &beta);
@@ -441,17 +457,20 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     if (!std::isfinite(beta)) return HELM6_NONFINITE;
     if (beta <= tol * normF) return HELM6_OK;
     if (iters >= maxit) return HELM6_NOT_CONVERGED;
-    launch_convert<double, float>(c->R64, c->V32, c->g.N, 1.0 / beta, c->stream);
+    launch_convert<double, float>(c->R64, c->u32, c->g.N, 1.0 / beta, c->stream);
     const double itol = std::max(inner, 0.3 * tol * normF / beta);
-    int j = 0;
-    double est = 0;
+    int k = 0;
+    double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    rc = arnoldi<float>(c, c->V32, c->Z32, c->w32, c->zt32, m, 1.0, itol, maxit - iters, true, precond32,
-                        c->coef, &j, &est, st);
+    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true, precond32, c->coef,
+                        &k, &b0, st);
     if (rc) return rc;
     fix_hist(st, h0, beta / normF);
-    iters += j;
-    launch_lincomb<float, double>(c->Z32, 2 * c->g.N, j, c->yv, beta, c->U64, c->g.N, 1, c->stream);
+    iters += k;
+    if (k > 0) {
+      launch_tri_mul(c->Tm, c->mrest, k, c->yv, c->qv, c->stream);
+      launch_lincomb<float, double>(c->Z32, 2 * c->g.N, k, c->qv, beta, c->U64, c->g.N, 1, c->stream);
+    }
     if (st) st->outer++;
     rc = residual64(c, &beta);
     if (rc) return rc;
@@ -614,12 +633,15 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     const bool krylov = o.method != HELM6_SKS;
     if (krylov && (rc = dalloc(c, &c->V64, v * (m + 1)))) return fail(rc);
     if (needZ && (rc = dalloc(c, &c->Z64, v * m))) return fail(rc);
+    if (krylov && (rc = dalloc(c, &c->u64, v))) return fail(rc);
     if ((rc = dalloc(c, &c->w64, v)) || (rc = dalloc(c, &c->zt64, v)) || (rc = dalloc(c, &c->tA64, v)) ||
         (rc = dalloc(c, &c->tB64, v)) || (rc = dalloc(c, &c->cw64, v)))
       return fail(rc);
   } else {
     const bool krylov = o.method != HELM6_SKS;
-    if (krylov && ((rc = dalloc(c, &c->V32, v * (m + 1))) || (rc = dalloc(c, &c->Z32, v * m)))) return fail(rc);
+    if (krylov && ((rc = dalloc(c, &c->V32, v * (m + 1))) || (rc = dalloc(c, &c->Z32, v * m)) ||
+                   (rc = dalloc(c, &c->u32, v))))
+      return fail(rc);
     if ((rc = dalloc(c, &c->w32, v)) || (rc = dalloc(c, &c->zt32, v)) || (rc = dalloc(c, &c->tA32, v)) ||
         (rc = dalloc(c, &c->tB32, v)) || (rc = dalloc(c, &c->cw32, v)))
       return fail(rc);
@@ -628,7 +650,14 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   }
   c->nred = std::max(1, device_sm_count() * 4);
   c->nsten = stencil_blocks(c->g);
-  if ((rc = dalloc(c, &c->partial, (size_t)c->nred * 2 * (m + 1))) || (rc = dalloc(c, &c->spart, (size_t)c->nsten)) ||
+  c->ncgs = (o.precision == HELM6_FP64) ? cgs_blocks<double>(N) : cgs_blocks<float>(N);
+  c->ndot = dot_blocks();
+  const int npart = std::max(c->nred, std::max(c->ncgs, c->ndot));
+  const size_t ncol = (size_t)4 * (m + 1) + 3;
+  if ((rc = dalloc(c, &c->partial, (size_t)npart * ncol)) || (rc = dalloc(c, &c->red, ncol)) ||
+      (rc = dalloc(c, &c->coefv, ncol)) || (rc = dalloc(c, &c->Hr, (size_t)2 * (m + 1) * m)) ||
+      (rc = dalloc(c, &c->Tm, (size_t)2 * m * m)) || (rc = dalloc(c, &c->qv, (size_t)2 * (m + 1))) ||
+      (rc = dalloc(c, &c->brk, 1)) || (rc = dalloc(c, &c->spart, (size_t)c->nsten)) ||
       (rc = dalloc(c, &c->H, (size_t)2 * (m + 1) * m)) || (rc = dalloc(c, &c->cs, (size_t)2 * (m + 1))) ||
       (rc = dalloc(c, &c->sn, (size_t)2 * (m + 1))) || (rc = dalloc(c, &c->gv, (size_t)2 * (m + 1))) ||
       (rc = dalloc(c, &c->yv, (size_t)2 * (m + 1))) || (rc = dalloc(c, &c->h2, (size_t)2 * (m + 1))) ||

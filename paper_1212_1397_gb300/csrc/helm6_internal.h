@@ -122,14 +122,8 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
                  const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor = 0);
 
 // BLAS-1 style kernels on planar complex vectors of N points.
-template <typename T>
-void launch_mdot(const T* V, int64_t vstride, int count, const T* w, int64_t N, double* partial,
-                 int nblocks, cudaStream_t s);  // partial[b][i] (complex double) = sum conj(V_i) w
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
                         cudaStream_t s);  // out[i] (+)= sum_b partial[b][i], complex double
-template <typename T>
-void launch_update(T* w, const T* V, int64_t vstride, int count, const double* h, int64_t N,
-                   cudaStream_t s);  // w -= sum_i V_i h_i
 template <typename T>
 void launch_sumsq(const T* x, int64_t N, double* partial, int nblocks, cudaStream_t s);
 template <typename T>
@@ -159,15 +153,30 @@ void launch_backsolve(const double* H, int ldh, int j, const double* g, double* 
 int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
                   double sigma, const double* noise, double* F, cudaStream_t s);
 
-// Reduce partial columns into out and also add them into accum.
-void launch_reduce_cols_accum(const double* partial, int nblocks, int ncols, double* out,
-                              double* accum, cudaStream_t s);
-
 // y += alpha x (planar, 2N reals), mixed input/output precision.
 template <typename TI, typename TO>
 void launch_axpy(const TI* x, TO* y, int64_t N, double alpha, cudaStream_t s);
 // p[0] = re, p[1] = im on the device (stream-ordered).
 void launch_set_complex(double* p, double re, double im, cudaStream_t s);
+
+// Arnoldi by delayed classical Gram-Schmidt (one reduction and one update pass per step):
+//   launch_dcgs_dot:    block partials of V_i^H u, V_i^H w (i < count), ||u||^2, u^H w
+//                       (w may be null: the last step of a cycle has no new vector)
+//   launch_dcgs_step:   FP64 small algebra of step j (see krylov.cu)
+//   launch_dcgs_update: v_out = (u - V s)/alpha,  u = (w - V t - v_out c)/alpha
+//   launch_tri_mul:     q = T y for the flexible solution update
+template <typename T>
+int cgs_blocks(int64_t N);
+int dot_blocks();
+template <typename T>
+void launch_dcgs_dot(const T* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
+                     int nblocks, cudaStream_t s);
+template <typename T>
+void launch_dcgs_update(const T* V, int64_t vs, int count, T* u, const T* w, T* v_out, int64_t N,
+                        const double* coef, int nblocks, cudaStream_t s);
+void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T, int ldt,
+                      double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s);
+void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s);
 
 int device_sm_count();
 

@@ -2,6 +2,7 @@
 // norms, linear combinations, precision conversions, and the FP64 Givens least-squares
 // update of GMRES, all on the device.  Dot products accumulate per thread in the vector
 // precision and combine block partials in FP64.
+#include <algorithm>
 #include <atomic>
 
 #include "helm6_internal.h"
@@ -11,7 +12,6 @@ namespace helm6 {
 namespace {
 
 constexpr int RB = 256;  // threads per block of the reduction kernels
-constexpr int CH = 8;    // basis vectors per pass of the multi-dot kernel
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -30,45 +30,6 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;
 }
 
-// partial[b][2*i + {0,1}] = sum over this block's points of conj(V_i) * w
-template <typename T>
-__global__ void __launch_bounds__(RB) mdot_kernel(const T* __restrict__ V, int64_t vstride, int count,
-                                                  const T* __restrict__ w, int64_t N,
-                                                  double* __restrict__ partial) {
-  __shared__ double sh[RB / 32];
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (int base = 0; base < count; base += CH) {
-    T ar[CH], ai[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) ar[c] = ai[c] = T(0);
-    const int nc = min(CH, count - base);
-    for (int64_t idx = i0; idx < N; idx += stride) {
-      const T wr = w[idx], wi = w[N + idx];
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        if (c < nc) {
-          const T* v = V + (int64_t)(base + c) * vstride;
-          const T vr = v[idx], vi = v[N + idx];
-          ar[c] = fma(vr, wr, fma(vi, wi, ar[c]));
-          ai[c] = fma(vr, wi, fma(-vi, wr, ai[c]));
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      if (c < nc) {
-        const double sr = block_sum((double)ar[c], sh);
-        const double si = block_sum((double)ai[c], sh);
-        if (threadIdx.x == 0) {
-          partial[(int64_t)blockIdx.x * 2 * count + 2 * (base + c)] = sr;
-          partial[(int64_t)blockIdx.x * 2 * count + 2 * (base + c) + 1] = si;
-        }
-      }
-    }
-  }
-}
-
 // out[c] (+)= sum_b partial[b*ncols + c]; also adds into accum[c] when accum != nullptr.
 __global__ void reduce_cols_kernel(const double* __restrict__ partial, int nblocks, int ncols,
                                    double* __restrict__ out, int accumulate, double* accum) {
@@ -80,30 +41,6 @@ __global__ void reduce_cols_kernel(const double* __restrict__ partial, int nbloc
   if (threadIdx.x == 0) {
     out[c] = accumulate ? out[c] + v : v;
     if (accum) accum[c] += v;
-  }
-}
-
-// w -= sum_i V_i h_i   (h complex double, count <= 64)
-template <typename T>
-__global__ void update_kernel(T* __restrict__ w, const T* __restrict__ V, int64_t vstride, int count,
-                              const double* __restrict__ h, int64_t N) {
-  __shared__ T hr[64], hi[64];
-  if (threadIdx.x < count) {
-    hr[threadIdx.x] = (T)h[2 * threadIdx.x];
-    hi[threadIdx.x] = (T)h[2 * threadIdx.x + 1];
-  }
-  __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
-    T wr = w[idx], wi = w[N + idx];
-    for (int c = 0; c < count; ++c) {
-      const T* v = V + (int64_t)c * vstride;
-      const T vr = v[idx], vi = v[N + idx];
-      wr = fma(-vr, hr[c], fma(vi, hi[c], wr));
-      wi = fma(-vr, hi[c], fma(-vi, hr[c], wi));
-    }
-    w[idx] = wr;
-    w[N + idx] = wi;
   }
 }
 
@@ -192,6 +129,211 @@ __global__ void reduce_sum_kernel(const double* __restrict__ partial, int n, dou
   if (threadIdx.x == 0) *out = v;
 }
 
+// ---- Arnoldi with delayed classical Gram-Schmidt (one reduction + one update per step) ----
+// Vector traits for 2-point loads of a planar field.
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+  using t = float2;
+};
+template <>
+struct V2<double> {
+  using t = double2;
+};
+
+constexpr int CHD = 8;  // basis vectors per chunk of the reduction pass
+
+// Loads of PTS consecutive points (PTS = 2: one 2-vector; PTS = 1: a scalar).
+template <typename T, int PTS>
+__device__ __forceinline__ void ldp(const T* p, int64_t q, T* o) {
+  if (PTS == 2) {
+    const typename V2<T>::t v = ((const typename V2<T>::t*)p)[q];
+    o[0] = v.x;
+    o[1] = v.y;
+  } else {
+    o[0] = p[q];
+  }
+}
+
+// One reduction pass over the basis V_0..V_{count-1}, u and (optionally) w.  Per block:
+//   s_i = sum conj(V_i) u,  t_i = sum conj(V_i) w  (i < count),
+//   a = sum |u|^2,  b = sum conj(u) w.
+// Partial layout per block (ncol = 4 count + 3 doubles): s (2 count), t (2 count), a, b (2).
+// Chunks of CHD basis vectors: the loads of a point's chunk are issued together; at the end
+// of a chunk every accumulator is reduced by warp shuffles and one shared-memory exchange
+// (a single barrier), so the per-block epilogue stays short.
+template <typename T, int PTS>
+__global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, int64_t vs, int count,
+                                                      const T* __restrict__ u, const T* __restrict__ w,
+                                                      int64_t N, double* __restrict__ partial) {
+  constexpr int NACC = 4 * CHD + 3;
+  __shared__ T sh[RB / 32][NACC];
+  const int ncol = 4 * count + 3;
+  const bool hw = (w != nullptr);
+  const int64_t npts = N / PTS;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double* out = partial + (int64_t)blockIdx.x * ncol;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunk = count > 0 ? (count + CHD - 1) / CHD : 1;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int base = ch * CHD;
+    const int nc = min(CHD, count - base);
+    T acc[NACC];
+#pragma unroll
+    for (int c = 0; c < NACC; ++c) acc[c] = T(0);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
+      T ur[PTS], ui[PTS], wr[PTS], wi[PTS];
+      ldp<T, PTS>(u, q, ur);
+      ldp<T, PTS>(u + N, q, ui);
+#pragma unroll
+      for (int k = 0; k < PTS; ++k) wr[k] = wi[k] = T(0);
+      if (hw) {
+        ldp<T, PTS>(w, q, wr);
+        ldp<T, PTS>(w + N, q, wi);
+      }
+      T vr[CHD][PTS], vi[CHD][PTS];
+#pragma unroll
+      for (int c = 0; c < CHD; ++c) {
+        if (c < nc) {
+          const T* v = V + (int64_t)(base + c) * vs;
+          ldp<T, PTS>(v, q, vr[c]);
+          ldp<T, PTS>(v + N, q, vi[c]);
+        }
+      }
+      if (ch == 0) {
+#pragma unroll
+        for (int k = 0; k < PTS; ++k) {
+          acc[4 * CHD] = fma(ur[k], ur[k], fma(ui[k], ui[k], acc[4 * CHD]));
+          acc[4 * CHD + 1] = fma(ur[k], wr[k], fma(ui[k], wi[k], acc[4 * CHD + 1]));
+          acc[4 * CHD + 2] = fma(ur[k], wi[k], fma(-ui[k], wr[k], acc[4 * CHD + 2]));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CHD; ++c) {
+        if (c < nc) {
+#pragma unroll
+          for (int k = 0; k < PTS; ++k) {
+            acc[4 * c] = fma(vr[c][k], ur[k], fma(vi[c][k], ui[k], acc[4 * c]));
+            acc[4 * c + 1] = fma(vr[c][k], ui[k], fma(-vi[c][k], ur[k], acc[4 * c + 1]));
+            acc[4 * c + 2] = fma(vr[c][k], wr[k], fma(vi[c][k], wi[k], acc[4 * c + 2]));
+            acc[4 * c + 3] = fma(vr[c][k], wi[k], fma(-vi[c][k], wr[k], acc[4 * c + 3]));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NACC; ++c) {
+      T v = acc[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NACC; c += blockDim.x) {
+      double sum = 0.0;
+      for (int ww = 0; ww < RB / 32; ++ww) sum += (double)sh[ww][c];
+      if (c < 4 * CHD) {
+        const int cc = c >> 2, kind = c & 3;
+        if (cc < nc) out[(kind < 2 ? 0 : 2 * count) + 2 * (base + cc) + (kind & 1)] = sum;
+      } else if (ch == 0) {
+        out[4 * count + (c - 4 * CHD)] = sum;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One update pass.  coef (complex double unless noted): s[count], t[count], c, inv (real).
+//   v_new = (u - sum_i V_i s_i) inv          -> written to v_out (the basis slot `count`)
+//   u     = (w - sum_i V_i t_i - v_new c) inv -> written over u (in place)
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(RB) dcgs_update_kernel(const T* __restrict__ V, int64_t vs, int count,
+                                                         T* u, const T* __restrict__ w, T* __restrict__ v_out,
+                                                         int64_t N, const double* __restrict__ coef) {
+  __shared__ T s_r[64], s_i[64], t_r[64], t_i[64];
+  __shared__ T cc[3];
+  using T2 = typename V2<T>::t;
+  for (int c = threadIdx.x; c < count; c += blockDim.x) {
+    s_r[c] = (T)coef[2 * c];
+    s_i[c] = (T)coef[2 * c + 1];
+    t_r[c] = (T)coef[2 * count + 2 * c];
+    t_i[c] = (T)coef[2 * count + 2 * c + 1];
+  }
+  if (threadIdx.x == 0) {
+    cc[0] = (T)coef[4 * count];
+    cc[1] = (T)coef[4 * count + 1];
+    cc[2] = (T)coef[4 * count + 2];
+  }
+  __syncthreads();
+  const T cr = cc[0], ci = cc[1], inv = cc[2];
+  const int64_t npts = VEC ? N / 2 : N;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  auto one = [&](int64_t q) {
+    T ur = u[q], ui = u[N + q];
+    T wr = w[q], wi = w[N + q];
+    for (int c = 0; c < count; ++c) {
+      const T* v = V + (int64_t)c * vs;
+      const T vr = v[q], vi = v[N + q];
+      ur = fma(-vr, s_r[c], fma(vi, s_i[c], ur));
+      ui = fma(-vr, s_i[c], fma(-vi, s_r[c], ui));
+      wr = fma(-vr, t_r[c], fma(vi, t_i[c], wr));
+      wi = fma(-vr, t_i[c], fma(-vi, t_r[c], wi));
+    }
+    const T nr = ur * inv, ni = ui * inv;
+    v_out[q] = nr;
+    v_out[N + q] = ni;
+    wr = fma(-nr, cr, fma(ni, ci, wr));
+    wi = fma(-nr, ci, fma(-ni, cr, wi));
+    u[q] = wr * inv;
+    u[N + q] = wi * inv;
+  };
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
+    if (VEC) {
+      T2 ur = ((const T2*)u)[q], ui = ((const T2*)(u + N))[q];
+      T2 wr = ((const T2*)w)[q], wi = ((const T2*)(w + N))[q];
+      // basis vectors in groups of UB: all loads of a group are issued before its FMAs
+      constexpr int UB = 8;
+      for (int c0 = 0; c0 < count; c0 += UB) {
+        T2 vr[UB], vi[UB];
+#pragma unroll
+        for (int e = 0; e < UB; ++e) {
+          if (c0 + e < count) {
+            const T* v = V + (int64_t)(c0 + e) * vs;
+            vr[e] = ((const T2*)v)[q];
+            vi[e] = ((const T2*)(v + N))[q];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < UB; ++e) {
+          if (c0 + e < count) {
+            const int c = c0 + e;
+            ur.x = fma(-vr[e].x, s_r[c], fma(vi[e].x, s_i[c], ur.x));
+            ui.x = fma(-vr[e].x, s_i[c], fma(-vi[e].x, s_r[c], ui.x));
+            ur.y = fma(-vr[e].y, s_r[c], fma(vi[e].y, s_i[c], ur.y));
+            ui.y = fma(-vr[e].y, s_i[c], fma(-vi[e].y, s_r[c], ui.y));
+            wr.x = fma(-vr[e].x, t_r[c], fma(vi[e].x, t_i[c], wr.x));
+            wi.x = fma(-vr[e].x, t_i[c], fma(-vi[e].x, t_r[c], wi.x));
+            wr.y = fma(-vr[e].y, t_r[c], fma(vi[e].y, t_i[c], wr.y));
+            wi.y = fma(-vr[e].y, t_i[c], fma(-vi[e].y, t_r[c], wi.y));
+          }
+        }
+      }
+      const T2 nr = {ur.x * inv, ur.y * inv}, ni = {ui.x * inv, ui.y * inv};
+      ((T2*)v_out)[q] = nr;
+      ((T2*)(v_out + N))[q] = ni;
+      wr.x = fma(-nr.x, cr, fma(ni.x, ci, wr.x));
+      wi.x = fma(-nr.x, ci, fma(-ni.x, cr, wi.x));
+      wr.y = fma(-nr.y, cr, fma(ni.y, ci, wr.y));
+      wi.y = fma(-nr.y, ci, fma(-ni.y, cr, wi.y));
+      ((T2*)u)[q] = T2{wr.x * inv, wr.y * inv};
+      ((T2*)(u + N))[q] = T2{wi.x * inv, wi.y * inv};
+    } else {
+      one(q);
+    }
+  }
+  if (VEC && (N & 1) && blockIdx.x == 0 && threadIdx.x == 0) one(N - 1);
+}
+
 // ---- GMRES least squares (FP64, one thread) ----
 struct zc {
   double re, im;
@@ -240,6 +382,158 @@ __global__ void givens_kernel(double* H, int ldh, int j, double* cs, double* sn,
   st(g + 2 * (j + 1), zmul(zc{-s.re, s.im}, gj));
   st(g + 2 * j, zc{c * gj.re, c * gj.im});
   *res = zabs(ld(g + 2 * (j + 1)));
+}
+
+// Apply rotations 0..jj-1 to column jj of R (rows 0..jj+1), make rotation jj, update g;
+// *res = |g_{jj+1}|.  Rotation i acts on rows (i, i+1): [c s; -conj(s) c], c real.
+__device__ void givens_column(double* col, int jj, double* cs, double* sn, double* g, double* res) {
+  for (int i = 0; i < jj; ++i) {
+    const zc hi = ld(col + 2 * i), hn = ld(col + 2 * (i + 1));
+    const double c = cs[2 * i];
+    const zc s = ld(sn + 2 * i);
+    const zc t = zadd(zc{c * hi.re, c * hi.im}, zmul(s, hn));
+    const zc u = zadd(zmul(zc{-s.re, s.im}, hi), zc{c * hn.re, c * hn.im});
+    st(col + 2 * i, t);
+    st(col + 2 * (i + 1), u);
+  }
+  const zc a = ld(col + 2 * jj), b = ld(col + 2 * (jj + 1));
+  const double aa = zabs(a), bb = zabs(b);
+  const double den = hypot(aa, bb);
+  double c;
+  zc s;
+  if (den == 0.0) {
+    c = 1.0;
+    s = zc{0.0, 0.0};
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = zc{1.0, 0.0};
+  } else {
+    c = aa / den;
+    s = zmul(zc{a.re / aa, a.im / aa}, zc{b.re / den, -b.im / den});
+  }
+  cs[2 * jj] = c;
+  cs[2 * jj + 1] = 0.0;
+  st(sn + 2 * jj, s);
+  st(col + 2 * jj, zadd(zc{c * a.re, c * a.im}, zmul(s, b)));
+  st(col + 2 * (jj + 1), zc{0.0, 0.0});
+  const zc gj = ld(g + 2 * jj);
+  st(g + 2 * (jj + 1), zmul(zc{-s.re, s.im}, gj));
+  st(g + 2 * jj, zc{c * gj.re, c * gj.im});
+  *res = zabs(ld(g + 2 * (jj + 1)));
+}
+
+// Small FP64 algebra of one delayed Gram-Schmidt Arnoldi step j (one thread).
+// red: reduced sums s_i = V_i^H u_j, t_i = V_i^H w (i < j), a = ||u_j||^2, b = u_j^H w.
+// u_j = V s + alpha v_j with alpha^2 = a - ||s||^2.
+//   * column j-1 of the raw Hessenberg Hr gets += s and subdiagonal alpha; it is copied to R
+//     and rotated (Givens), giving the residual estimate *est = |g_j| (j = 0: g_0 = alpha);
+//   * with w = A M^{-1} u_j (has_w): v_j^H w = (b - s^H t)/alpha = c_j, column j of Hr is
+//     ([t; c_j] - Hr[:, 0..j-1] s)/alpha, and T (z_l = sum_i T[i,l] z~_i) gets column
+//     (e_j - T s)/alpha;
+//   * coef = [s, t, c_j, 1/alpha] for the update pass v_j = (u - V s)/alpha,
+//     u_{j+1} = (w - V t - v_j c_j)/alpha.
+// *brk = 1 when alpha^2 <= 1e-28 a (u_j in the span of the basis: breakdown).
+__global__ void dcgs_step_kernel(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T,
+                                 int ldt, double* cs, double* sn, double* g, double* coef, double* est, int* brk) {
+  // one warp: lane r handles rows r, r + 32, ...; the Givens sweep runs on lane 0
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const double* sv = red;
+  const double* tv = red + 2 * j;
+  const double a = red[4 * j];
+  const zc b = zc{red[4 * j + 1], red[4 * j + 2]};
+  double s2 = 0.0;
+  for (int i = lane; i < j; i += 32) s2 += sv[2 * i] * sv[2 * i] + sv[2 * i + 1] * sv[2 * i + 1];
+  s2 = warp_sum(s2);
+  const double al2 = a - s2;
+  const bool bd = !(al2 > 1e-28 * fmax(a, 1e-300)) || !isfinite(al2);
+  const double al = bd ? 0.0 : sqrt(al2);
+  const double inv = bd ? 0.0 : 1.0 / al;
+  if (lane == 0) *brk = bd ? 1 : 0;
+  if (j >= 1) {
+    double* hc = Hr + 2 * (int64_t)(j - 1) * ldh;
+    double* rc = R + 2 * (int64_t)(j - 1) * ldh;
+    for (int i = lane; i < j; i += 32) {
+      hc[2 * i] += sv[2 * i];
+      hc[2 * i + 1] += sv[2 * i + 1];
+    }
+    if (lane == 0) {
+      hc[2 * j] = al;
+      hc[2 * j + 1] = 0.0;
+    }
+    __syncwarp();
+    for (int r = lane; r <= 2 * j + 1; r += 32) rc[r] = hc[r];
+    __syncwarp();
+    if (lane == 0) givens_column(rc, j - 1, cs, sn, g, est);
+  } else if (lane == 0) {
+    g[0] = al;
+    g[1] = 0.0;
+    *est = al;
+  }
+  for (int i = lane; i < j; i += 32) {
+    coef[2 * i] = sv[2 * i];
+    coef[2 * i + 1] = sv[2 * i + 1];
+    coef[2 * j + 2 * i] = tv[2 * i];
+    coef[2 * j + 2 * i + 1] = tv[2 * i + 1];
+  }
+  if (!has_w || bd) {
+    if (lane == 0) {
+      coef[4 * j] = 0.0;
+      coef[4 * j + 1] = 0.0;
+      coef[4 * j + 2] = inv;
+    }
+    return;
+  }
+  // c_j = (b - s^H t) / alpha
+  double pr = 0.0, pi = 0.0;
+  for (int i = lane; i < j; i += 32) {
+    const zc p = zmul(zc{sv[2 * i], -sv[2 * i + 1]}, ld(tv + 2 * i));
+    pr += p.re;
+    pi += p.im;
+  }
+  pr = warp_sum(pr);
+  pi = warp_sum(pi);
+  const zc cj = zc{(b.re - pr) * inv, (b.im - pi) * inv};
+  // column j: ([t; c_j] - Hr[:, 0..j-1] s) / alpha, rows 0..j
+  double* hj = Hr + 2 * (int64_t)j * ldh;
+  for (int r = lane; r <= j; r += 32) {
+    zc acc = (r < j) ? ld(tv + 2 * r) : cj;
+    for (int i = (r > 0 ? r - 1 : 0); i < j; ++i) {
+      const zc p = zmul(ld(Hr + 2 * ((int64_t)i * ldh + r)), ld(sv + 2 * i));
+      acc.re -= p.re;
+      acc.im -= p.im;
+    }
+    hj[2 * r] = acc.re * inv;
+    hj[2 * r + 1] = acc.im * inv;
+  }
+  // T column j: (e_j - T s) / alpha
+  if (T) {
+    for (int r = lane; r < j; r += 32) {
+      zc acc = zc{0.0, 0.0};
+      for (int i = r; i < j; ++i) acc = zadd(acc, zmul(ld(T + 2 * ((int64_t)i * ldt + r)), ld(sv + 2 * i)));
+      T[2 * ((int64_t)j * ldt + r)] = -acc.re * inv;
+      T[2 * ((int64_t)j * ldt + r) + 1] = -acc.im * inv;
+    }
+    if (lane == 0) {
+      T[2 * ((int64_t)j * ldt + j)] = inv;
+      T[2 * ((int64_t)j * ldt + j) + 1] = 0.0;
+    }
+  }
+  if (lane == 0) {
+    coef[4 * j] = cj.re;
+    coef[4 * j + 1] = cj.im;
+    coef[4 * j + 2] = inv;
+  }
+}
+
+// q = T[0..k-1, 0..k-1] y (T upper triangular, column-major, leading dimension ldt).
+__global__ void tri_mul_kernel(const double* T, int ldt, int k, const double* y, double* q) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int r = 0; r < k; ++r) {
+    zc acc = zc{0.0, 0.0};
+    for (int i = r; i < k; ++i) acc = zadd(acc, zmul(ld(T + 2 * ((int64_t)i * ldt + r)), ld(y + 2 * i)));
+    st(q + 2 * r, acc);
+  }
 }
 
 __global__ void set_subdiag_kernel(double* H, int ldh, int j, const double* sumsq, double* inv) {
@@ -307,30 +601,10 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-template <typename T>
-void launch_mdot(const T* V, int64_t vstride, int count, const T* w, int64_t N, double* partial,
-                 int nblocks, cudaStream_t s) {
-  note_launch();
-  mdot_kernel<T><<<nblocks, RB, 0, s>>>(V, vstride, count, w, N, partial);
-}
-
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
                         cudaStream_t s) {
   note_launch();
   reduce_cols_kernel<<<ncols, RB, 0, s>>>(partial, nblocks, ncols, out, accumulate, nullptr);
-}
-
-void launch_reduce_cols_accum(const double* partial, int nblocks, int ncols, double* out,
-                              double* accum, cudaStream_t s) {
-  note_launch();
-  reduce_cols_kernel<<<ncols, RB, 0, s>>>(partial, nblocks, ncols, out, 0, accum);
-}
-
-template <typename T>
-void launch_update(T* w, const T* V, int64_t vstride, int count, const double* h, int64_t N,
-                   cudaStream_t s) {
-  note_launch();
-  update_kernel<T><<<grid_for(N, RB), RB, 0, s>>>(w, V, vstride, count, h, N);
 }
 
 template <typename T>
@@ -380,6 +654,17 @@ void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g,
   givens_kernel<<<1, 32, 0, s>>>(H, ldh, j, cs, sn, g, res);
 }
 
+void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T, int ldt,
+                      double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s) {
+  note_launch();
+  dcgs_step_kernel<<<1, 32, 0, s>>>(j, has_w, red, Hr, R, ldh, T, ldt, cs, sn, g, coef, est, brk);
+}
+
+void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s) {
+  note_launch();
+  tri_mul_kernel<<<1, 32, 0, s>>>(T, ldt, k, y, q);
+}
+
 void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* inv, cudaStream_t s) {
   note_launch();
   set_subdiag_kernel<<<1, 32, 0, s>>>(H, ldh, j, sumsq, inv);
@@ -404,10 +689,50 @@ void launch_set_complex(double* p, double re, double im, cudaStream_t s) {
 template void launch_axpy<float, double>(const float*, double*, int64_t, double, cudaStream_t);
 template void launch_axpy<double, double>(const double*, double*, int64_t, double, cudaStream_t);
 
+template <typename T>
+int cgs_blocks(int64_t N) {
+  static int sms = 0;
+  if (!sms) sms = device_sm_count();
+  int64_t g = (N + RB - 1) / RB;
+  const int64_t cap = (int64_t)sms * 8;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+template <typename T>
+void launch_dcgs_dot(const T* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
+                     int nblocks, cudaStream_t s) {
+  note_launch();
+  if ((vs & 1) == 0 && (N & 1) == 0)
+    dcgs_dot_kernel<T, 2><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial);
+  else
+    dcgs_dot_kernel<T, 1><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial);
+}
+
+// Blocks of the reduction pass: two per SM (its per-block epilogue favours few blocks).
+int dot_blocks() { return 2 * device_sm_count(); }
+
+template <typename T>
+void launch_dcgs_update(const T* V, int64_t vs, int count, T* u, const T* w, T* v_out, int64_t N,
+                        const double* coef, int nblocks, cudaStream_t s) {
+  note_launch();
+  if ((vs & 1) == 0 && (N & 1) == 0)
+    dcgs_update_kernel<T, true><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef);
+  else
+    dcgs_update_kernel<T, false><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef);
+}
+
+template int cgs_blocks<float>(int64_t);
+template int cgs_blocks<double>(int64_t);
+template void launch_dcgs_dot<float>(const float*, int64_t, int, const float*, const float*, int64_t, double*, int,
+                                     cudaStream_t);
+template void launch_dcgs_dot<double>(const double*, int64_t, int, const double*, const double*, int64_t, double*,
+                                      int, cudaStream_t);
+template void launch_dcgs_update<float>(const float*, int64_t, int, float*, const float*, float*, int64_t,
+                                        const double*, int, cudaStream_t);
+template void launch_dcgs_update<double>(const double*, int64_t, int, double*, const double*, double*, int64_t,
+                                         const double*, int, cudaStream_t);
+
 #define INST_T(T)                                                                              \
-  template void launch_mdot<T>(const T*, int64_t, int, const T*, int64_t, double*, int,         \
-                               cudaStream_t);                                                   \
-  template void launch_update<T>(T*, const T*, int64_t, int, const double*, int64_t, cudaStream_t); \
   template void launch_sumsq<T>(const T*, int64_t, double*, int, cudaStream_t);                  \
   template void launch_scale_copy<T>(const T*, T*, int64_t, const double*, double, cudaStream_t);
 INST_T(float)

@@ -109,45 +109,77 @@ __global__ void ztri_kernel(Geom g, const double* __restrict__ lamx, const doubl
   const cpx<T> al = cast<T>(alpha);
   const int64_t N = g.N;
 
+  // Both sweeps read 8 steps of the line into registers before using them, so that each
+  // thread keeps several independent loads in flight.
+  constexpr int U = 8;
   cpx<T> cprev = mk(T(0), T(0)), yprev = mk(T(0), T(0));
   bool bad = false;
-  for (int r = 0; r < m; ++r) {
-    const int l = rev ? (m - 1 - r) : r;
-    // coefficients in elimination order: sub = towards the previous row, sup = next
-    T a_l = (l == m - 1) ? a_hi : T(1);
-    T c_l = (l == 0) ? c_lo : T(1);
-    if (l == 0) a_l = T(0);
-    if (l == m - 1) c_l = T(0);
-    const T sub = rev ? c_l : a_l;
-    const T sup = rev ? a_l : c_l;
-    cpx<T> d = dint;
-    if (l == 0 && lo_s) d = d + al;
-    if (l == m - 1 && hi_s) d = d + al;
-    const cpx<T> den = d - sub * cprev;
-    const T n2 = den.re * den.re + den.im * den.im;
-    if (!(n2 > T(0))) bad = true;
-    const T inv = T(1) / n2;
-    const cpx<T> rinv = mk(den.re * inv, -den.im * inv);
-    const int64_t idx = (int64_t)l * plane + pq;
-    const cpx<T> xv = mk(x[idx], x[N + idx]);
-    const cpx<T> cp = sup * rinv;
-    const cpx<T> yp = (xv - sub * yprev) * rinv;
-    cw[idx] = cp.re;
-    cw[N + idx] = cp.im;
-    y[idx] = yp.re;
-    y[N + idx] = yp.im;
-    cprev = cp;
-    yprev = yp;
+  for (int r0 = 0; r0 < m; r0 += U) {
+    cpx<T> xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r < m) {
+        const int l = rev ? (m - 1 - r) : r;
+        const int64_t idx = (int64_t)l * plane + pq;
+        xv[u] = mk(x[idx], x[N + idx]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r >= m) break;
+      const int l = rev ? (m - 1 - r) : r;
+      // coefficients in elimination order: sub = towards the previous row, sup = next
+      T a_l = (l == m - 1) ? a_hi : T(1);
+      T c_l = (l == 0) ? c_lo : T(1);
+      if (l == 0) a_l = T(0);
+      if (l == m - 1) c_l = T(0);
+      const T sub = rev ? c_l : a_l;
+      const T sup = rev ? a_l : c_l;
+      cpx<T> d = dint;
+      if (l == 0 && lo_s) d = d + al;
+      if (l == m - 1 && hi_s) d = d + al;
+      const cpx<T> den = d - sub * cprev;
+      const T n2 = den.re * den.re + den.im * den.im;
+      if (!(n2 > T(0))) bad = true;
+      const T inv = T(1) / n2;
+      const cpx<T> rinv = mk(den.re * inv, -den.im * inv);
+      const int64_t idx = (int64_t)l * plane + pq;
+      const cpx<T> cp = sup * rinv;
+      const cpx<T> yp = (xv[u] - sub * yprev) * rinv;
+      cw[idx] = cp.re;
+      cw[N + idx] = cp.im;
+      y[idx] = yp.re;
+      y[N + idx] = yp.im;
+      cprev = cp;
+      yprev = yp;
+    }
   }
   cpx<T> next = mk(T(0), T(0));
-  for (int r = m - 1; r >= 0; --r) {
-    const int l = rev ? (m - 1 - r) : r;
-    const int64_t idx = (int64_t)l * plane + pq;
-    const cpx<T> cp = mk(cw[idx], cw[N + idx]);
-    const cpx<T> v = mk(y[idx], y[N + idx]) - cp * next;
-    y[idx] = v.re;
-    y[N + idx] = v.im;
-    next = v;
+  for (int r0 = m - 1; r0 >= 0; r0 -= U) {
+    cpx<T> cv[U], yv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      if (r >= 0) {
+        const int l = rev ? (m - 1 - r) : r;
+        const int64_t idx = (int64_t)l * plane + pq;
+        cv[u] = mk(cw[idx], cw[N + idx]);
+        yv[u] = mk(y[idx], y[N + idx]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      if (r < 0) break;
+      const int l = rev ? (m - 1 - r) : r;
+      const int64_t idx = (int64_t)l * plane + pq;
+      const cpx<T> v = yv[u] - cv[u] * next;
+      y[idx] = v.re;
+      y[N + idx] = v.im;
+      next = v;
+    }
   }
   if (bad) atomicExch(status, (int)HELM6_BREAKDOWN);
 }

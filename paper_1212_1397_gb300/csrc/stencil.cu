@@ -9,17 +9,18 @@
 // across x/y faces and across Neumann z faces are even reflections (U_{-1} = U_1);
 // across Dirichlet faces they are zero.
 //
-// Thread block: a 32 x 8 (x, y) tile marching over a chunk of z planes.  Each plane tile
-// plus a one-point halo is staged in shared memory (double-buffered, one barrier per
-// plane); each thread keeps the three plane sums (C, Nb, Dg) of planes l-1, l, l+1 in
-// registers, so every input value is read from global memory once per chunk.
+// Thread block: a 32 x 8 (x, y) tile marching over a chunk of 32 z planes.  Each plane
+// tile plus a one-point halo is staged in shared memory by asynchronous copies issued
+// three planes ahead into a ring of five buffers (one barrier per plane); each thread
+// keeps the three plane sums (C, Nb, Dg) of planes l-1, l, l+1 in registers, so every
+// input value is read from global memory once per chunk.
 #include "helm6_internal.h"
 
 namespace helm6 {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, ZCH = 16;
+constexpr int TX = 32, TY = 8, ZCH = 32;
 
 template <typename T>
 struct Sums {
@@ -31,12 +32,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Asynchronous 4- or 8-byte copy global -> shared; src_bytes = 0 zero-fills (ghost = 0).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, int src_bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(TX* TY)
     stencil_kernel(Geom g, StencilCoef coef, const T* __restrict__ x, T* __restrict__ y,
                    const T* __restrict__ f, double* __restrict__ sumsq) {
-  __shared__ T sre[2][TY + 2][TX + 2];
-  __shared__ T sim[2][TY + 2][TX + 2];
+  // ring of NBUF staged planes; plane p + DIST is requested while plane p is used
+  constexpr int DIST = 3, NBUF = DIST + 2;
+  __shared__ T sre[NBUF][TY + 2][TX + 2];
+  __shared__ T sim[NBUF][TY + 2][TX + 2];
   __shared__ double red[TX * TY / 32];
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -51,26 +65,18 @@ __global__ void __launch_bounds__(TX* TY)
   const cpx<T> c2 = cast<T>(coef.interior.w[1][2]);
   const cpx<T> c3 = cast<T>(coef.interior.w[0][2]);
 
-  Sums<T> P0, P1, P2;  // planes l-1, l, l+1 as the march proceeds
-  const cpx<T> zero = {T(0), T(0)};
-  P0 = P1 = P2 = Sums<T>{zero, zero, zero};
-  double acc = 0.0;
-  int buf = 0;
-
-  for (int p = l0 - 1; p <= l1; ++p) {
-    // ---- which plane feeds position p (ghost planes across z faces) ----
-    int src = p;
-    bool zplane = false;
-    if (p < 0) {
-      if (g.face[4] == HELM6_NEUMANN) src = 1; else zplane = true;
-    } else if (p >= g.mz) {
-      if (g.face[5] == HELM6_NEUMANN) src = g.mz - 2; else zplane = true;
-    }
-    // ---- stage the (TY+2) x (TX+2) halo tile of that plane ----
-    for (int t = tid; t < (TX + 2) * (TY + 2); t += TX * TY) {
+  // Halo tile element t = tid + k * TX*TY (k = 0, 1) of every plane: its in-plane source
+  // offset (reflection across Neumann x/y faces) or -1 for a zero ghost, computed once.
+  constexpr int HALO = (TX + 2) * (TY + 2);
+  int hoff[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int t = tid + k * TX * TY;
+    hoff[k] = -1;
+    if (t < HALO) {
       const int sy = t / (TX + 2), sx = t - sy * (TX + 2);
       int gi = blockIdx.x * TX + sx - 1, gj = blockIdx.y * TY + sy - 1;
-      bool ok = !zplane;
+      bool ok = true;
       if (gi < 0) {
         if (g.face[0] == HELM6_NEUMANN) gi = 1; else ok = false;
       } else if (gi >= g.mx) {
@@ -81,16 +87,52 @@ __global__ void __launch_bounds__(TX* TY)
       } else if (gj >= g.my) {
         if (g.face[3] == HELM6_NEUMANN && gj == g.my) gj = g.my - 2; else ok = false;
       }
-      T vr = T(0), vi = T(0);
-      if (ok) {
-        const int64_t idx = (int64_t)src * plane + (int64_t)gj * g.mx + gi;
-        vr = x[idx];
-        vi = x[g.N + idx];
-      }
-      sre[buf][sy][sx] = vr;
-      sim[buf][sy][sx] = vi;
+      if (ok) hoff[k] = gj * g.mx + gi;
     }
+  }
+  T* sre_flat = &sre[0][0][0];
+  T* sim_flat = &sim[0][0][0];
+
+  // stage the halo tile of the plane feeding position p (ghost planes: reflection across a
+  // Neumann z face, zero otherwise) into ring slot `slot`
+  auto stage = [&](int p, int slot) {
+    int src = p;
+    bool zplane = false;
+    if (p < 0) {
+      if (g.face[4] == HELM6_NEUMANN) src = 1; else zplane = true;
+    } else if (p >= g.mz) {
+      if (g.face[5] == HELM6_NEUMANN) src = g.mz - 2; else zplane = true;
+    }
+    const int64_t pbase = (int64_t)src * plane;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int t = tid + k * TX * TY;
+      if (t < HALO) {
+        const bool ok = !zplane && hoff[k] >= 0;
+        const int64_t idx = ok ? pbase + hoff[k] : 0;
+        cp_async<sizeof(T)>(sre_flat + slot * HALO + t, x + idx, ok ? (int)sizeof(T) : 0);
+        cp_async<sizeof(T)>(sim_flat + slot * HALO + t, x + g.N + idx, ok ? (int)sizeof(T) : 0);
+      }
+    }
+  };
+
+  Sums<T> P0, P1, P2;  // planes l-1, l, l+1 as the march proceeds
+  const cpx<T> zero = {T(0), T(0)};
+  P0 = P1 = P2 = Sums<T>{zero, zero, zero};
+  double acc = 0.0;
+
+  const int pfirst = l0 - 1;
+  for (int d = 0; d < DIST; ++d) {
+    if (pfirst + d <= l1) stage(pfirst + d, d);
+    cp_commit();
+  }
+  for (int p = pfirst; p <= l1; ++p) {
+    const int k = p - pfirst;
+    if (p + DIST <= l1) stage(p + DIST, (k + DIST) % NBUF);
+    cp_commit();
+    cp_wait<DIST>();  // the group of plane p has landed
     __syncthreads();
+    const int buf = k % NBUF;
 
     // ---- in-plane sums of plane p at (i, j) ----
     Sums<T> cur;
@@ -107,7 +149,6 @@ __global__ void __launch_bounds__(TX* TY)
     P0 = P1;
     P1 = P2;
     P2 = cur;
-    buf ^= 1;
 
     const int l = p - 1;  // row whose three planes are now in P0, P1, P2
     if (l >= l0 && active) {
@@ -142,6 +183,7 @@ __global__ void __launch_bounds__(TX* TY)
       if (sumsq) acc += (double)out.re * out.re + (double)out.im * out.im;
     }
   }
+  cp_wait<0>();
 
   if (sumsq) {
     acc = warp_sum(acc);
