@@ -36,6 +36,7 @@ struct helm6_ctx {
   double* u64 = nullptr;
   float* u32 = nullptr;
   double last_beta = 0;  // ||F - A U|| after the last FP64 residual
+  bool zline_breakdown = false;  // a z line of the precomputed tables had a zero pivot
   // preconditioner tables (device): V, W = V^{-1} row-major m x m, eigenvalues
   double *Vx64 = nullptr, *Wx64 = nullptr, *Vy64 = nullptr, *Wy64 = nullptr;
   float *Vx32 = nullptr, *Wx32 = nullptr, *Vy32 = nullptr, *Wy32 = nullptr;
@@ -43,6 +44,7 @@ struct helm6_ctx {
   // MIXED: BF16 hi/lo basis tiles for the tensor-core transforms (null: SIMT FP32 path)
   uint8_t *Wx_tc = nullptr, *Wy_tc = nullptr, *Vx_tc = nullptr, *Vy_tc = nullptr;
   int* tcerr = nullptr;
+  float *zrinv32 = nullptr, *zcp32 = nullptr;  // z-line pivot tables (tensor-core path)
   // FP64 vectors (2N doubles each)
   double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
   double *V64 = nullptr, *Z64 = nullptr, *w64 = nullptr, *zt64 = nullptr, *tA64 = nullptr,
@@ -275,7 +277,7 @@ void precond_tc(helm6_ctx* c, const float* in, float* out) {
   launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s);
   prof_stop(c, HELM6_PH_YFWD, e);
   e = prof_start(c);
-  launch_ztri<float>(g, c->lamx, c->lamy, c->diag0, c->alpha, c->tB32, c->tA32, c->cw32, c->status, s, 1);
+  launch_ztri_apply<float>(g, c->zrinv32, c->zcp32, c->tB32, c->tA32, s);
   prof_stop(c, HELM6_PH_ZTRI, e);
   e = prof_start(c);
   launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s);
@@ -401,6 +403,7 @@ int check_status(helm6_ctx* c) {
   std::memcpy(&st, &c->pinned[4], sizeof(int));
   std::memcpy(&te, &c->pinned[5], sizeof(int));
   if (te) return HELM6_ERR_CUDA;
+  if (c->zline_breakdown) return HELM6_BREAKDOWN;
   return st;
 }
 
@@ -462,8 +465,8 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     int k = 0;
     double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true, precond32, c->coef,
-                        &k, &b0, st);
+    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true, precond32,
+                        c->coef, &k, &b0, st);
     if (rc) return rc;
     fix_hist(st, h0, beta / normF);
     iters += k;
@@ -678,6 +681,13 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     if ((rc = upt(&c->Wx_tc, Wx, c->g.mx)) || (rc = upt(&c->Vx_tc, Vx, c->g.mx)) ||
         (rc = upt(&c->Wy_tc, Wy, c->g.my)) || (rc = upt(&c->Vy_tc, Vy, c->g.my)))
       return fail(rc);
+    if ((rc = dalloc(c, &c->zrinv32, v)) || (rc = dalloc(c, &c->zcp32, v))) return fail(rc);
+    if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+    launch_ztri_table<float>(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zrinv32, c->zcp32, c->status, 0, 1);
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
+    int zst = 0;
+    if (cudaMemcpy(&zst, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+    c->zline_breakdown = zst != 0;
   }
   if (cudaMallocHost((void**)&c->pinned, 16 * sizeof(double)) != cudaSuccess) return fail(HELM6_ERR_NOMEM);
   if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);

@@ -84,9 +84,9 @@ void stencil_coefficients(cd k, double h, StencilCoef& c);
 // Kernel launchers (stream-ordered).  Defined in the .cu files.
 // ---------------------------------------------------------------------------------------
 
-// y = A x  (mode 0);  y = f - A x (mode 1);  r = f - A x, y += r (mode 2, SKS-style).
-// sumsq (nullable): per-block partial sums of |result|^2 (mode 0/1: |y|^2, mode 2: |r|^2),
-// nblk entries written, reduced by reduce_sum.
+// y = A x (mode 0);  y = f - A x (mode 1);  y = f + A x (mode 2), A given by its row weights.
+// sumsq (nullable): per-block partial sums of |y|^2, nblk entries written, reduced by
+// reduce_sum.
 template <typename T>
 void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const T* f, T* r,
                     int mode, double* sumsq, int* nblk, cudaStream_t s);
@@ -120,6 +120,14 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
 template <typename T>
 void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha,
                  const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor = 0);
+
+// The same z-line solve with the elimination's pivots precomputed in FP64 (once per
+// context) and stored as tables rinv (pivot reciprocals) and cpr (c') of 2N T each.
+template <typename T>
+void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, T* rinv,
+                       T* cpr, int* status, cudaStream_t s, int xmajor);
+template <typename T>
+void launch_ztri_apply(const Geom& g, const T* rinv, const T* cpr, const T* x, T* y, cudaStream_t s);
 
 // BLAS-1 style kernels on planar complex vectors of N points.
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,

@@ -184,6 +184,130 @@ __global__ void ztri_kernel(Geom g, const double* __restrict__ lamx, const doubl
   if (bad) atomicExch(status, (int)HELM6_BREAKDOWN);
 }
 
+// Line coefficients of the elimination, computed once in FP64 and stored in the working
+// precision: for every (p, q) line and step r of the elimination order, the pivot
+// reciprocal rinv_r = 1 / (d_r - sub_r c'_{r-1}) and c'_r = sup_r rinv_r.  With them the
+// per-apply sweeps are  y'_r = (x_r - sub_r y'_{r-1}) rinv_r  and  x_r = y'_r - c'_r x_{r+1},
+// so the rounding of the pivot recursion does not accumulate along ill-conditioned lines.
+__device__ __forceinline__ void line_coef(const Geom& g, int l, bool rev, double& sub, double& sup) {
+  const int m = g.mz;
+  double a_l = (l == m - 1) ? ((g.face[5] != HELM6_DIRICHLET) ? 2.0 : 1.0) : 1.0;
+  double c_l = (l == 0) ? ((g.face[4] != HELM6_DIRICHLET) ? 2.0 : 1.0) : 1.0;
+  if (l == 0) a_l = 0.0;
+  if (l == m - 1) c_l = 0.0;
+  sub = rev ? c_l : a_l;
+  sup = rev ? a_l : c_l;
+}
+
+template <typename T>
+__global__ void ztri_table_kernel(Geom g, const double* __restrict__ lamx, const double* __restrict__ lamy,
+                                  c64d diag0, c64d alpha, T* __restrict__ rinv, T* __restrict__ cpr, int* status,
+                                  int xmajor) {
+  const int64_t plane = (int64_t)g.mx * g.my;
+  const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= plane) return;
+  const int p = xmajor ? (int)(pq / g.my) : (int)(pq % g.mx);
+  const int q = xmajor ? (int)(pq % g.my) : (int)(pq / g.mx);
+  const double sig = lamx[p] + lamy[q];
+  const int m = g.mz;
+  const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
+  const bool rev = (!lo_s && hi_s);
+  const int64_t N = g.N;
+  double cr = 0.0, ci = 0.0;
+  bool bad = false;
+  for (int r = 0; r < m; ++r) {
+    const int l = rev ? (m - 1 - r) : r;
+    double sub, sup;
+    line_coef(g, l, rev, sub, sup);
+    double dr = diag0.re + sig, di = diag0.im;
+    if (l == 0 && lo_s) {
+      dr += alpha.re;
+      di += alpha.im;
+    }
+    if (l == m - 1 && hi_s) {
+      dr += alpha.re;
+      di += alpha.im;
+    }
+    const double er = dr - sub * cr, ei = di - sub * ci;
+    const double n2 = er * er + ei * ei;
+    if (!(n2 > 0.0)) bad = true;
+    const double ir = er / n2, ii = -ei / n2;
+    cr = sup * ir;
+    ci = sup * ii;
+    const int64_t idx = (int64_t)l * plane + pq;
+    rinv[idx] = (T)ir;
+    rinv[N + idx] = (T)ii;
+    cpr[idx] = (T)cr;
+    cpr[N + idx] = (T)ci;
+  }
+  if (bad) atomicExch(status, (int)HELM6_BREAKDOWN);
+}
+
+template <typename T>
+__global__ void ztri_apply_kernel(Geom g, const T* __restrict__ rinv, const T* __restrict__ cpr,
+                                  const T* __restrict__ x, T* __restrict__ y) {
+  const int64_t plane = (int64_t)g.mx * g.my;
+  const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pq >= plane) return;
+  const int m = g.mz;
+  const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
+  const bool rev = (!lo_s && hi_s);
+  const int64_t N = g.N;
+  constexpr int U = 8;
+  cpx<T> yprev = mk(T(0), T(0));
+  for (int r0 = 0; r0 < m; r0 += U) {
+    cpx<T> xv[U], iv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r < m) {
+        const int l = rev ? (m - 1 - r) : r;
+        const int64_t idx = (int64_t)l * plane + pq;
+        xv[u] = mk(x[idx], x[N + idx]);
+        iv[u] = mk(rinv[idx], rinv[N + idx]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u;
+      if (r >= m) break;
+      const int l = rev ? (m - 1 - r) : r;
+      double sub, sup;
+      line_coef(g, l, rev, sub, sup);
+      const cpx<T> yp = (xv[u] - (T)sub * yprev) * iv[u];
+      const int64_t idx = (int64_t)l * plane + pq;
+      y[idx] = yp.re;
+      y[N + idx] = yp.im;
+      yprev = yp;
+    }
+  }
+  cpx<T> next = mk(T(0), T(0));
+  for (int r0 = m - 1; r0 >= 0; r0 -= U) {
+    cpx<T> cv[U], yv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      if (r >= 0) {
+        const int l = rev ? (m - 1 - r) : r;
+        const int64_t idx = (int64_t)l * plane + pq;
+        cv[u] = mk(cpr[idx], cpr[N + idx]);
+        yv[u] = mk(y[idx], y[N + idx]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 - u;
+      if (r < 0) break;
+      const int l = rev ? (m - 1 - r) : r;
+      const int64_t idx = (int64_t)l * plane + pq;
+      const cpx<T> v = yv[u] - cv[u] * next;
+      y[idx] = v.re;
+      y[N + idx] = v.im;
+      next = v;
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -206,6 +330,27 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
   ztri_kernel<T><<<(unsigned)((lines + bs - 1) / bs), bs, 0, s>>>(g, lamx, lamy, diag0, alpha, x, y,
                                                                   cw, status, xmajor);
 }
+
+
+template <typename T>
+void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, T* rinv,
+                       T* cpr, int* status, cudaStream_t s, int xmajor) {
+  const int64_t lines = (int64_t)g.mx * g.my;
+  note_launch();
+  ztri_table_kernel<T><<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, lamx, lamy, diag0, alpha, rinv, cpr, status,
+                                                                      xmajor);
+}
+
+template <typename T>
+void launch_ztri_apply(const Geom& g, const T* rinv, const T* cpr, const T* x, T* y, cudaStream_t s) {
+  const int64_t lines = (int64_t)g.mx * g.my;
+  note_launch();
+  ztri_apply_kernel<T><<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, rinv, cpr, x, y);
+}
+
+template void launch_ztri_table<float>(const Geom&, const double*, const double*, c64d, c64d, float*, float*, int*,
+                                       cudaStream_t, int);
+template void launch_ztri_apply<float>(const Geom&, const float*, const float*, const float*, float*, cudaStream_t);
 
 template void launch_axis_gemm<float>(const float*, const float*, float*, int, int, int, int64_t, int,
                                       bool, cudaStream_t);

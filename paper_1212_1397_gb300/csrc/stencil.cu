@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(TX* TY)
       const int64_t idx = (int64_t)l * plane + (int64_t)j * g.mx + i;
       if (MODE == 1) {
         out = mk(f[idx] - out.re, f[g.N + idx] - out.im);
+      } else if (MODE == 2) {
+        out = mk(f[idx] + out.re, f[g.N + idx] + out.im);
       }
       y[idx] = out.re;
       y[g.N + idx] = out.im;
@@ -216,8 +218,10 @@ void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const
   note_launch();
   if (mode == 0)
     stencil_kernel<T, 0><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
-  else
+  else if (mode == 1)
     stencil_kernel<T, 1><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+  else
+    stencil_kernel<T, 2><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
 }
 
 template void launch_stencil<float>(const Geom&, const StencilCoef&, const float*, float*,
