@@ -157,6 +157,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
   const int btx = (p.terms == 3 ? 2 : 1) * p.Npad * 128;  // bytes the bulk copy brings
   const int nchunk = p.Npad > 256 ? 2 : 1;
 
+  // basis stages 0 and 1 are requested up front; stage kt + 1 is requested as soon as the
+  // MMAs of step kt - 1 have released its buffer (right after step kt is committed)
+  auto issue_b = [&](int kt) {
+    const int st = kt & 1;
+    uint8_t* sB = smem + st * stage_bytes + 2 * A_TILE;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(btx) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(sB)),
+        "l"(p.W + (size_t)kt * bstage), "r"(btx), "r"(full(st))
+        : "memory");
+  };
+  if (tid == 0) {
+    issue_b(0);
+    if (p.nk > 1) issue_b(1);
+  }
   // data stage in registers: thread t holds rows (t >> 5) + 8 i, k pair (t & 31) * 2
   float2 xr[A_PER_THREAD];
   load_stage(p, m0, 0, tid, xr);
@@ -170,13 +185,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     }
     __syncthreads();
     if (*fail) break;
-    if (tid == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(btx) : "memory");
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(sB)),
-          "l"(p.W + (size_t)kt * bstage), "r"(btx), "r"(full(st))
-          : "memory");
-    }
     store_stage(sA, tid, xr);
     if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, tid, xr);  // in flight during the MMAs
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -203,6 +211,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
                      : "memory");
+        // stage (kt + 1) & 1 was last read by the MMAs of step kt - 1
+        if (kt >= 1 && kt + 1 < p.nk) {
+          if (!poll(done(st ^ 1), ((kt - 1) >> 1) & 1))
+            *fail = 1;
+          else
+            issue_b(kt + 1);
+        }
       }
     }
   }
@@ -251,11 +266,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     if (!p.transposed) {
       __syncthreads();
       const int rows = min(TC_M, p.M_total - m0);
-      const int64_t total = (int64_t)rows * p.P;
       float* dst = p.out + (int64_t)m0 * p.P;
-      for (int64_t i = tid; i < total; i += TC_THREADS) {
-        const int rr = (int)(i / p.P), cc = (int)(i - (int64_t)rr * p.P);
-        dst[i] = stile[rr * sld + cc];
+      if ((p.P & 3) == 0) {
+        // rows of P floats, 16-byte aligned: one warp per row, float4 stores
+        const int q4 = p.P >> 2;
+        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
+          const float* srow = stile + rr * sld;
+          float4* drow = (float4*)(dst + (int64_t)rr * p.P);
+          for (int c4 = lane; c4 < q4; c4 += 32)
+            drow[c4] = make_float4(srow[4 * c4], srow[4 * c4 + 1], srow[4 * c4 + 2], srow[4 * c4 + 3]);
+        }
+      } else {
+        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
+          const float* srow = stile + rr * sld;
+          float* drow = dst + (int64_t)rr * p.P;
+          for (int cc = lane; cc < p.P; cc += 32) drow[cc] = srow[cc];
+        }
       }
     }
   } else if (tid == 0) {
