@@ -40,8 +40,21 @@ METRIC = "time to rel-res 1e-8 at 256^3 k=80 (mixed FP32/BF16 + FP64 refinement)
 # same algorithm), used to scale the oracle's per-iteration sample to a time-to-solution.
 FP64_ITERS_NOMINAL = 12
 
-# ncu dram bytes (read + write) per launch of the dominant kernel at this workload, from
-# the capture summarised under profiles/ (None when the kernel changed since).
+# Library phases that are one kernel each (the roofline is reported for the slowest).
+KERNEL_OF = {
+    "stencil": "stencil_kernel<float,0>",
+    "xform_x_fwd": "xform_tc_kernel (x forward)",
+    "xform_y_fwd": "xform_tc_kernel (y forward)",
+    "ztri": "ztri_apply_kernel<float>",
+    "xform_y_inv": "xform_tc_kernel (y inverse)",
+    "xform_x_inv": "xform_tc_kernel (x inverse)",
+    "gs_dot": "dcgs_dot_kernel<float,2>",
+    "gs_update": "dcgs_update_kernel<float,1>",
+    "resid64": "stencil_kernel<double,1>",
+}
+
+# ncu dram bytes (read + write) per launch of a kernel at this workload, from the captures
+# summarised under profiles/ (absent: not captured since the kernel last changed).
 NCU_TRAFFIC = {}
 
 
@@ -284,17 +297,18 @@ def main():
     # ---- roofline of the dominant kernel (live per-phase events) ----
     hbm, bf16, peak_src = peaks()
     phases = prof["phases"]
-    dom = max(phases, key=lambda p: phases[p]["ms"])
+    single = [p for p in phases if p in KERNEL_OF and phases[p]["count"] > 0]
+    dom = max(single, key=lambda p: phases[p]["ms"])
     cnt = max(phases[dom]["count"], 1)
     per_launch_ms = phases[dom]["ms"] / cnt
-    alg_bytes = 16.0 * N        # FP32 complex read + write per point (one pass)
-    if dom == "resid64":
-        alg_bytes = 48.0 * N    # FP64: read U and F, write r
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": NCU_TRAFFIC.get(dom), "per_launch_ms": per_launch_ms,
-            "alg_bytes_per_launch": alg_bytes}
+    alg_bytes = phases[dom]["bytes"] / cnt        # algorithmic bytes per launch (mean)
+    achieved = phases[dom]["bytes"] / (phases[dom]["ms"] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": KERNEL_OF[dom], "phase": dom, "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
+            "traffic": NCU_TRAFFIC.get(KERNEL_OF[dom]), "per_launch_ms": per_launch_ms,
+            "alg_bytes_per_launch": alg_bytes,
+            "phase_frac": {p: (phases[p]["bytes"] / (phases[p]["ms"] * 1e-3) / 1e9) / hbm
+                           for p in single}}
 
     # ---- CPU oracle baseline (rank 0, N = 1) ----
     cpu = None

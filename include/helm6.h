@@ -150,16 +150,21 @@ enum {
   HELM6_PH_ZTRI = 3,     /* z tridiagonal lines */
   HELM6_PH_YINV = 4,     /* y inverse transform */
   HELM6_PH_XINV = 5,     /* x inverse transform */
-  HELM6_PH_ORTHO = 6,    /* CGS2 dot products, updates, norms, Givens */
-  HELM6_PH_RESID64 = 7,  /* FP64 true residual F - A U and its norm */
-  HELM6_PH_OTHER = 8,    /* conversions, solution updates */
-  HELM6_NPHASE = 9
+  HELM6_PH_DOT = 6,      /* Gram-Schmidt reduction pass (basis inner products) */
+  HELM6_PH_UPDATE = 7,   /* Gram-Schmidt update pass (new basis vector) */
+  HELM6_PH_SMALL = 8,    /* partial-sum reduction, FP64 step algebra and Givens */
+  HELM6_PH_RESID64 = 9,  /* FP64 true residual F - A U and its norm */
+  HELM6_PH_OTHER = 10,   /* conversions, solution updates */
+  HELM6_NPHASE = 11
 };
 
 typedef struct {
   int64_t launches;              /* kernels launched by the library since enabling */
   int64_t count[HELM6_NPHASE];   /* timed intervals per phase */
   double ms[HELM6_NPHASE];       /* summed device milliseconds per phase */
+  double bytes[HELM6_NPHASE];    /* summed algorithmic bytes per phase: one read of each
+                                    input and one write of each output, in the phase's
+                                    working precision */
 } helm6_profile;
 
 /* enable != 0 starts (and resets) measurement, 0 stops it.  INVALID if ctx is NULL. */

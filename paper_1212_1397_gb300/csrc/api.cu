@@ -61,6 +61,7 @@ struct helm6_ctx {
   // measurement (helm6_profile_enable)
   struct Pending {
     int ph;
+    double bytes;
     cudaEvent_t a, b;
   };
   bool prof_on = false;
@@ -68,6 +69,7 @@ struct helm6_ctx {
   std::vector<Pending> ev_pend;
   int64_t prof_count[HELM6_NPHASE] = {};
   double prof_ms[HELM6_NPHASE] = {};
+  double prof_bytes[HELM6_NPHASE] = {};
   long long prof_l0 = 0;
 };
 
@@ -104,6 +106,7 @@ void prof_flush(helm6_ctx* c) {
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->prof_count[p.ph] += 1;
       c->prof_ms[p.ph] += ms;
+      c->prof_bytes[p.ph] += p.bytes;
     }
     c->ev_pool.push_back(p.a);
     c->ev_pool.push_back(p.b);
@@ -121,12 +124,18 @@ cudaEvent_t prof_start(helm6_ctx* c) {
   return a;
 }
 
-void prof_stop(helm6_ctx* c, int ph, cudaEvent_t a) {
+// bytes: algorithmic bytes of the interval (0: use the phase's default for one pass over
+// a field in the Krylov precision, read + write).
+void prof_stop(helm6_ctx* c, int ph, cudaEvent_t a, double bytes = 0.0) {
   if (!a) return;
   cudaEvent_t b = c->ev_pool.back();
   c->ev_pool.pop_back();
   cudaEventRecord(b, c->stream);
-  c->ev_pend.push_back({ph, a, b});
+  if (bytes == 0.0) {
+    const double s = (c->opts.precision == HELM6_FP64) ? 16.0 : 8.0;  // bytes per complex unknown
+    bytes = 2.0 * s * (double)c->g.N;
+  }
+  c->ev_pend.push_back({ph, bytes, a, b});
 }
 
 // ---- 1D eigenbases of the x and y second-difference matrices (closed forms) ----
@@ -312,7 +321,7 @@ int residual64(helm6_ctx* c, double* beta) {
   cudaEvent_t e = prof_start(c);
   launch_stencil<double>(c->g, c->coef, c->U64, c->R64, c->F64, nullptr, 1, c->spart, &nb, c->stream);
   launch_reduce_sum(c->spart, nb, c->scal, c->stream);
-  prof_stop(c, HELM6_PH_RESID64, e);
+  prof_stop(c, HELM6_PH_RESID64, e, 48.0 * (double)c->g.N);
   CK(cudaMemcpyAsync(c->pinned, c->scal, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *beta = std::sqrt(c->pinned[0]);
@@ -353,13 +362,20 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
       prof_stop(c, HELM6_PH_STENCIL, e);
       ++applied;
     }
+    const double vb = 2.0 * sizeof(T) * (double)N;  // one complex field
     cudaEvent_t e = prof_start(c);
     launch_dcgs_dot<T>(V, vs, j, u, full ? w : nullptr, N, c->partial, c->ndot, s);
+    prof_stop(c, HELM6_PH_DOT, e, vb * (j + (full ? 2 : 1)));
+    e = prof_start(c);
     launch_reduce_cols(c->partial, c->ndot, 4 * j + 3, c->red, 0, s);
     launch_dcgs_step(j, full ? 1 : 0, c->red, c->Hr, c->H, ldh, flexible ? c->Tm : nullptr, c->mrest, c->cs, c->sn,
                      c->gv, c->coefv, c->scal + 2, c->brk, s);
-    if (full) launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
-    prof_stop(c, HELM6_PH_ORTHO, e);
+    prof_stop(c, HELM6_PH_SMALL, e, 8.0 * c->ndot * (4 * j + 3));
+    if (full) {
+      e = prof_start(c);
+      launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
+      prof_stop(c, HELM6_PH_UPDATE, e, vb * (j + 4));
+    }
     CK(cudaMemcpyAsync(c->pinned, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&c->pinned[6], c->brk, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -797,6 +813,7 @@ int helm6_profile_enable(helm6_ctx* c, int enable) {
   for (int i = 0; i < HELM6_NPHASE; ++i) {
     c->prof_count[i] = 0;
     c->prof_ms[i] = 0.0;
+    c->prof_bytes[i] = 0.0;
   }
   c->prof_l0 = launch_total();
   return HELM6_OK;
@@ -810,6 +827,7 @@ int helm6_profile_read(helm6_ctx* c, helm6_profile* out) {
   for (int i = 0; i < HELM6_NPHASE; ++i) {
     out->count[i] = c->prof_count[i];
     out->ms[i] = c->prof_ms[i];
+    out->bytes[i] = c->prof_bytes[i];
   }
   return HELM6_OK;
 }

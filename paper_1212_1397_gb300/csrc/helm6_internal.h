@@ -21,6 +21,10 @@ using cd = std::complex<double>;
 // ---------------------------------------------------------------------------------------
 // Small complex type usable in device code.
 // ---------------------------------------------------------------------------------------
+// Fused multiply-add in the operands' own precision (fmaf for float, fma for double).
+__host__ __device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+
 template <typename T>
 struct cpx {
   T re, im;
@@ -41,10 +45,10 @@ __host__ __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s 
 // a + w * s  (complex fused multiply-add)
 template <typename T>
 __host__ __device__ __forceinline__ cpx<T> cfma(cpx<T> w, cpx<T> s, cpx<T> a) {
-  a.re = fma(w.re, s.re, a.re);
-  a.re = fma(-w.im, s.im, a.re);
-  a.im = fma(w.re, s.im, a.im);
-  a.im = fma(w.im, s.re, a.im);
+  a.re = fmx(w.re, s.re, a.re);
+  a.re = fmx(-w.im, s.im, a.re);
+  a.im = fmx(w.re, s.im, a.im);
+  a.im = fmx(w.im, s.re, a.im);
   return a;
 }
 
@@ -84,7 +88,8 @@ void stencil_coefficients(cd k, double h, StencilCoef& c);
 // Kernel launchers (stream-ordered).  Defined in the .cu files.
 // ---------------------------------------------------------------------------------------
 
-// y = A x (mode 0);  y = f - A x (mode 1);  y = f + A x (mode 2), A given by its row weights.
+// y = A x (mode 0);  y = f - A x (mode 1);  y = f + A x (mode 2, no norm), A given by its row
+// weights.
 // sumsq (nullable): per-block partial sums of |y|^2, nblk entries written, reduced by
 // reduce_sum.
 template <typename T>

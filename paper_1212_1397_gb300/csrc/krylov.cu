@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(RB) sumsq_kernel(const T* __restrict__ x, int6
   T a = T(0);
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * N; idx += stride) {
     const T v = x[idx];
-    a = fma(v, v, a);
+    a = fmx(v, v, a);
   }
   const double s = block_sum((double)a, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -86,8 +86,8 @@ __global__ void lincomb_kernel(const TI* __restrict__ V, int64_t vstride, int co
       const TI* v = V + (int64_t)c * vstride;
       const TI vr = v[idx], vi = v[N + idx];
       const TI a = (TI)yr[c], b = (TI)yi[c];
-      sr = fma(vr, a, fma(-vi, b, sr));
-      si = fma(vr, b, fma(vi, a, si));
+      sr = fmx(vr, a, fmx(-vi, b, sr));
+      si = fmx(vr, b, fmx(vi, a, si));
     }
     if (accumulate) {
       out[idx] += (TO)sr;
@@ -204,9 +204,9 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
       if (ch == 0) {
 #pragma unroll
         for (int k = 0; k < PTS; ++k) {
-          acc[4 * CHD] = fma(ur[k], ur[k], fma(ui[k], ui[k], acc[4 * CHD]));
-          acc[4 * CHD + 1] = fma(ur[k], wr[k], fma(ui[k], wi[k], acc[4 * CHD + 1]));
-          acc[4 * CHD + 2] = fma(ur[k], wi[k], fma(-ui[k], wr[k], acc[4 * CHD + 2]));
+          acc[4 * CHD] = fmx(ur[k], ur[k], fmx(ui[k], ui[k], acc[4 * CHD]));
+          acc[4 * CHD + 1] = fmx(ur[k], wr[k], fmx(ui[k], wi[k], acc[4 * CHD + 1]));
+          acc[4 * CHD + 2] = fmx(ur[k], wi[k], fmx(-ui[k], wr[k], acc[4 * CHD + 2]));
         }
       }
 #pragma unroll
@@ -214,10 +214,10 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
         if (c < nc) {
 #pragma unroll
           for (int k = 0; k < PTS; ++k) {
-            acc[4 * c] = fma(vr[c][k], ur[k], fma(vi[c][k], ui[k], acc[4 * c]));
-            acc[4 * c + 1] = fma(vr[c][k], ui[k], fma(-vi[c][k], ur[k], acc[4 * c + 1]));
-            acc[4 * c + 2] = fma(vr[c][k], wr[k], fma(vi[c][k], wi[k], acc[4 * c + 2]));
-            acc[4 * c + 3] = fma(vr[c][k], wi[k], fma(-vi[c][k], wr[k], acc[4 * c + 3]));
+            acc[4 * c] = fmx(vr[c][k], ur[k], fmx(vi[c][k], ui[k], acc[4 * c]));
+            acc[4 * c + 1] = fmx(vr[c][k], ui[k], fmx(-vi[c][k], ur[k], acc[4 * c + 1]));
+            acc[4 * c + 2] = fmx(vr[c][k], wr[k], fmx(vi[c][k], wi[k], acc[4 * c + 2]));
+            acc[4 * c + 3] = fmx(vr[c][k], wi[k], fmx(-vi[c][k], wr[k], acc[4 * c + 3]));
           }
         }
       }
@@ -274,16 +274,16 @@ __global__ void __launch_bounds__(RB) dcgs_update_kernel(const T* __restrict__ V
     for (int c = 0; c < count; ++c) {
       const T* v = V + (int64_t)c * vs;
       const T vr = v[q], vi = v[N + q];
-      ur = fma(-vr, s_r[c], fma(vi, s_i[c], ur));
-      ui = fma(-vr, s_i[c], fma(-vi, s_r[c], ui));
-      wr = fma(-vr, t_r[c], fma(vi, t_i[c], wr));
-      wi = fma(-vr, t_i[c], fma(-vi, t_r[c], wi));
+      ur = fmx(-vr, s_r[c], fmx(vi, s_i[c], ur));
+      ui = fmx(-vr, s_i[c], fmx(-vi, s_r[c], ui));
+      wr = fmx(-vr, t_r[c], fmx(vi, t_i[c], wr));
+      wi = fmx(-vr, t_i[c], fmx(-vi, t_r[c], wi));
     }
     const T nr = ur * inv, ni = ui * inv;
     v_out[q] = nr;
     v_out[N + q] = ni;
-    wr = fma(-nr, cr, fma(ni, ci, wr));
-    wi = fma(-nr, ci, fma(-ni, cr, wi));
+    wr = fmx(-nr, cr, fmx(ni, ci, wr));
+    wi = fmx(-nr, ci, fmx(-ni, cr, wi));
     u[q] = wr * inv;
     u[N + q] = wi * inv;
   };
@@ -307,24 +307,24 @@ __global__ void __launch_bounds__(RB) dcgs_update_kernel(const T* __restrict__ V
         for (int e = 0; e < UB; ++e) {
           if (c0 + e < count) {
             const int c = c0 + e;
-            ur.x = fma(-vr[e].x, s_r[c], fma(vi[e].x, s_i[c], ur.x));
-            ui.x = fma(-vr[e].x, s_i[c], fma(-vi[e].x, s_r[c], ui.x));
-            ur.y = fma(-vr[e].y, s_r[c], fma(vi[e].y, s_i[c], ur.y));
-            ui.y = fma(-vr[e].y, s_i[c], fma(-vi[e].y, s_r[c], ui.y));
-            wr.x = fma(-vr[e].x, t_r[c], fma(vi[e].x, t_i[c], wr.x));
-            wi.x = fma(-vr[e].x, t_i[c], fma(-vi[e].x, t_r[c], wi.x));
-            wr.y = fma(-vr[e].y, t_r[c], fma(vi[e].y, t_i[c], wr.y));
-            wi.y = fma(-vr[e].y, t_i[c], fma(-vi[e].y, t_r[c], wi.y));
+            ur.x = fmx(-vr[e].x, s_r[c], fmx(vi[e].x, s_i[c], ur.x));
+            ui.x = fmx(-vr[e].x, s_i[c], fmx(-vi[e].x, s_r[c], ui.x));
+            ur.y = fmx(-vr[e].y, s_r[c], fmx(vi[e].y, s_i[c], ur.y));
+            ui.y = fmx(-vr[e].y, s_i[c], fmx(-vi[e].y, s_r[c], ui.y));
+            wr.x = fmx(-vr[e].x, t_r[c], fmx(vi[e].x, t_i[c], wr.x));
+            wi.x = fmx(-vr[e].x, t_i[c], fmx(-vi[e].x, t_r[c], wi.x));
+            wr.y = fmx(-vr[e].y, t_r[c], fmx(vi[e].y, t_i[c], wr.y));
+            wi.y = fmx(-vr[e].y, t_i[c], fmx(-vi[e].y, t_r[c], wi.y));
           }
         }
       }
       const T2 nr = {ur.x * inv, ur.y * inv}, ni = {ui.x * inv, ui.y * inv};
       ((T2*)v_out)[q] = nr;
       ((T2*)(v_out + N))[q] = ni;
-      wr.x = fma(-nr.x, cr, fma(ni.x, ci, wr.x));
-      wi.x = fma(-nr.x, ci, fma(-ni.x, cr, wi.x));
-      wr.y = fma(-nr.y, cr, fma(ni.y, ci, wr.y));
-      wi.y = fma(-nr.y, ci, fma(-ni.y, cr, wi.y));
+      wr.x = fmx(-nr.x, cr, fmx(ni.x, ci, wr.x));
+      wi.x = fmx(-nr.x, ci, fmx(-ni.x, cr, wi.x));
+      wr.y = fmx(-nr.y, cr, fmx(ni.y, ci, wr.y));
+      wi.y = fmx(-nr.y, ci, fmx(-ni.y, cr, wi.y));
       ((T2*)u)[q] = T2{wr.x * inv, wr.y * inv};
       ((T2*)(u + N))[q] = T2{wi.x * inv, wi.y * inv};
     } else {

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmx(av[a], bv[b], acc[a][b]);
     }
     __syncthreads();
   }

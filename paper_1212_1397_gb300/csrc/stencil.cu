@@ -43,7 +43,7 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int MODE>
+template <typename T, int MODE, bool NORM>
 __global__ void __launch_bounds__(TX* TY)
     stencil_kernel(Geom g, StencilCoef coef, const T* __restrict__ x, T* __restrict__ y,
                    const T* __restrict__ f, double* __restrict__ sumsq) {
@@ -182,12 +182,12 @@ __global__ void __launch_bounds__(TX* TY)
       }
       y[idx] = out.re;
       y[g.N + idx] = out.im;
-      if (sumsq) acc += (double)out.re * out.re + (double)out.im * out.im;
+      if (NORM) acc += (double)out.re * out.re + (double)out.im * out.im;
     }
   }
   cp_wait<0>();
 
-  if (sumsq) {
+  if (NORM) {
     acc = warp_sum(acc);
     if ((tid & 31) == 0) red[tid >> 5] = acc;
     __syncthreads();
@@ -202,9 +202,227 @@ __global__ void __launch_bounds__(TX* TY)
   }
 }
 
+// FP32 variant for the Krylov bulk: 32 x 16 (x, y) tile, a 32 x 4 thread block, each
+// thread computing 4 y-adjacent points from 6 x 3 shared-memory loads per component.  A
+// halo row is staged in shared memory as [unused x3 | left ghost | 32 points | right ghost]
+// (stride 40 floats) so that the 32-point middle is 16-byte aligned and can be copied in
+// 16-byte chunks when mx % 4 == 0; the two edge columns, and everything when a chunk would
+// cross the field's x extent, are copied element by element with the ghost rules.
+constexpr int T4X = 32, T4Y = 16, T4R = 4, T4ROWS = T4Y + 2, T4LD = 40;
+constexpr int T4SLOTS = 2 * T4ROWS * 10;  // components x rows x (8 chunks + 2 edges)
+
+__device__ __forceinline__ int ghost_index(int gi, int m, int lo_neumann, int hi_neumann) {
+  if (gi < 0) return lo_neumann ? 1 : -1;
+  if (gi >= m) return (hi_neumann && gi == m) ? m - 2 : -1;
+  return gi;
+}
+
+// NORM: accumulate the block's |y|^2 (FP64) into sumsq; a compile-time flag so that the
+// FP32 path carries no FP64 arithmetic when no norm is wanted.
+template <int MODE, bool NORM>
+__global__ void __launch_bounds__(T4X* T4Y / T4R)
+    stencil4_kernel(Geom g, StencilCoef coef, const float* __restrict__ x, float* __restrict__ y,
+                    const float* __restrict__ f, double* __restrict__ sumsq) {
+  constexpr int DIST = 3, NBUF = DIST + 2;
+  constexpr int NT = T4X * T4Y / T4R;  // 128 threads
+  __shared__ __align__(16) float sbuf[NBUF][2][T4ROWS][T4LD];
+  __shared__ double red[NT / 32];
+
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T4X + tx;
+  const int x0 = blockIdx.x * T4X, y0 = blockIdx.y * T4Y;
+  const int i = x0 + tx;
+  const int l0 = blockIdx.z * ZCH;
+  const int l1 = min(l0 + ZCH, g.mz);
+  const int64_t plane = (int64_t)g.mx * g.my;
+  const bool xn0 = g.face[0] == HELM6_NEUMANN, xn1 = g.face[1] == HELM6_NEUMANN;
+  const bool yn0 = g.face[2] == HELM6_NEUMANN, yn1 = g.face[3] == HELM6_NEUMANN;
+  const bool vec_ok = (g.mx & 3) == 0;
+
+  // per-thread staging slots (fixed for every plane): component, halo row, slot kind
+  int soff[3], sdst[3], skind[3];  // skind: 0 none, 1 vector chunk, 2 scalar x4, 3 scalar edge
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int t = tid + k * NT;
+    skind[k] = 0;
+    soff[k] = -1;
+    sdst[k] = 0;
+    if (t < T4SLOTS) {
+      const int comp = t / (T4ROWS * 10), rem = t - comp * (T4ROWS * 10);
+      const int sy = rem / 10, sl = rem - sy * 10;
+      const int gj = ghost_index(y0 + sy - 1, g.my, yn0, yn1);
+      sdst[k] = (comp * T4ROWS + sy) * T4LD;  // start of the row in one ring slot
+      if (sl < 8) {
+        const int xs = x0 + 4 * sl;
+        sdst[k] += 4 + 4 * sl;
+        skind[k] = (vec_ok && xs + 3 < g.mx) ? 1 : 2;
+        soff[k] = (gj < 0) ? -1 : gj * g.mx + xs;  // row offset of the chunk's first point
+      } else {
+        const int gi = ghost_index(sl == 8 ? x0 - 1 : x0 + T4X, g.mx, xn0, xn1);
+        sdst[k] += (sl == 8) ? 3 : 4 + T4X;
+        skind[k] = 3;
+        soff[k] = (gj < 0 || gi < 0) ? -1 : gj * g.mx + gi;
+      }
+      soff[k] = (soff[k] < 0) ? -1 : soff[k];
+      // component offset in the source is added at staging time
+      skind[k] |= comp << 4;
+      // for scalar chunks keep the row index for per-element ghost mapping
+      if ((skind[k] & 15) == 2) soff[k] = (gj < 0) ? -1 : gj;  // row only
+    }
+  }
+
+  auto stage = [&](int p, int slot) {
+    int src = p;
+    bool zplane = false;
+    if (p < 0) {
+      if (g.face[4] == HELM6_NEUMANN) src = 1; else zplane = true;
+    } else if (p >= g.mz) {
+      if (g.face[5] == HELM6_NEUMANN) src = g.mz - 2; else zplane = true;
+    }
+    const int64_t pbase = (int64_t)src * plane;
+    float* sl_base = &sbuf[slot][0][0][0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int kind = skind[k] & 15;
+      if (kind == 0) continue;
+      const int comp = skind[k] >> 4;
+      const float* xb = x + (comp ? g.N : 0) + pbase;
+      float* d = sl_base + sdst[k];
+      if (kind == 1) {
+        const bool ok = !zplane && soff[k] >= 0;
+        const uint32_t da = (uint32_t)__cvta_generic_to_shared(d);
+        const float* sp = ok ? xb + soff[k] : x;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(da), "l"(sp), "r"(ok ? 16 : 0)
+                     : "memory");
+      } else if (kind == 2) {
+        // the 4 points of the chunk one by one (x extent not a multiple of 4, or partial tile)
+        const int sl = ((sdst[k] % T4LD) - 4) / 4;
+        for (int e = 0; e < 4; ++e) {
+          const int gi = ghost_index(x0 + 4 * sl + e, g.mx, xn0, xn1);
+          const bool ok = !zplane && soff[k] >= 0 && gi >= 0;
+          const float* sp = ok ? xb + (int64_t)soff[k] * g.mx + gi : x;
+          cp_async<4>(d + e, sp, ok ? 4 : 0);
+        }
+      } else {
+        const bool ok = !zplane && soff[k] >= 0;
+        cp_async<4>(d, ok ? xb + soff[k] : x, ok ? 4 : 0);
+      }
+    }
+  };
+
+  const cpx<float> c0 = cast<float>(coef.interior.w[1][0]);
+  const cpx<float> c1 = cast<float>(coef.interior.w[1][1]);
+  const cpx<float> c2 = cast<float>(coef.interior.w[1][2]);
+  const cpx<float> c3 = cast<float>(coef.interior.w[0][2]);
+  // Sommerfeld-like face rows of this block, if any (one z chunk holds at most one such
+  // face plane when ZCH < mz; both when the chunk spans the whole axis)
+  cpx<float> wlo[3][3], whi[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      wlo[a][b] = cast<float>(coef.s_lo.w[a][b]);
+      whi[a][b] = cast<float>(coef.s_hi.w[a][b]);
+    }
+  const cpx<float> zero = {0.f, 0.f};
+  Sums<float> P0[T4R], P1[T4R], P2[T4R];
+#pragma unroll
+  for (int r = 0; r < T4R; ++r) P0[r] = P1[r] = P2[r] = Sums<float>{zero, zero, zero};
+  double acc = 0.0;
+
+  const int pfirst = l0 - 1;
+  for (int d = 0; d < DIST; ++d) {
+    if (pfirst + d <= l1) stage(pfirst + d, d);
+    cp_commit();
+  }
+  for (int p = pfirst; p <= l1; ++p) {
+    const int k = p - pfirst;
+    if (p + DIST <= l1) stage(p + DIST, (k + DIST) % NBUF);
+    cp_commit();
+    cp_wait<DIST>();
+    __syncthreads();
+    const int buf = k % NBUF;
+    // 6 halo rows x 3 columns per component for this thread's 4 points
+    float vr[T4R + 2][3], vi[T4R + 2][3];
+#pragma unroll
+    for (int rr = 0; rr < T4R + 2; ++rr) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        vr[rr][cc] = sbuf[buf][0][T4R * ty + rr][tx + 3 + cc];
+        vi[rr][cc] = sbuf[buf][1][T4R * ty + rr][tx + 3 + cc];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < T4R; ++r) {
+      Sums<float> cur;
+      cur.c = mk(vr[r + 1][1], vi[r + 1][1]);
+      cur.n = mk(vr[r + 1][0] + vr[r + 1][2] + vr[r][1] + vr[r + 2][1],
+                 vi[r + 1][0] + vi[r + 1][2] + vi[r][1] + vi[r + 2][1]);
+      cur.d = mk(vr[r][0] + vr[r][2] + vr[r + 2][0] + vr[r + 2][2], vi[r][0] + vi[r][2] + vi[r + 2][0] + vi[r + 2][2]);
+      P0[r] = P1[r];
+      P1[r] = P2[r];
+      P2[r] = cur;
+    }
+    const int l = p - 1;
+    if (l >= l0 && i < g.mx) {
+      const bool slo = (l == 0) && (g.face[4] == HELM6_SOMMERFELD);
+      const bool shi = (l == g.mz - 1) && (g.face[5] == HELM6_SOMMERFELD);
+#pragma unroll
+      for (int r = 0; r < T4R; ++r) {
+        const int j = y0 + T4R * ty + r;
+        if (j >= g.my) continue;
+        cpx<float> out;
+        if (!slo && !shi) {
+          out = c0 * P1[r].c;
+          out = cfma(c1, P1[r].n + P0[r].c + P2[r].c, out);
+          out = cfma(c2, P1[r].d + P0[r].n + P2[r].n, out);
+          out = cfma(c3, P0[r].d + P2[r].d, out);
+        } else {
+          out = zero;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const cpx<float> wc = slo ? wlo[0][a] : whi[0][a];
+            const cpx<float> wm = slo ? wlo[1][a] : whi[1][a];
+            const cpx<float> wp = slo ? wlo[2][a] : whi[2][a];
+            const cpx<float> s0 = (a == 0) ? P0[r].c : (a == 1) ? P0[r].n : P0[r].d;
+            const cpx<float> s1 = (a == 0) ? P1[r].c : (a == 1) ? P1[r].n : P1[r].d;
+            const cpx<float> s2 = (a == 0) ? P2[r].c : (a == 1) ? P2[r].n : P2[r].d;
+            out = cfma(wc, s0, out);
+            out = cfma(wm, s1, out);
+            out = cfma(wp, s2, out);
+          }
+        }
+        const int64_t idx = (int64_t)l * plane + (int64_t)j * g.mx + i;
+        if (MODE == 1) {
+          out = mk(f[idx] - out.re, f[g.N + idx] - out.im);
+        } else if (MODE == 2) {
+          out = mk(f[idx] + out.re, f[g.N + idx] + out.im);
+        }
+        y[idx] = out.re;
+        y[g.N + idx] = out.im;
+        if (NORM) acc += (double)out.re * out.re + (double)out.im * out.im;
+      }
+    }
+  }
+  cp_wait<0>();
+  if (NORM) {
+    acc = warp_sum(acc);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid < 32) {
+      double v = (tid < NT / 32) ? red[tid] : 0.0;
+      v = warp_sum(v);
+      if (tid == 0) {
+        const int64_t b = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        sumsq[b] = v;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int stencil_blocks(const Geom& g) {
+  // the larger of the two kernels' grids (FP64: 32 x 8 tiles, FP32: 32 x 16 tiles)
   return ((g.mx + TX - 1) / TX) * ((g.my + TY - 1) / TY) * ((g.mz + ZCH - 1) / ZCH);
 }
 
@@ -212,16 +430,42 @@ template <typename T>
 void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const T* f, T* r,
                     int mode, double* sumsq, int* nblk, cudaStream_t s) {
   (void)r;
+  if (sizeof(T) == 4) {
+    dim3 block(T4X, T4Y / T4R);
+    dim3 grid((g.mx + T4X - 1) / T4X, (g.my + T4Y - 1) / T4Y, (g.mz + ZCH - 1) / ZCH);
+    if (nblk) *nblk = (int)(grid.x * grid.y * grid.z);
+    note_launch();
+    const float* xf = (const float*)x;
+    float* yf = (float*)y;
+    const float* ff = (const float*)f;
+    const bool nrm = sumsq != nullptr;
+    if (mode == 0 && !nrm)
+      stencil4_kernel<0, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+    else if (mode == 0)
+      stencil4_kernel<0, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+    else if (mode == 1 && !nrm)
+      stencil4_kernel<1, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+    else if (mode == 1)
+      stencil4_kernel<1, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+    else
+      stencil4_kernel<2, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, nullptr);
+    return;
+  }
   dim3 block(TX, TY);
   dim3 grid((g.mx + TX - 1) / TX, (g.my + TY - 1) / TY, (g.mz + ZCH - 1) / ZCH);
   if (nblk) *nblk = (int)(grid.x * grid.y * grid.z);
   note_launch();
-  if (mode == 0)
-    stencil_kernel<T, 0><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+  const bool nrm = sumsq != nullptr;
+  if (mode == 0 && !nrm)
+    stencil_kernel<T, 0, false><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+  else if (mode == 0)
+    stencil_kernel<T, 0, true><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+  else if (mode == 1 && !nrm)
+    stencil_kernel<T, 1, false><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
   else if (mode == 1)
-    stencil_kernel<T, 1><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+    stencil_kernel<T, 1, true><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
   else
-    stencil_kernel<T, 2><<<grid, block, 0, s>>>(g, c, x, y, f, sumsq);
+    stencil_kernel<T, 2, false><<<grid, block, 0, s>>>(g, c, x, y, f, nullptr);
 }
 
 template void launch_stencil<float>(const Geom&, const StencilCoef&, const float*, float*,

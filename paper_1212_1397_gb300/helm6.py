@@ -27,8 +27,8 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", 
            "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc")
 
-PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "ortho",
-          "resid64", "other")
+PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
+          "gs_update", "gs_small", "resid64", "other")
 
 
 class C64(C.Structure):
@@ -53,11 +53,11 @@ class Stats(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64), ("count", C.c_int64 * len(PHASES)),
-                ("ms", C.c_double * len(PHASES))]
+                ("ms", C.c_double * len(PHASES)), ("bytes", C.c_double * len(PHASES))]
 
     def to_dict(self):
         return dict(launches=self.launches,
-                    phases={PHASES[i]: dict(count=self.count[i], ms=self.ms[i])
+                    phases={PHASES[i]: dict(count=self.count[i], ms=self.ms[i], bytes=self.bytes[i])
                             for i in range(len(PHASES))})
 
 
