@@ -57,6 +57,7 @@ struct helm6_ctx {
          *gv = nullptr, *yv = nullptr, *h2 = nullptr, *scal = nullptr;
   int* status = nullptr;
   double* pinned = nullptr;  // host-pinned readback slots
+  cudaEvent_t step_ev[2] = {nullptr, nullptr};  // Arnoldi step completion (alternating)
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
   struct Pending {
@@ -100,8 +101,12 @@ int dalloc(helm6_ctx* c, T** p, size_t count) {
 }
 
 // ---- per-phase event timing (measurement only) ----
-void prof_flush(helm6_ctx* c) {
+// Accumulate finished intervals.  blocking = false stops at the first interval whose end
+// event has not completed (so that the host does not wait for queued work).
+void prof_flush(helm6_ctx* c, bool blocking = true) {
+  size_t done = 0;
   for (auto& p : c->ev_pend) {
+    if (!blocking && cudaEventQuery(p.b) != cudaSuccess) break;
     float ms = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       c->prof_count[p.ph] += 1;
@@ -110,8 +115,10 @@ void prof_flush(helm6_ctx* c) {
     }
     c->ev_pool.push_back(p.a);
     c->ev_pool.push_back(p.b);
+    ++done;
   }
-  c->ev_pend.clear();
+  c->ev_pend.erase(c->ev_pend.begin(), c->ev_pend.begin() + done);
+  cudaGetLastError();  // a query of an unfinished event is not an error
 }
 
 cudaEvent_t prof_start(helm6_ctx* c) {
@@ -352,6 +359,28 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
   if (flexible) CK(cudaMemsetAsync(c->Tm, 0, sizeof(double) * 2 * c->mrest * c->mrest, s));
   int k = 0, applied = 0;
   *beta = 0.0;
+  // The host enqueues step j before reading the results of step j - 1 (two pinned slots and
+  // events alternate), so the device never waits for the host between steps.  Step s
+  // reports the estimate of column s - 1; when that meets the tolerance, the one step
+  // queued behind it is wasted work that leaves columns < s untouched.
+  auto finish = [&](int sidx, bool* stop) -> int {
+    CK(cudaEventSynchronize(c->step_ev[sidx & 1]));
+    if (c->prof_on) prof_flush(c, false);
+    const double est = c->pinned[8 + (sidx & 1)];
+    int brk = 0;
+    std::memcpy(&brk, &c->pinned[10 + (sidx & 1)], sizeof(int));
+    *stop = false;
+    if (sidx == 0) {
+      *beta = est;
+      if (brk || !std::isfinite(est)) *stop = true;
+    } else {
+      k = sidx;
+      if (st) st->iters++;
+      push_hist(st, est);  // rescaled by the caller
+      if (!(est > abs_tol) || !std::isfinite(est) || brk) *stop = true;
+    }
+    return HELM6_OK;
+  };
   for (int j = 0;; ++j) {
     const bool full = (j < m) && (applied < maxsteps);
     if (full) {
@@ -371,28 +400,25 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
     launch_dcgs_step(j, full ? 1 : 0, c->red, c->Hr, c->H, ldh, flexible ? c->Tm : nullptr, c->mrest, c->cs, c->sn,
                      c->gv, c->coefv, c->scal + 2, c->brk, s);
     prof_stop(c, HELM6_PH_SMALL, e, 8.0 * c->ndot * (4 * j + 3));
+    CK(cudaMemcpyAsync(&c->pinned[8 + (j & 1)], c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&c->pinned[10 + (j & 1)], c->brk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->step_ev[j & 1], s));
     if (full) {
       e = prof_start(c);
       launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
       prof_stop(c, HELM6_PH_UPDATE, e, vb * (j + 4));
     }
-    CK(cudaMemcpyAsync(c->pinned, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(&c->pinned[6], c->brk, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (c->prof_on) prof_flush(c);
-    const double est = c->pinned[0];
-    int brk = 0;
-    std::memcpy(&brk, &c->pinned[6], sizeof(int));
-    if (j == 0) {
-      *beta = est;
-      if (brk || !std::isfinite(est)) break;
-    } else {
-      k = j;
-      if (st) st->iters++;
-      push_hist(st, est);  // rescaled by the caller
-      if (!(est > abs_tol) || !std::isfinite(est) || brk) break;
+    bool stop = false;
+    if (j >= 1) {
+      int rc2 = finish(j - 1, &stop);
+      if (rc2) return rc2;
+      if (stop) break;
     }
-    if (!full) break;
+    if (!full) {
+      int rc2 = finish(j, &stop);
+      if (rc2) return rc2;
+      break;
+    }
   }
   *kout = k;
   if (k > 0) launch_backsolve(c->H, ldh, k, c->gv, c->yv, s);
@@ -573,6 +599,8 @@ void helm6_destroy(helm6_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->step_ev)
+    if (e) cudaEventDestroy(e);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
@@ -706,6 +734,8 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     c->zline_breakdown = zst != 0;
   }
   if (cudaMallocHost((void**)&c->pinned, 16 * sizeof(double)) != cudaSuccess) return fail(HELM6_ERR_NOMEM);
+  for (int i = 0; i < 2; ++i)
+    if (cudaEventCreateWithFlags(&c->step_ev[i], cudaEventDisableTiming) != cudaSuccess) return fail(HELM6_ERR_CUDA);
   if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
   *out = c;
