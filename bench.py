@@ -38,7 +38,7 @@ WORKLOAD = "mixed_n256_k80"
 METRIC = "time to rel-res 1e-8 at 256^3 k=80 (mixed FP32/BF16 + FP64 refinement)"
 # FP64 GMRES(30) iterations of this workload to 1e-8 (plain GPU path; the oracle runs the
 # same algorithm), used to scale the oracle's per-iteration sample to a time-to-solution.
-FP64_ITERS_NOMINAL = 12
+FP64_ITERS_NOMINAL = 175
 
 # Library phases that are one kernel each (the roofline is reported for the slowest).
 KERNEL_OF = {
