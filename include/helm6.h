@@ -92,6 +92,8 @@ typedef struct {
   int nhist;          /* entries in hist */
   double hist[HELM6_MAX_HIST];  /* relative residual after each iteration (estimates for
                                    GMRES, true residuals for SKS and refinement steps) */
+  int cnn_cycles;     /* MIXED FGMRES with a learned stage attached: inner cycles that used
+                         it (the others used the direct preconditioner alone) */
 } helm6_stats;
 
 /* Fill opts with the defaults listed above. */
@@ -155,7 +157,8 @@ enum {
   HELM6_PH_SMALL = 8,    /* partial-sum reduction, FP64 step algebra and Givens */
   HELM6_PH_RESID64 = 9,  /* FP64 true residual F - A U and its norm */
   HELM6_PH_OTHER = 10,   /* conversions, solution updates */
-  HELM6_NPHASE = 11
+  HELM6_PH_CNN = 11,     /* learned stage: residual of the direct preconditioner and network */
+  HELM6_NPHASE = 12
 };
 
 typedef struct {
@@ -201,6 +204,57 @@ int helm6_profile_read(helm6_ctx* ctx, helm6_profile* out);
 #define HELM6_NOALLOC_MAX_BLOCKS 65536
 int helm6_residual_noalloc(int n, double h, helm6_c64 k, const int faces[6], const void* F,
                            const void* u, void* r, double* sumsq, void* stream);
+
+/* ---- Learned second preconditioner stage (the paper has no counterpart) ----
+ * A small 3D convolutional network N (4 layers of zero-padded 3x3x3 cross-correlation,
+ * channels 2 -> 16 -> 16 -> 16 -> 2, bias, GELU x*Phi(x) after layers 1-3; channel 0/1 =
+ * real/imaginary part) corrects what the direct preconditioner of Eq. 3DAP leaves:
+ *
+ *     z = A_p^{-1} u + c s N((u - A A_p^{-1} u) / s),   s = sqrt(mean |u - A A_p^{-1} u|^2),
+ *
+ * used as the preconditioner of MIXED FGMRES (flexible GMRES accepts any map per column).
+ * Parameters: one flat vector of HELM6_CNN_NPARAMS floats, per layer W[c_out][c_in][dz][dy][dx]
+ * (C order) then b[c_out].  Arithmetic: BF16-rounded weights and network input, BF16
+ * activations between layers, FP32 accumulation, FP32 biases and output. */
+#define HELM6_CNN_NPARAMS 15602
+enum { HELM6_CNN_OFF = 0,   /* detach: the direct preconditioner alone */
+       HELM6_CNN_ON = 1,    /* every inner cycle uses the learned stage */
+       HELM6_CNN_AUTO = 2   /* inner cycles 0 and 1 use it, cycle 2 does not; the rest use
+                               whichever of cycles 1 and 2 reduced the true residual more per
+                               iteration (the direct preconditioner is the fallback) */ };
+
+/* Attach (or with HELM6_CNN_OFF detach) a network to a MIXED FGMRES context.  theta: HOST
+ * array of HELM6_CNN_NPARAMS floats (copied); out_scale: c above.  Allocates two BF16
+ * activation fields (32 B per unknown each) and one FP32 complex field.  Synchronises the
+ * context's stream.  Returns OK, INVALID (NULL ctx or theta, bad mode, non-finite scale),
+ * UNSUPPORTED (precision not MIXED or method not FGMRES), NOMEM or CUDA. */
+int helm6_set_cnn(helm6_ctx* ctx, const float* theta, double out_scale, int mode);
+
+/* y = the two-stage preconditioner above applied to x (DEVICE complex128 arrays as for
+ * helm6_apply_A; y may equal x).  Requires an attached network (else UNSUPPORTED). */
+int helm6_apply_stage2(helm6_ctx* ctx, const void* x, void* y);
+
+/* Trainer: the network's forward pass, mean-squared-error gradient and Adam steps
+ * (beta1 0.9, beta2 0.999, eps 1e-8) on batches of `batch` images of nz x ny x nx points,
+ * stored channel-last as DEVICE float arrays [batch][nz][ny][nx][2].  Zero padding at every
+ * image's border.  The gradient is that of the rounded network with each rounding taken
+ * as the identity (straight-through) and the GELU differentiated at its FP32 input.
+ * theta0: HOST initial parameters.  All work is on `stream` (NULL = default). */
+typedef struct helm6_cnn_trainer helm6_cnn_trainer;
+int helm6_cnn_trainer_create(helm6_cnn_trainer** out, int batch, int nz, int ny, int nx,
+                             const float* theta0, void* stream);
+/* y (DEVICE, same layout as x) = N(x).  Stream-ordered, no synchronisation. */
+int helm6_cnn_forward(helm6_cnn_trainer* tr, const float* x, float* y);
+/* grad (DEVICE, HELM6_CNN_NPARAMS floats) = d/dtheta mean((N(x) - target)^2) over every
+ * element; *loss (HOST, nullable) = that mean (then the call synchronises). */
+int helm6_cnn_gradient(helm6_cnn_trainer* tr, const float* x, const float* target, float* grad,
+                       double* loss);
+/* One Adam step of learning rate lr on that gradient; *loss (nullable) as above. */
+int helm6_cnn_train_step(helm6_cnn_trainer* tr, const float* x, const float* target, float lr,
+                         double* loss);
+/* Copy the current FP32 parameters to theta (HOST, HELM6_CNN_NPARAMS floats). */
+int helm6_cnn_get_params(helm6_cnn_trainer* tr, float* theta);
+void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr);
 
 /* Release the workspace and the context (NULL is allowed).  Synchronises its stream. */
 void helm6_destroy(helm6_ctx* ctx);

@@ -58,6 +58,14 @@ struct helm6_ctx {
   int* status = nullptr;
   double* pinned = nullptr;  // host-pinned readback slots
   cudaEvent_t step_ev[2] = {nullptr, nullptr};  // Arnoldi step completion (alternating)
+  // learned second stage (helm6_set_cnn)
+  CnnNet cnn;
+  int cnn_mode = HELM6_CNN_OFF;
+  float cnn_scale = 0.f;
+  float* cnn_t = nullptr;                          // u - A A_p^{-1} u, planar FP32
+  uint16_t *cnn_a0 = nullptr, *cnn_a1 = nullptr;   // BF16 activations, 16 per point
+  double* cnn_ss = nullptr;                        // ||u - A A_p^{-1} u||^2
+  double cyc_rate[3] = {1.0, 1.0, 1.0};            // per-iteration reduction of mixed cycles 0-2
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
   struct Pending {
@@ -311,6 +319,20 @@ void precond32(helm6_ctx* c, const float* in, float* out) {
   precond<float>(c, in, out, c->tA32, c->tB32, c->cw32, c->Vx32, c->Wx32, c->Vy32, c->Wy32);
 }
 
+// Two-stage preconditioner: out = A_p^{-1} in + c s N((in - A A_p^{-1} in) / s).
+void precond_cnn32(helm6_ctx* c, const float* in, float* out) {
+  precond32(c, in, out);
+  cudaEvent_t e = prof_start(c);
+  int nb = 0;
+  launch_stencil<float>(c->g, c->coef, out, c->cnn_t, in, nullptr, 1, c->spart, &nb, c->stream);
+  launch_reduce_sum(c->spart, nb, c->cnn_ss, c->stream);
+  cnn_apply_field(c->cnn, c->g.mz, c->g.my, c->g.mx, c->cnn_t, c->cnn_ss, c->cnn_a0, c->cnn_a1, c->cnn_scale, out,
+                  c->stream);
+  // stencil pass (2 fields in, 1 out) and the four layers (2, 16, 16, 16 channels in; 16,
+  // 16, 16 out in BF16; the last layer updates z in place)
+  prof_stop(c, HELM6_PH_CNN, e, (double)c->g.N * (24.0 + 8.0 + 3 * 32.0 + 32.0 + 3 * 32.0 + 16.0));
+}
+
 // ---- norms ----
 template <typename T>
 int norm2(helm6_ctx* c, const T* x, double* out) {
@@ -491,6 +513,17 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
 }
 
 // MIXED: FP64 refinement around FP32 FGMRES with the FP32 preconditioner.
+// Whether inner cycle `cyc` of a mixed solve uses the learned stage: ON always; AUTO uses
+// it in cycles 0 and 1, not in cycle 2, and afterwards keeps whichever of cycles 1 (with)
+// and 2 (without) reduced the true residual more per iteration.
+bool cnn_cycle(const helm6_ctx* c, int cyc) {
+  if (c->cnn_mode == HELM6_CNN_ON) return true;
+  if (c->cnn_mode != HELM6_CNN_AUTO) return false;
+  if (cyc < 2) return true;
+  if (cyc == 2) return false;
+  return c->cyc_rate[1] < c->cyc_rate[2];
+}
+
 int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {
   double beta;
   int rc = residual64(c, &beta);
@@ -498,6 +531,7 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
   push_hist(st, beta / normF);
   int iters = 0;
   const double inner = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-5;
+  int cyc = 0;
   while (true) {
     if (!std::isfinite(beta)) return HELM6_NONFINITE;
     if (beta <= tol * normF) return HELM6_OK;
@@ -507,11 +541,14 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     int k = 0;
     double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true, precond32,
-                        c->coef, &k, &b0, st);
+    const bool use_cnn = cnn_cycle(c, cyc);
+    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
+                        use_cnn ? precond_cnn32 : precond32, c->coef, &k, &b0, st);
     if (rc) return rc;
+    if (st && use_cnn) st->cnn_cycles++;
     fix_hist(st, h0, beta / normF);
     iters += k;
+    const double beta_in = beta;
     if (k > 0) {
       launch_tri_mul(c->Tm, c->mrest, k, c->yv, c->qv, c->stream);
       launch_lincomb<float, double>(c->Z32, 2 * c->g.N, k, c->qv, beta, c->U64, c->g.N, 1, c->stream);
@@ -524,6 +561,9 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
       const int cs = check_status(c);
       if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
     }
+    // per-iteration reduction of this cycle (for the AUTO choice of the learned stage)
+    if (cyc < 3) c->cyc_rate[cyc] = (k > 0 && beta_in > 0) ? std::pow(beta / beta_in, 1.0 / k) : 1.0;
+    ++cyc;
   }
 }
 
@@ -598,6 +638,7 @@ void helm6_destroy(helm6_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
   for (cudaEvent_t e : c->step_ev)
     if (e) cudaEventDestroy(e);
@@ -781,6 +822,53 @@ int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
     precond32(c, c->w32, c->zt32);
     launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
   }
+  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  CK(cudaGetLastError());
+  const int st = check_status(c);
+  return (st == HELM6_BREAKDOWN || st < 0) ? st : HELM6_OK;
+}
+
+int helm6_set_cnn(helm6_ctx* c, const float* theta, double out_scale, int mode) {
+  if (!c) return HELM6_ERR_INVALID;
+  if (mode == HELM6_CNN_OFF) {
+    c->cnn_mode = HELM6_CNN_OFF;
+    return HELM6_OK;
+  }
+  if (mode != HELM6_CNN_ON && mode != HELM6_CNN_AUTO) return HELM6_ERR_INVALID;
+  if (!theta || !std::isfinite(out_scale)) return HELM6_ERR_INVALID;
+  if (c->opts.precision != HELM6_MIXED || c->opts.method != HELM6_FGMRES) return HELM6_ERR_UNSUPPORTED;
+  cudaStream_t s = c->stream;
+  if (s) CK(cudaStreamSynchronize(s)); else CK(cudaDeviceSynchronize());
+  if (!c->cnn.theta) {
+    if (cnn_alloc(c->cnn) != HELM6_OK) {
+      cnn_free(c->cnn);
+      return HELM6_ERR_NOMEM;
+    }
+    const size_t N = (size_t)c->g.N;
+    int rc;
+    if ((rc = dalloc(c, &c->cnn_t, 2 * N)) || (rc = dalloc(c, &c->cnn_a0, 16 * N)) ||
+        (rc = dalloc(c, &c->cnn_a1, 16 * N)) || (rc = dalloc(c, &c->cnn_ss, 1)))
+      return rc;
+  }
+  CK(cudaMemcpy(c->cnn.theta, theta, sizeof(float) * HELM6_CNN_NPARAMS, cudaMemcpyHostToDevice));
+  cnn_prepare(c->cnn, s);
+  if (s) CK(cudaStreamSynchronize(s)); else CK(cudaDeviceSynchronize());
+  c->cnn_scale = (float)out_scale;
+  c->cnn_mode = mode;
+  return HELM6_OK;
+}
+
+int helm6_apply_stage2(helm6_ctx* c, const void* x, void* y) {
+  if (!c || !x || !y) return HELM6_ERR_INVALID;
+  if (c->cnn_mode == HELM6_CNN_OFF || !c->cnn.theta) return HELM6_ERR_UNSUPPORTED;
+  cudaStream_t s = c->stream;
+  const int64_t N = c->g.N;
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
+  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  launch_convert<double, float>(c->R64, c->w32, N, 1.0, s);
+  precond_cnn32(c, c->w32, c->zt32);
+  launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
   launch_planar_to_interleaved(c->E64, (double*)y, N, s);
   CK(cudaGetLastError());
   const int st = check_status(c);

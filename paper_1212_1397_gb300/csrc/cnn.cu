@@ -1,0 +1,708 @@
+// Learned second preconditioner stage: a small 3D convolutional network N applied after
+// the direct second-order preconditioner M (Eq. 3DAP) inside flexible GMRES,
+//
+//     z = M^-1 u + c s N((u - A M^-1 u) / s),   s = sqrt(mean |u - A M^-1 u|^2),
+//
+// with A the sixth-order operator (Eq. scheme).  The paper has no such stage.
+//
+// Network: 4 layers of zero-padded 3x3x3 cross-correlation, channels 2-16-16-16-2, bias,
+// GELU x Phi(x) after layers 1-3.  Channel 0/1 = real/imaginary part.  Parameters are one
+// flat FP32 vector (per layer W[c_out][c_in][dz][dy][dx], then b[c_out]); the kernels use
+// BF16-rounded weights, BF16 activations between layers, FP32 accumulation, FP32 biases.
+//
+// Kernels (SIMT, one output point per thread, 32x4x2-point tiles with the input halo and
+// all taps of a layer staged in shared memory as FP32):
+//   conv_kernel   forward layer; also the input gradient (the transpose of a zero-padded
+//                 correlation is the correlation with the flipped, channel-transposed taps)
+//   wgrad_kernel  weight and bias gradients, block partials over persistent tiles
+//   mse_kernel, adam_kernel, prep_kernel (BF16 taps in both layouts from the master vector)
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "helm6_internal.h"
+
+namespace helm6 {
+
+namespace {
+
+constexpr int TXc = 32, TYc = 4, TZc = 2, NT = TXc * TYc * TZc;  // output tile, threads per block
+constexpr int HX = TXc + 2, HY = TYc + 2, HZ = TZc + 2, HP = HX * HY * HZ;
+constexpr int NL = 4;
+// channels entering layer l (l = 0..3) and leaving the last one (l = 4)
+__host__ __device__ constexpr int ch(int l) { return (l == 0 || l == NL) ? 2 : 16; }
+
+// halo floats per point (16 channels padded to 20: conflict-free 16-byte shared loads)
+template <int C>
+struct PStride {
+  static constexpr int v = (C == 16) ? 20 : C;
+};
+
+enum { IN_F32 = 0, IN_BF16 = 1, IN_PLANAR = 2 };
+enum { OUT_HIDDEN = 0, OUT_F32 = 1, OUT_FIELD = 2, OUT_GRAD = 3 };
+
+struct ConvArgs {
+  int nb, nz, ny, nx;  // images and their size (x fastest, channel-last)
+  int tx, ty, tz;      // tiles per axis
+  const void* in;
+  int round_in;        // IN_F32: round the input to BF16 first
+  const float* w;      // taps [27][CIN][COUT]
+  const float* bias;   // [COUT] or null
+  float* pre;          // OUT_HIDDEN: FP32 pre-activations written (nullable); OUT_GRAD: read
+  void* out;
+  const double* sumsq;  // IN_PLANAR and OUT_FIELD: sum of |t|^2 over the input field
+  float out_scale;      // OUT_FIELD: c
+};
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_df(float x) {
+  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat16 lo = __float2bfloat16_rn(a), hi = __float2bfloat16_rn(b);
+  uint16_t l, h;
+  memcpy(&l, &lo, 2);
+  memcpy(&h, &hi, 2);
+  return (uint32_t)l | ((uint32_t)h << 16);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+
+// tile index -> (image, z0, y0, x0) of the output tile
+__device__ __forceinline__ void tile_origin(const ConvArgs& a, int64_t tile, int& img, int& z0, int& y0, int& x0) {
+  const int bx = (int)(tile % a.tx);
+  tile /= a.tx;
+  const int by = (int)(tile % a.ty);
+  tile /= a.ty;
+  const int bz = (int)(tile % a.tz);
+  img = (int)(tile / a.tz);
+  x0 = bx * TXc;
+  y0 = by * TYc;
+  z0 = bz * TZc;
+}
+
+__device__ __forceinline__ float plane_scale(const ConvArgs& a, int64_t npts) {
+  const double ss = *a.sumsq;
+  return ss > 0.0 ? (float)(1.0 / sqrt(ss / (double)npts)) : 0.f;
+}
+
+// Stage the input halo of one tile into sx (HP points x PStride<CIN> floats).
+template <int CIN, int IN>
+__device__ __forceinline__ void load_halo(const ConvArgs& a, int img, int z0, int y0, int x0, float sc,
+                                          float* sx) {
+  constexpr int PS = PStride<CIN>::v;
+  const int64_t npts = (int64_t)a.nb * a.nz * a.ny * a.nx;
+  for (int i = threadIdx.x; i < HP; i += NT) {
+    const int hx = i % HX, r = i / HX, hy = r % HY, hz = r / HY;
+    const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+    const bool ok = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+    const int64_t p = (((int64_t)img * a.nz + gz) * a.ny + gy) * a.nx + gx;
+    float* d = sx + i * PS;
+    if constexpr (IN == IN_PLANAR) {
+      const float* f = (const float*)a.in;
+      d[0] = ok ? bf16r(f[p] * sc) : 0.f;
+      d[1] = ok ? bf16r(f[npts + p] * sc) : 0.f;
+    } else if constexpr (IN == IN_BF16) {
+      static_assert(IN != IN_BF16 || CIN == 16, "BF16 activations carry 16 channels");
+      uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+      if (ok) {
+        const uint4* s = (const uint4*)a.in + 2 * p;
+        q0 = s[0];
+        q1 = s[1];
+      }
+      float4* d4 = (float4*)d;
+      d4[0] = make_float4(bf16_lo(q0.x), bf16_hi(q0.x), bf16_lo(q0.y), bf16_hi(q0.y));
+      d4[1] = make_float4(bf16_lo(q0.z), bf16_hi(q0.z), bf16_lo(q0.w), bf16_hi(q0.w));
+      d4[2] = make_float4(bf16_lo(q1.x), bf16_hi(q1.x), bf16_lo(q1.y), bf16_hi(q1.y));
+      d4[3] = make_float4(bf16_lo(q1.z), bf16_hi(q1.z), bf16_lo(q1.w), bf16_hi(q1.w));
+    } else {
+      const float* f = (const float*)a.in + p * CIN;
+      if constexpr (CIN == 16) {
+        float4* d4 = (float4*)d;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float4 v = ok ? ((const float4*)f)[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+          if (a.round_in) v = make_float4(bf16r(v.x), bf16r(v.y), bf16r(v.z), bf16r(v.w));
+          d4[c] = v;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CIN; ++c) {
+          const float v = ok ? f[c] : 0.f;
+          d[c] = a.round_in ? bf16r(v) : v;
+        }
+      }
+    }
+  }
+}
+
+template <int CIN, int COUT, int IN, int OUT>
+__global__ void __launch_bounds__(NT, 2) conv_kernel(ConvArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int PS = PStride<CIN>::v;
+  float* sw = smem;                  // 27 * CIN * COUT
+  float* sx = smem + 27 * CIN * COUT;  // HP * PS (27*CIN*COUT is a multiple of 4)
+  const int tid = threadIdx.x;
+  const int64_t npts = (int64_t)a.nb * a.nz * a.ny * a.nx;
+  for (int i = tid; i < 27 * CIN * COUT; i += NT) sw[i] = a.w[i];
+  int img, z0, y0, x0;
+  tile_origin(a, blockIdx.x, img, z0, y0, x0);
+  const float sc = (IN == IN_PLANAR) ? plane_scale(a, npts) : 1.f;
+  load_halo<CIN, IN>(a, img, z0, y0, x0, sc, sx);
+  __syncthreads();
+
+  const int lx = tid % TXc, ly = (tid / TXc) % TYc, lz = tid / (TXc * TYc);
+  float acc[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc[o] = a.bias ? a.bias[o] : 0.f;
+  const int base = (lz * HY + ly) * HX + lx;
+#pragma unroll 1
+  for (int t = 0; t < 27; ++t) {
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+    const float* xp = sx + (base + (dz * HY + dy) * HX + dx) * PS;
+    const float* wp = sw + t * CIN * COUT;
+    float xv[CIN];
+    if constexpr (CIN == 16) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float4 v = ((const float4*)xp)[c];
+        xv[4 * c] = v.x;
+        xv[4 * c + 1] = v.y;
+        xv[4 * c + 2] = v.z;
+        xv[4 * c + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CIN; ++c) xv[c] = xp[c];
+    }
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) {
+      if constexpr (COUT == 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 w4 = ((const float4*)(wp + ci * COUT))[q];
+          acc[4 * q] = fmaf(xv[ci], w4.x, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(xv[ci], w4.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(xv[ci], w4.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(xv[ci], w4.w, acc[4 * q + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) acc[o] = fmaf(xv[ci], wp[ci * COUT + o], acc[o]);
+      }
+    }
+  }
+
+  const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+  if (gx >= a.nx || gy >= a.ny || gz >= a.nz) return;
+  const int64_t p = (((int64_t)img * a.nz + gz) * a.ny + gy) * a.nx + gx;
+  if constexpr (OUT == OUT_HIDDEN) {
+    static_assert(OUT != OUT_HIDDEN || COUT == 16, "hidden layers have 16 channels");
+    if (a.pre) {
+      float4* pr = (float4*)(a.pre + p * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) pr[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pk[q] = pack_bf16(gelu_f(acc[2 * q]), gelu_f(acc[2 * q + 1]));
+    uint4* o4 = (uint4*)a.out + 2 * p;
+    o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  } else if constexpr (OUT == OUT_F32) {
+    float* o = (float*)a.out + p * COUT;
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) o[c] = acc[c];
+  } else if constexpr (OUT == OUT_GRAD) {
+    const float* pr = a.pre + p * COUT;
+    float* o = (float*)a.out + p * COUT;
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) o[c] = acc[c] * gelu_df(pr[c]);
+  } else {  // OUT_FIELD: z += c s y on the planar complex field
+    static_assert(OUT != OUT_FIELD || COUT == 2, "the field output has 2 channels");
+    const double ss = *a.sumsq;
+    if (!(ss > 0.0)) return;
+    const float cs = a.out_scale * (float)sqrt(ss / (double)npts);
+    float* z = (float*)a.out;
+    z[p] = fmaf(cs, acc[0], z[p]);
+    z[npts + p] = fmaf(cs, acc[1 % COUT], z[npts + p]);
+  }
+}
+
+// Weight and bias gradients of one layer: dW[t][ci][co] = sum_p in[p + d_t][ci] g[p][co],
+// db[co] = sum_p g[p][co].  Persistent blocks over tiles, one partial row per block.
+template <int CIN, int COUT, int IN>
+__global__ void __launch_bounds__(NT) wgrad_kernel(ConvArgs a, const float* __restrict__ g,
+                                                   float* __restrict__ partial, int64_t ntiles) {
+  extern __shared__ __align__(16) float smem[];
+  constexpr int PS = PStride<CIN>::v;
+  constexpr int E = 27 * CIN * COUT;
+  constexpr int KE = (E + NT - 1) / NT;
+  float* sx = smem;            // HP * PS
+  float* sg = smem + HP * PS;  // NT * COUT
+  const int tid = threadIdx.x;
+  int xo[KE], go[KE];
+  float acc[KE];
+#pragma unroll
+  for (int k = 0; k < KE; ++k) {
+    const int e = (tid + k * NT < E) ? tid + k * NT : 0;  // entries past E read entry 0, unused
+    const int t = e / (CIN * COUT), r = e % (CIN * COUT);
+    const int ci = r / COUT, co = r % COUT;
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+    xo[k] = ((dz * HY + dy) * HX + dx) * PS + ci;
+    go[k] = co;
+    acc[k] = 0.f;
+  }
+  float bacc = 0.f;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int img, z0, y0, x0;
+    tile_origin(a, tile, img, z0, y0, x0);
+    load_halo<CIN, IN>(a, img, z0, y0, x0, 1.f, sx);
+    {
+      const int lx = tid % TXc, ly = (tid / TXc) % TYc, lz = tid / (TXc * TYc);
+      const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+      const bool ok = gx < a.nx && gy < a.ny && gz < a.nz;
+      const int64_t p = (((int64_t)img * a.nz + gz) * a.ny + gy) * a.nx + gx;
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) sg[tid * COUT + c] = ok ? g[p * COUT + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int q = 0; q < NT; ++q) {
+      const int hb = ((q / (TXc * TYc)) * HY + (q / TXc) % TYc) * HX + q % TXc;
+      const float* xq = sx + hb * PS;
+      const float* gq = sg + q * COUT;
+#pragma unroll
+      for (int k = 0; k < KE; ++k)
+        if (KE * NT == E || tid + k * NT < E) acc[k] = fmaf(xq[xo[k]], gq[go[k]], acc[k]);
+    }
+    if (tid < COUT)
+      for (int q = 0; q < NT; ++q) bacc += sg[q * COUT + tid];
+    __syncthreads();
+  }
+  float* row = partial + (int64_t)blockIdx.x * (E + COUT);
+#pragma unroll
+  for (int k = 0; k < KE; ++k)
+    if (tid + k * NT < E) row[tid + k * NT] = acc[k];
+  if (tid < COUT) row[E + tid] = bacc;
+}
+
+// grad[flat] = sum over blocks of the partial rows, entries mapped from the kernel's
+// [t][ci][co] order to the parameter vector's [co][ci][t] order; biases follow.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ partial, int nblk, int cin, int cout,
+                                    float* __restrict__ grad_w, float* __restrict__ grad_b) {
+  const int E = 27 * cin * cout;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E + cout) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * (E + cout) + e];
+  if (e < E) {
+    const int t = e / (cin * cout), r = e % (cin * cout), ci = r / cout, co = r % cout;
+    grad_w[(co * cin + ci) * 27 + t] = (float)s;
+  } else {
+    grad_b[e - E] = (float)s;
+  }
+}
+
+// g = 2 (y - t) / n and block partial sums of (y - t)^2.
+__global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t n,
+                           float* __restrict__ g, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const float sc = (float)(2.0 / (double)n);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    g[i] = sc * d;
+    acc += (double)d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  }
+}
+
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8) with bias corrections c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, int n, float lr, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+struct LayerDims {
+  int cin[NL], cout[NL], toff[NL], boff[NL], woff[NL];
+};
+
+__host__ __device__ inline LayerDims layer_dims() {
+  LayerDims d{};
+  int t = 0, w = 0;
+  for (int l = 0; l < NL; ++l) {
+    d.cin[l] = ch(l);
+    d.cout[l] = ch(l + 1);
+    d.toff[l] = t;
+    d.boff[l] = t + 27 * ch(l) * ch(l + 1);
+    d.woff[l] = w;
+    t = d.boff[l] + ch(l + 1);
+    w += 27 * ch(l) * ch(l + 1);
+  }
+  return d;
+}
+
+// BF16-rounded taps of every layer in the forward layout [t][ci][co] (wf) and in the
+// input-gradient layout [t'][co][ci] with t' = 26 - t (wb).
+__global__ void prep_kernel(const float* __restrict__ theta, float* __restrict__ wf, float* __restrict__ wb) {
+  const LayerDims d = layer_dims();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int l = 0; l < NL; ++l) {
+    const int n = 27 * d.cin[l] * d.cout[l];
+    if (i >= n) continue;
+    const int ci_n = d.cin[l], co_n = d.cout[l];
+    // forward entry i = (t * cin + ci) * cout + co
+    {
+      const int t = i / (ci_n * co_n), r = i % (ci_n * co_n), ci = r / co_n, co = r % co_n;
+      wf[d.woff[l] + i] = bf16r(theta[d.toff[l] + (co * ci_n + ci) * 27 + t]);
+    }
+    // input-gradient entry i = (t' * cout + co) * cin + ci
+    {
+      const int t2 = i / (ci_n * co_n), r = i % (ci_n * co_n), co = r / ci_n, ci = r % ci_n;
+      wb[d.woff[l] + i] = bf16r(theta[d.toff[l] + (co * ci_n + ci) * 27 + (26 - t2)]);
+    }
+  }
+}
+
+constexpr int kWeights = 27 * (2 * 16 + 16 * 16 + 16 * 16 + 16 * 2);  // 15552 taps
+static_assert(kWeights + 16 + 16 + 16 + 2 == HELM6_CNN_NPARAMS, "parameter count");
+
+template <int CIN, int COUT>
+constexpr size_t conv_smem() {
+  return sizeof(float) * (27 * CIN * COUT + HP * PStride<CIN>::v);
+}
+template <int CIN, int COUT>
+constexpr size_t wgrad_smem() {
+  return sizeof(float) * (HP * PStride<CIN>::v + NT * COUT);
+}
+
+template <int CIN, int COUT, int IN, int OUT>
+cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
+  const size_t sm = conv_smem<CIN, COUT>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, IN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t tiles = (int64_t)a.tx * a.ty * a.tz * a.nb;
+  note_launch();
+  conv_kernel<CIN, COUT, IN, OUT><<<(unsigned)tiles, NT, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int IN>
+cudaError_t launch_wgrad(const ConvArgs& a, const float* g, float* partial, int nblk, cudaStream_t s) {
+  const size_t sm = wgrad_smem<CIN, COUT>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(wgrad_kernel<CIN, COUT, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int64_t tiles = (int64_t)a.tx * a.ty * a.tz * a.nb;
+  note_launch();
+  wgrad_kernel<CIN, COUT, IN><<<nblk, NT, sm, s>>>(a, g, partial, tiles);
+  return cudaGetLastError();
+}
+
+ConvArgs vol_args(int nb, int nz, int ny, int nx) {
+  ConvArgs a{};
+  a.nb = nb;
+  a.nz = nz;
+  a.ny = ny;
+  a.nx = nx;
+  a.tx = (nx + TXc - 1) / TXc;
+  a.ty = (ny + TYc - 1) / TYc;
+  a.tz = (nz + TZc - 1) / TZc;
+  return a;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Library-internal interface (helm6_internal.h)
+// ---------------------------------------------------------------------------------------
+
+int cnn_alloc(CnnNet& net) {
+  if (cudaMalloc((void**)&net.theta, sizeof(float) * HELM6_CNN_NPARAMS) != cudaSuccess) return HELM6_ERR_NOMEM;
+  if (cudaMalloc((void**)&net.wf, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
+  if (cudaMalloc((void**)&net.wb, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
+  return HELM6_OK;
+}
+
+void cnn_free(CnnNet& net) {
+  cudaFree(net.theta);
+  cudaFree(net.wf);
+  cudaFree(net.wb);
+  net = CnnNet{};
+}
+
+void cnn_prepare(const CnnNet& net, cudaStream_t s) {
+  note_launch();
+  prep_kernel<<<(27 * 16 * 16 + 255) / 256, 256, 0, s>>>(net.theta, net.wf, net.wb);
+}
+
+int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq, uint16_t* act0,
+                    uint16_t* act1, float out_scale, float* z, cudaStream_t s) {
+  const LayerDims d = layer_dims();
+  ConvArgs a = vol_args(1, nz, ny, nx);
+  a.sumsq = sumsq;
+  a.out_scale = out_scale;
+  a.in = t;
+  a.w = net.wf + d.woff[0];
+  a.bias = net.theta + d.boff[0];
+  a.out = act0;
+  if ((launch_conv<2, 16, IN_PLANAR, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
+  a.in = act0;
+  a.w = net.wf + d.woff[1];
+  a.bias = net.theta + d.boff[1];
+  a.out = act1;
+  if ((launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
+  a.in = act1;
+  a.w = net.wf + d.woff[2];
+  a.bias = net.theta + d.boff[2];
+  a.out = act0;
+  if ((launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
+  a.in = act0;
+  a.w = net.wf + d.woff[3];
+  a.bias = net.theta + d.boff[3];
+  a.out = z;
+  if ((launch_conv<16, 2, IN_BF16, OUT_FIELD>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
+  return HELM6_OK;
+}
+
+}  // namespace helm6
+
+// ---------------------------------------------------------------------------------------
+// C-ABI: the trainer
+// ---------------------------------------------------------------------------------------
+
+using namespace helm6;
+
+struct helm6_cnn_trainer {
+  int nb = 0, nz = 0, ny = 0, nx = 0;
+  int64_t npts = 0;
+  cudaStream_t stream = nullptr;
+  CnnNet net;
+  float *m = nullptr, *v = nullptr, *grad = nullptr;
+  float *pre[3] = {nullptr, nullptr, nullptr};   // FP32 pre-activations of layers 1-3
+  uint16_t* act[3] = {nullptr, nullptr, nullptr};  // BF16 activations after layers 1-3
+  float *y = nullptr, *g4 = nullptr, *ga = nullptr, *gb = nullptr;
+  float* partial = nullptr;
+  double *lpart = nullptr, *loss = nullptr;
+  double* pinned = nullptr;
+  int nblk = 0, nloss = 0;
+  long long step = 0;
+};
+
+namespace {
+
+int tr_forward(helm6_cnn_trainer* tr, const float* x) {
+  const LayerDims d = layer_dims();
+  ConvArgs a = vol_args(tr->nb, tr->nz, tr->ny, tr->nx);
+  cudaStream_t s = tr->stream;
+  a.in = x;
+  a.round_in = 1;
+  a.w = tr->net.wf + d.woff[0];
+  a.bias = tr->net.theta + d.boff[0];
+  a.pre = tr->pre[0];
+  a.out = tr->act[0];
+  if (launch_conv<2, 16, IN_F32, OUT_HIDDEN>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  a.round_in = 0;
+  for (int l = 1; l < 3; ++l) {
+    a.in = tr->act[l - 1];
+    a.w = tr->net.wf + d.woff[l];
+    a.bias = tr->net.theta + d.boff[l];
+    a.pre = tr->pre[l];
+    a.out = tr->act[l];
+    if (launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  }
+  a.in = tr->act[2];
+  a.w = tr->net.wf + d.woff[3];
+  a.bias = tr->net.theta + d.boff[3];
+  a.pre = nullptr;
+  a.out = tr->y;
+  if (launch_conv<16, 2, IN_BF16, OUT_F32>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  return HELM6_OK;
+}
+
+// loss, g4 = dL/dy, then every layer's weight/bias gradient into tr->grad
+int tr_backward(helm6_cnn_trainer* tr, const float* x, const float* target) {
+  const LayerDims d = layer_dims();
+  cudaStream_t s = tr->stream;
+  const int64_t n = tr->npts * 2;
+  note_launch(2);
+  mse_kernel<<<tr->nloss, 256, 0, s>>>(tr->y, target, n, tr->g4, tr->lpart);
+  launch_reduce_sum(tr->lpart, tr->nloss, tr->loss, s);
+  ConvArgs a = vol_args(tr->nb, tr->nz, tr->ny, tr->nx);
+  auto reduce = [&](int l) {
+    note_launch();
+    const int ne = 27 * d.cin[l] * d.cout[l] + d.cout[l];
+    wgrad_reduce_kernel<<<(ne + 255) / 256, 256, 0, s>>>(tr->partial, tr->nblk, d.cin[l], d.cout[l],
+                                                         tr->grad + d.toff[l], tr->grad + d.boff[l]);
+  };
+  // layer 4: dW from act3 and g4; g3 = (W4^T * g4) gelu'(pre3)
+  a.in = tr->act[2];
+  if (launch_wgrad<16, 2, IN_BF16>(a, tr->g4, tr->partial, tr->nblk, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  reduce(3);
+  a.in = tr->g4;
+  a.round_in = 0;
+  a.w = tr->net.wb + d.woff[3];
+  a.bias = nullptr;
+  a.pre = tr->pre[2];
+  a.out = tr->ga;
+  if (launch_conv<2, 16, IN_F32, OUT_GRAD>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  // layers 3 and 2
+  float* gcur = tr->ga;
+  float* gnext = tr->gb;
+  for (int l = 2; l >= 1; --l) {
+    a.in = tr->act[l - 1];
+    if (launch_wgrad<16, 16, IN_BF16>(a, gcur, tr->partial, tr->nblk, s) != cudaSuccess) return HELM6_ERR_CUDA;
+    reduce(l);
+    a.in = gcur;
+    a.w = tr->net.wb + d.woff[l];
+    a.pre = tr->pre[l - 1];
+    a.out = gnext;
+    if (launch_conv<16, 16, IN_F32, OUT_GRAD>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+    std::swap(gcur, gnext);
+  }
+  // layer 1: dW from the BF16-rounded input and g1
+  a.in = x;
+  a.round_in = 1;
+  if (launch_wgrad<2, 16, IN_F32>(a, gcur, tr->partial, tr->nblk, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  reduce(0);
+  return HELM6_OK;
+}
+
+int read_loss(helm6_cnn_trainer* tr, double* loss) {
+  if (!loss) return HELM6_OK;
+  if (cudaMemcpyAsync(tr->pinned, tr->loss, sizeof(double), cudaMemcpyDeviceToHost, tr->stream) != cudaSuccess)
+    return HELM6_ERR_CUDA;
+  if (cudaStreamSynchronize(tr->stream) != cudaSuccess) return HELM6_ERR_CUDA;
+  *loss = tr->pinned[0] / (double)(tr->npts * 2);
+  return HELM6_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr) {
+  if (!tr) return;
+  if (tr->stream) cudaStreamSynchronize(tr->stream);
+  else cudaDeviceSynchronize();
+  cnn_free(tr->net);
+  void* bufs[] = {tr->m, tr->v, tr->grad, tr->pre[0], tr->pre[1], tr->pre[2], tr->act[0], tr->act[1],
+                  tr->act[2], tr->y, tr->g4, tr->ga, tr->gb, tr->partial, tr->lpart, tr->loss};
+  for (void* p : bufs) cudaFree(p);
+  if (tr->pinned) cudaFreeHost(tr->pinned);
+  delete tr;
+}
+
+int helm6_cnn_trainer_create(helm6_cnn_trainer** out, int batch, int nz, int ny, int nx, const float* theta0,
+                             void* stream) {
+  if (!out || !theta0 || batch < 1 || nz < 1 || ny < 1 || nx < 1) return HELM6_ERR_INVALID;
+  *out = nullptr;
+  const int64_t npts = (int64_t)batch * nz * ny * nx;
+  const int64_t tiles = (int64_t)((nx + TXc - 1) / TXc) * ((ny + TYc - 1) / TYc) * ((nz + TZc - 1) / TZc) * batch;
+  if (tiles > INT32_MAX || npts > ((int64_t)1 << 34)) return HELM6_ERR_INVALID;
+  auto* tr = new helm6_cnn_trainer();
+  tr->nb = batch;
+  tr->nz = nz;
+  tr->ny = ny;
+  tr->nx = nx;
+  tr->npts = npts;
+  tr->stream = (cudaStream_t)stream;
+  tr->nblk = (int)std::min<int64_t>(tiles, 2 * (int64_t)device_sm_count());
+  tr->nloss = 4 * device_sm_count();
+  auto fail = [&](int rc) {
+    helm6_cnn_trainer_destroy(tr);
+    return rc;
+  };
+  auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+  const size_t np = HELM6_CNN_NPARAMS;
+  if (cnn_alloc(tr->net) != HELM6_OK) return fail(HELM6_ERR_NOMEM);
+  bool ok = al((void**)&tr->m, np * 4) && al((void**)&tr->v, np * 4) && al((void**)&tr->grad, np * 4) &&
+            al((void**)&tr->y, npts * 8) && al((void**)&tr->g4, npts * 8) && al((void**)&tr->ga, npts * 64) &&
+            al((void**)&tr->gb, npts * 64) && al((void**)&tr->partial, (size_t)tr->nblk * (6912 + 16) * 4) &&
+            al((void**)&tr->lpart, (size_t)tr->nloss * 8) && al((void**)&tr->loss, 8);
+  for (int l = 0; l < 3 && ok; ++l) ok = al((void**)&tr->pre[l], npts * 64) && al((void**)&tr->act[l], npts * 32);
+  if (!ok) return fail(HELM6_ERR_NOMEM);
+  if (cudaMallocHost((void**)&tr->pinned, 64) != cudaSuccess) return fail(HELM6_ERR_NOMEM);
+  if (cudaMemcpy(tr->net.theta, theta0, np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(tr->m, 0, np * 4) != cudaSuccess || cudaMemset(tr->v, 0, np * 4) != cudaSuccess ||
+      cudaMemset(tr->grad, 0, np * 4) != cudaSuccess)
+    return fail(HELM6_ERR_CUDA);
+  cnn_prepare(tr->net, tr->stream);
+  if (cudaStreamSynchronize(tr->stream) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+  *out = tr;
+  return HELM6_OK;
+}
+
+int helm6_cnn_forward(helm6_cnn_trainer* tr, const float* x, float* y) {
+  if (!tr || !x || !y) return HELM6_ERR_INVALID;
+  int rc = tr_forward(tr, x);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(y, tr->y, tr->npts * 8, cudaMemcpyDeviceToDevice, tr->stream) != cudaSuccess)
+    return HELM6_ERR_CUDA;
+  return HELM6_OK;
+}
+
+int helm6_cnn_gradient(helm6_cnn_trainer* tr, const float* x, const float* target, float* grad, double* loss) {
+  if (!tr || !x || !target || !grad) return HELM6_ERR_INVALID;
+  int rc = tr_forward(tr, x);
+  if (!rc) rc = tr_backward(tr, x, target);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(grad, tr->grad, sizeof(float) * HELM6_CNN_NPARAMS, cudaMemcpyDeviceToDevice, tr->stream) !=
+      cudaSuccess)
+    return HELM6_ERR_CUDA;
+  return read_loss(tr, loss);
+}
+
+int helm6_cnn_train_step(helm6_cnn_trainer* tr, const float* x, const float* target, float lr, double* loss) {
+  if (!tr || !x || !target || !(lr >= 0.f)) return HELM6_ERR_INVALID;
+  int rc = tr_forward(tr, x);
+  if (!rc) rc = tr_backward(tr, x, target);
+  if (rc) return rc;
+  tr->step += 1;
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)tr->step));
+  const float c2 = (float)(1.0 - std::pow(0.999, (double)tr->step));
+  note_launch();
+  adam_kernel<<<(HELM6_CNN_NPARAMS + 255) / 256, 256, 0, tr->stream>>>(tr->net.theta, tr->m, tr->v, tr->grad,
+                                                                     HELM6_CNN_NPARAMS, lr, c1, c2);
+  cnn_prepare(tr->net, tr->stream);
+  if (cudaGetLastError() != cudaSuccess) return HELM6_ERR_CUDA;
+  return read_loss(tr, loss);
+}
+
+int helm6_cnn_get_params(helm6_cnn_trainer* tr, float* theta) {
+  if (!tr || !theta) return HELM6_ERR_INVALID;
+  if (cudaMemcpyAsync(theta, tr->net.theta, sizeof(float) * HELM6_CNN_NPARAMS, cudaMemcpyDeviceToHost,
+                      tr->stream) != cudaSuccess ||
+      cudaStreamSynchronize(tr->stream) != cudaSuccess)
+    return HELM6_ERR_CUDA;
+  return HELM6_OK;
+}
+
+}  // extern "C"

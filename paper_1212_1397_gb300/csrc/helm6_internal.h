@@ -191,6 +191,22 @@ void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R
                       double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s);
 void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s);
 
+// Learned second preconditioner stage (cnn.cu).  theta: HELM6_CNN_NPARAMS master
+// parameters; wf / wb: BF16-rounded taps of every layer in the forward layout
+// [t][c_in][c_out] and in the input-gradient layout [26 - t][c_out][c_in].
+struct CnnNet {
+  float* theta = nullptr;
+  float* wf = nullptr;
+  float* wb = nullptr;
+};
+int cnn_alloc(CnnNet& net);
+void cnn_free(CnnNet& net);
+void cnn_prepare(const CnnNet& net, cudaStream_t s);  // wf, wb from theta
+// z += c s N(t / s) on planar complex FP32 fields of nz*ny*nx points, s = sqrt(*sumsq / N)
+// (z unchanged when *sumsq is 0); act0/act1: scratch of 16 BF16 per point each.
+int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq,
+                    uint16_t* act0, uint16_t* act1, float out_scale, float* z, cudaStream_t s);
+
 int device_sm_count();
 
 // Kernels launched by the library so far (process-wide counter, for measurement).

@@ -16,6 +16,8 @@ DIRICHLET, NEUMANN, SOMMERFELD = 0, 1, 2
 FP64, MIXED = 0, 1
 GMRES, FGMRES, SKS = 0, 1, 2
 MAX_HIST = 1024
+CNN_NPARAMS = 15602
+CNN_OFF, CNN_ON, CNN_AUTO = 0, 1, 2
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "DIVERGED", 3: "BREAKDOWN", 4: "NONFINITE",
           -1: "ERR_INVALID", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED"}
@@ -25,10 +27,12 @@ _FACE_CODE = {"D": DIRICHLET, "N": NEUMANN, "S": SOMMERFELD}
 # every symbol declared in include/helm6.h
 EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", "helm6_apply_Pinv",
            "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
-           "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc")
+           "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
+           "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
+           "helm6_cnn_train_step", "helm6_cnn_get_params", "helm6_cnn_trainer_destroy")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
-          "gs_update", "gs_small", "resid64", "other")
+          "gs_update", "gs_small", "resid64", "other", "cnn")
 
 
 class C64(C.Structure):
@@ -43,12 +47,12 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
                 ("relres", C.c_double), ("t_total_ms", C.c_double), ("nhist", C.c_int),
-                ("hist", C.c_double * MAX_HIST)]
+                ("hist", C.c_double * MAX_HIST), ("cnn_cycles", C.c_int)]
 
     def to_dict(self):
         return dict(iters=self.iters, outer=self.outer, status=STATUS.get(self.status, self.status),
                     relres=self.relres, t_total_ms=self.t_total_ms,
-                    history=list(self.hist[: self.nhist]))
+                    history=list(self.hist[: self.nhist]), cnn_cycles=self.cnn_cycles)
 
 
 class Profile(C.Structure):
@@ -95,6 +99,23 @@ def load(path: str = LIB_PATH):
     lib.helm6_profile_read.restype = I
     lib.helm6_residual_noalloc.argtypes = [I, D, C64, C.POINTER(C.c_int), P, P, P, P, P]
     lib.helm6_residual_noalloc.restype = I
+    F32P = C.POINTER(C.c_float)
+    lib.helm6_set_cnn.argtypes = [P, F32P, D, I]
+    lib.helm6_set_cnn.restype = I
+    lib.helm6_apply_stage2.argtypes = [P, P, P]
+    lib.helm6_apply_stage2.restype = I
+    lib.helm6_cnn_trainer_create.argtypes = [C.POINTER(P), I, I, I, I, F32P, P]
+    lib.helm6_cnn_trainer_create.restype = I
+    lib.helm6_cnn_forward.argtypes = [P, P, P]
+    lib.helm6_cnn_forward.restype = I
+    lib.helm6_cnn_gradient.argtypes = [P, P, P, P, C.POINTER(D)]
+    lib.helm6_cnn_gradient.restype = I
+    lib.helm6_cnn_train_step.argtypes = [P, P, P, C.c_float, C.POINTER(D)]
+    lib.helm6_cnn_train_step.restype = I
+    lib.helm6_cnn_get_params.argtypes = [P, F32P]
+    lib.helm6_cnn_get_params.restype = I
+    lib.helm6_cnn_trainer_destroy.argtypes = [P]
+    lib.helm6_cnn_trainer_destroy.restype = None
     lib.helm6_status_string.argtypes = [I]
     lib.helm6_status_string.restype = C.c_char_p
     _lib = lib
@@ -204,6 +225,22 @@ class Solver:
             raise Helm6Error(f"helm6_apply_Pinv: {STATUS.get(rc)}")
         return y
 
+    def set_cnn(self, theta, out_scale, mode=CNN_ON):
+        """Attach the learned second stage (theta: CNN_NPARAMS floats, host) or detach it."""
+        import numpy as np
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).ravel())
+        if th.size != CNN_NPARAMS:
+            raise ValueError(f"expected {CNN_NPARAMS} parameters, got {th.size}")
+        _check(self._lib.helm6_set_cnn(self._ctx, th.ctypes.data_as(C.POINTER(C.c_float)), float(out_scale),
+                                       int(mode)), "helm6_set_cnn")
+
+    def apply_stage2(self, x, y=None):
+        y = self.empty() if y is None else y
+        rc = _check(self._lib.helm6_apply_stage2(self._ctx, _ptr(x), _ptr(y)), "helm6_apply_stage2")
+        if rc != 0:
+            raise Helm6Error(f"helm6_apply_stage2: {STATUS.get(rc)}")
+        return y
+
     def solve(self, F, u=None, tol=1e-8, restart=30, maxit=500):
         """Solve A u = F (u in/out, zero if None).  Returns (u, stats dict)."""
         u = self.empty() if u is None else u
@@ -233,3 +270,82 @@ class Solver:
         _check(self._lib.helm6_rhs_gaussians(self._ctx, ns, cen, amps, float(sources.sigma), nptr,
                                              _ptr(F)), "helm6_rhs_gaussians")
         return F
+
+
+def _fptr(t, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Trainer:
+    """helm6_cnn_trainer: forward, MSE gradient and Adam steps of the learned stage's network
+    on batches of channel-last float32 CUDA tensors of shape (batch, nz, ny, nx, 2)."""
+
+    def __init__(self, batch, nz, ny, nx, theta0, stream=None):
+        import numpy as np
+        lib = load()
+        self._lib = lib
+        th = np.ascontiguousarray(np.asarray(theta0, dtype=np.float32).ravel())
+        if th.size != CNN_NPARAMS:
+            raise ValueError(f"expected {CNN_NPARAMS} parameters, got {th.size}")
+        s = None
+        if stream is not None:
+            s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        tr = C.c_void_p()
+        _check(lib.helm6_cnn_trainer_create(C.byref(tr), int(batch), int(nz), int(ny), int(nx),
+                                            th.ctypes.data_as(C.POINTER(C.c_float)), s),
+               "helm6_cnn_trainer_create")
+        self._tr = tr
+        self.shape = (batch, nz, ny, nx, 2)
+        self.numel = batch * nz * ny * nx * 2
+
+    def close(self):
+        if getattr(self, "_tr", None):
+            self._lib.helm6_cnn_trainer_destroy(self._tr)
+            self._tr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def forward(self, x, y=None):
+        import torch
+        y = torch.empty(self.shape, dtype=torch.float32, device="cuda") if y is None else y
+        _check(self._lib.helm6_cnn_forward(self._tr, _fptr(x, self.numel), _fptr(y, self.numel)),
+               "helm6_cnn_forward")
+        return y
+
+    def gradient(self, x, target):
+        """(loss, grad tensor of CNN_NPARAMS floats)."""
+        import torch
+        g = torch.empty(CNN_NPARAMS, dtype=torch.float32, device="cuda")
+        loss = C.c_double()
+        _check(self._lib.helm6_cnn_gradient(self._tr, _fptr(x, self.numel), _fptr(target, self.numel),
+                                            _fptr(g), C.byref(loss)), "helm6_cnn_gradient")
+        return loss.value, g
+
+    def step(self, x, target, lr, want_loss=True):
+        loss = C.c_double()
+        _check(self._lib.helm6_cnn_train_step(self._tr, _fptr(x, self.numel), _fptr(target, self.numel),
+                                              float(lr), C.byref(loss) if want_loss else None),
+               "helm6_cnn_train_step")
+        return loss.value if want_loss else None
+
+    def params(self):
+        import numpy as np
+        th = np.empty(CNN_NPARAMS, dtype=np.float32)
+        _check(self._lib.helm6_cnn_get_params(self._tr, th.ctypes.data_as(C.POINTER(C.c_float))),
+               "helm6_cnn_get_params")
+        return th
