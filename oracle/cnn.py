@@ -21,6 +21,17 @@ Network (all arrays channel-last, [batch, z, y, x, channel], x fastest):
 Weights W[l] have shape [c_out, c_in, 3, 3, 3] (tap order dz, dy, dx); the flat parameter
 vector packs, per layer in order, W (C order) then b.
 
+Training losses.  `loss_and_grad`: mean squared error against a target (the error e~ the
+stage should add).  `residual_loss_and_grad`: the residual form that makes N a local
+approximate inverse of A: with X = x_0 + i x_1 the input, Y = y_0 + i y_1 the output and
+A_h the interior 27-point operator of Eq. scheme on the patch with zero values outside it,
+
+    L = sum over interior points p of |(A_h Y - X)_p|^2 / (2 * number of interior points),
+
+interior meaning at least one point away from every face of the patch (there A_h needs no
+value outside it).  Then A (c s N(t/s)) ~ t for c = 1, so z = A_p^-1 u + s N(t/s) removes
+what the direct preconditioner left.
+
 Precision model of the GPU kernels (`bf16=True`): the network input, the weights and the
 activations after each GELU are rounded to BF16 (round to nearest, ties to even); sums
 are exact here (FP64) and FP32 on the GPU; the last layer's output and all biases stay
@@ -185,3 +196,61 @@ def stage2(theta, out_scale, u, precond, apply_A, bf16=True):
     xin = np.stack([t.real / s, t.imag / s], axis=-1)[None]
     y = forward(theta, xin, bf16)[0]
     return z1 + out_scale * s * (y[..., 0] + 1j * y[..., 1])
+
+
+def stencil_weights(k: complex, h: float):
+    """Class weights (centre, face, edge, corner) of the interior 27-point operator of
+    Eq. scheme written as D_x+D_y+D_z + a(D_xD_y+D_xD_z+D_yD_z) + b D_xD_yD_z + kappa with
+    D = [1, -2, 1]: the centre collects -6, 12a, -8b and kappa; a face neighbour 1, -4a
+    (two products) and 4b; an edge neighbour a (one product) and -2b; a corner b."""
+    from .helm6_oracle import scheme_coefficients
+    s = scheme_coefficients(complex(k), h)
+    a, b, kap = s["a"], s["b"], s["kappa"]
+    return (-6 + 12 * a - 8 * b + kap, 1 - 4 * a + 4 * b, a - 2 * b, b + 0j)
+
+
+def patch_operator(Y: np.ndarray, w, conj: bool = False) -> np.ndarray:
+    """Interior 27-point operator (weights w = (c0 centre, c1 faces, c2 edges, c3 corners),
+    complex) on complex arrays [B, Z, Y, X] with zero values outside the array; conj=True
+    applies the conjugated weights (the adjoint: the stencil is symmetric)."""
+    c = [complex(v).conjugate() if conj else complex(v) for v in w]
+    B, Z, Yn, X = Y.shape
+    P = np.zeros((B, Z + 2, Yn + 2, X + 2), dtype=complex)
+    P[:, 1:-1, 1:-1, 1:-1] = Y
+    out = np.zeros_like(Y, dtype=complex)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                m = abs(dz) + abs(dy) + abs(dx)
+                out += c[m] * P[:, 1 + dz:1 + dz + Z, 1 + dy:1 + dy + Yn, 1 + dx:1 + dx + X]
+    return out
+
+
+def interior_mask(shape) -> np.ndarray:
+    """True at the points of [B, Z, Y, X] at least one point away from every face."""
+    m = np.zeros(shape, dtype=bool)
+    m[:, 1:-1, 1:-1, 1:-1] = True
+    return m
+
+
+def residual_loss_and_grad(theta, x, w, bf16=True, channels=CHANNELS):
+    """The residual-form loss above and its gradient with respect to the parameters."""
+    q = bf16_round if bf16 else (lambda v: v)
+    layers = unpack(theta, channels)
+    y, acts, pre = forward(theta, x, bf16, channels, keep=True)
+    X = x[..., 0] + 1j * x[..., 1]
+    Yc = y[..., 0] + 1j * y[..., 1]
+    mask = interior_mask(X.shape)
+    M = int(mask.sum())
+    R = np.where(mask, patch_operator(Yc, w) - X, 0.0)
+    loss = float(np.sum(np.abs(R) ** 2) / (2 * M))
+    # dL/dy_0 = Re(A^H R)/M, dL/dy_1 = Im(A^H R)/M
+    AR = patch_operator(R, w, conj=True) / M
+    g = np.stack([AR.real, AR.imag], axis=-1)
+    grads = [None] * len(layers)
+    for li in range(len(layers) - 1, -1, -1):
+        W, _ = layers[li]
+        grads[li] = (conv3d_weight_grad(acts[li], g), g.sum(axis=(0, 1, 2, 3)))
+        if li > 0:
+            g = conv3d_input_grad(g, q(W)) * gelu_grad(pre[li - 1])
+    return loss, pack(grads)

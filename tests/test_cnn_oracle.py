@@ -7,7 +7,10 @@
 * the two adjoint identities <conv(x), g> = <x, input_grad(g)> = <W, weight_grad(x, g)>;
 * the full loss gradient against central finite differences (FP64, no rounding);
 * the parameter count of the 2-16-16-16-2 network;
-* the two-stage preconditioner reducing to M^-1 when every parameter is zero.
+* the two-stage preconditioner reducing to M^-1 when every parameter is zero;
+* the patch operator against the oracle's full 27-point operator on a Dirichlet cube
+  (whose ghost values are zero too), its adjoint identity, and the residual-form loss
+  gradient against central finite differences.
 """
 import numpy as np
 import pytest
@@ -99,3 +102,41 @@ def test_stage2_with_zero_network_is_the_direct_preconditioner():
     u = inputs.complex_normal(31, P.shape)
     z = cnn.stage2(np.zeros(cnn.n_params()), 3.0, u, pre, lambda v: orc.apply_A(P, v))
     assert np.allclose(z, pre(u), rtol=0, atol=1e-14 * np.abs(z).max())
+
+
+def test_patch_operator_is_the_dirichlet_operator():
+    from oracle import helm6_oracle as orc
+    P = orc.Problem(7, 6.0 + 0.5j, "DDDDDD")
+    U = inputs.complex_normal(41, P.shape)
+    ref = orc.apply_A(P, U)
+    out = cnn.patch_operator(U[None], cnn.stencil_weights(P.k, P.h))[0]
+    assert np.allclose(out, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_patch_operator_adjoint():
+    w = (-5.1 + 0.2j, 0.6 - 0.1j, 0.09 + 0.03j, 0.033 - 0.01j)
+    a = inputs.complex_normal(42, (2, 4, 5, 6))
+    b = inputs.complex_normal(43, (2, 4, 5, 6))
+    lhs = np.vdot(b, cnn.patch_operator(a, w))
+    rhs = np.vdot(cnn.patch_operator(b, w, conj=True), a)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_residual_loss_gradient_against_finite_differences():
+    ch = (2, 3, 3, 2)
+    w = (-5.1 + 0.2j, 0.6 - 0.1j, 0.09 + 0.03j, 0.033 - 0.01j)
+    theta = _rand(51, (cnn.n_params(ch),)) * 0.4
+    x = _rand(52, (2, 4, 4, 5, 2))
+    loss, grad = cnn.residual_loss_and_grad(theta, x, w, bf16=False, channels=ch)
+
+    def L(th):
+        y = cnn.forward(th, x, False, ch)
+        R = cnn.patch_operator(y[..., 0] + 1j * y[..., 1], w) - (x[..., 0] + 1j * x[..., 1])
+        m = cnn.interior_mask(R.shape)
+        return np.sum(np.abs(R[m]) ** 2) / (2 * m.sum())
+
+    assert abs(L(theta) - loss) < 1e-14 * loss
+    e = 1e-6
+    fd = np.array([(L(theta + e * np.eye(theta.size)[i]) - L(theta - e * np.eye(theta.size)[i])) / (2 * e)
+                   for i in range(theta.size)])
+    assert np.max(np.abs(fd - grad)) < 1e-7 * max(1.0, np.max(np.abs(grad)))
