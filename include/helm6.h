@@ -219,9 +219,10 @@ int helm6_residual_noalloc(int n, double h, helm6_c64 k, const int faces[6], con
 #define HELM6_CNN_NPARAMS 15602
 enum { HELM6_CNN_OFF = 0,   /* detach: the direct preconditioner alone */
        HELM6_CNN_ON = 1,    /* every inner cycle uses the learned stage */
-       HELM6_CNN_AUTO = 2   /* inner cycles 0 and 1 use it, cycle 2 does not; the rest use
-                               whichever of cycles 1 and 2 reduced the true residual more per
-                               iteration (the direct preconditioner is the fallback) */ };
+       HELM6_CNN_AUTO = 2   /* of inner cycles 0-2 only cycle 1 uses it; the later cycles use
+                               it only if cycle 1 reduced the true residual per iteration at
+                               least 10 % more (in logarithm) than cycle 2 did without it;
+                               otherwise the direct preconditioner alone (the fallback) */ };
 
 /* Attach (or with HELM6_CNN_OFF detach) a network to a MIXED FGMRES context.  theta: HOST
  * array of HELM6_CNN_NPARAMS floats (copied); out_scale: c above.  Allocates two BF16
@@ -252,6 +253,12 @@ int helm6_cnn_gradient(helm6_cnn_trainer* tr, const float* x, const float* targe
 /* One Adam step of learning rate lr on that gradient; *loss (nullable) as above. */
 int helm6_cnn_train_step(helm6_cnn_trainer* tr, const float* x, const float* target, float lr,
                          double* loss);
+/* Switch the trainer's loss (for helm6_cnn_gradient and helm6_cnn_train_step) to the
+ * residual form  sum |A_h N(x) - target|^2 / (2M)  over the M interior points of the images
+ * (at least one point from every face), A_h the interior 27-point operator of Eq. scheme
+ * for wavenumber k and step h, with zero values outside each image; target = x makes N a
+ * local approximate inverse of A_h.  INVALID for non-finite k, h <= 0 or an image side < 3. */
+int helm6_cnn_set_residual_loss(helm6_cnn_trainer* tr, helm6_c64 k, double h);
 /* Copy the current FP32 parameters to theta (HOST, HELM6_CNN_NPARAMS floats). */
 int helm6_cnn_get_params(helm6_cnn_trainer* tr, float* theta);
 void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr);

@@ -514,14 +514,15 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
 
 // MIXED: FP64 refinement around FP32 FGMRES with the FP32 preconditioner.
 // Whether inner cycle `cyc` of a mixed solve uses the learned stage: ON always; AUTO uses
-// it in cycles 0 and 1, not in cycle 2, and afterwards keeps whichever of cycles 1 (with)
-// and 2 (without) reduced the true residual more per iteration.
+// it in cycle 1 only of cycles 0-2 (cycle 0, from the initial guess, reduces faster than
+// any later one and is not compared), and afterwards only if cycle 1 (with) reduced the
+// true residual per iteration by at least 10 % more, in logarithm, than cycle 2 (without).
 bool cnn_cycle(const helm6_ctx* c, int cyc) {
   if (c->cnn_mode == HELM6_CNN_ON) return true;
   if (c->cnn_mode != HELM6_CNN_AUTO) return false;
-  if (cyc < 2) return true;
-  if (cyc == 2) return false;
-  return c->cyc_rate[1] < c->cyc_rate[2];
+  if (cyc < 3) return cyc == 1;
+  const double l1 = std::log(std::max(c->cyc_rate[1], 1e-300)), l2 = std::log(std::max(c->cyc_rate[2], 1e-300));
+  return l2 < 0 && l1 < 1.1 * l2;
 }
 
 int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {

@@ -341,6 +341,73 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
   theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
 }
 
+// Interior 27-point operator on channel-last complex patches [pts][2] with zero values
+// outside each image: out = scale * sum over the 27 offsets of w[class] * y[p + d], class
+// = number of nonzero offset components (centre, face, edge, corner).  The caller
+// conjugates the weights for the adjoint.
+struct PatchW {
+  float re[4], im[4];
+};
+
+__global__ void patch_op_kernel(int nb, int nz, int ny, int nx, const float* __restrict__ y, float* __restrict__ out,
+                                PatchW w, float scale) {
+  const int64_t npts = (int64_t)nb * nz * ny * nx;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const int x = (int)(p % nx);
+  int64_t r = p / nx;
+  const int yy = (int)(r % ny);
+  r /= ny;
+  const int z = (int)(r % nz);
+  float ar = 0.f, ai = 0.f;
+  for (int dz = -1; dz <= 1; ++dz) {
+    if (z + dz < 0 || z + dz >= nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (yy + dy < 0 || yy + dy >= ny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (x + dx < 0 || x + dx >= nx) continue;
+        const int cls = (dz != 0) + (dy != 0) + (dx != 0);
+        const float2 v = ((const float2*)y)[p + ((int64_t)dz * ny + dy) * nx + dx];
+        ar = fmaf(w.re[cls], v.x, fmaf(-w.im[cls], v.y, ar));
+        ai = fmaf(w.re[cls], v.y, fmaf(w.im[cls], v.x, ai));
+      }
+    }
+  }
+  ((float2*)out)[p] = make_float2(scale * ar, scale * ai);
+}
+
+// R = (Ay - x) at interior points (1 away from every image face), 0 elsewhere, and block
+// partial sums of |R|^2.
+__global__ void resid_loss_kernel(int nb, int nz, int ny, int nx, const float* __restrict__ Ay,
+                                  const float* __restrict__ x, float* __restrict__ R, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t npts = (int64_t)nb * nz * ny * nx;
+  double acc = 0.0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x) {
+    const int xi = (int)(p % nx);
+    int64_t r = p / nx;
+    const int yi = (int)(r % ny);
+    r /= ny;
+    const int zi = (int)(r % nz);
+    const bool in = xi > 0 && xi < nx - 1 && yi > 0 && yi < ny - 1 && zi > 0 && zi < nz - 1;
+    float2 d = make_float2(0.f, 0.f);
+    if (in) {
+      const float2 a = ((const float2*)Ay)[p], b = ((const float2*)x)[p];
+      d = make_float2(a.x - b.x, a.y - b.y);
+      acc += (double)d.x * d.x + (double)d.y * d.y;
+    }
+    ((float2*)R)[p] = d;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = (threadIdx.x < blockDim.x / 32) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  }
+}
+
 struct LayerDims {
   int cin[NL], cout[NL], toff[NL], boff[NL], woff[NL];
 };
@@ -514,6 +581,9 @@ struct helm6_cnn_trainer {
   double* pinned = nullptr;
   int nblk = 0, nloss = 0;
   long long step = 0;
+  bool residual = false;    // loss mean|A_h y - x|^2 over interior points (else MSE)
+  PatchW w{}, wconj{};      // interior operator weights and their conjugates
+  double loss_div = 1.0;    // normaliser of the summed squares
 };
 
 namespace {
@@ -552,8 +622,19 @@ int tr_backward(helm6_cnn_trainer* tr, const float* x, const float* target) {
   const LayerDims d = layer_dims();
   cudaStream_t s = tr->stream;
   const int64_t n = tr->npts * 2;
-  note_launch(2);
-  mse_kernel<<<tr->nloss, 256, 0, s>>>(tr->y, target, n, tr->g4, tr->lpart);
+  if (tr->residual) {
+    // R = A y - x (interior), loss = |R|^2 / (2M), g4 = A^H R / M
+    const unsigned nb = (unsigned)((tr->npts + 255) / 256);
+    const int64_t M = (int64_t)tr->nb * (tr->nz - 2) * (tr->ny - 2) * (tr->nx - 2);
+    note_launch(3);
+    patch_op_kernel<<<nb, 256, 0, s>>>(tr->nb, tr->nz, tr->ny, tr->nx, tr->y, tr->ga, tr->w, 1.f);
+    resid_loss_kernel<<<tr->nloss, 256, 0, s>>>(tr->nb, tr->nz, tr->ny, tr->nx, tr->ga, target, tr->gb, tr->lpart);
+    patch_op_kernel<<<nb, 256, 0, s>>>(tr->nb, tr->nz, tr->ny, tr->nx, tr->gb, tr->g4, tr->wconj,
+                                       (float)(1.0 / (double)M));
+  } else {
+    note_launch();
+    mse_kernel<<<tr->nloss, 256, 0, s>>>(tr->y, target, n, tr->g4, tr->lpart);
+  }
   launch_reduce_sum(tr->lpart, tr->nloss, tr->loss, s);
   ConvArgs a = vol_args(tr->nb, tr->nz, tr->ny, tr->nx);
   auto reduce = [&](int l) {
@@ -600,7 +681,7 @@ int read_loss(helm6_cnn_trainer* tr, double* loss) {
   if (cudaMemcpyAsync(tr->pinned, tr->loss, sizeof(double), cudaMemcpyDeviceToHost, tr->stream) != cudaSuccess)
     return HELM6_ERR_CUDA;
   if (cudaStreamSynchronize(tr->stream) != cudaSuccess) return HELM6_ERR_CUDA;
-  *loss = tr->pinned[0] / (double)(tr->npts * 2);
+  *loss = tr->pinned[0] / tr->loss_div;
   return HELM6_OK;
 }
 
@@ -634,6 +715,7 @@ int helm6_cnn_trainer_create(helm6_cnn_trainer** out, int batch, int nz, int ny,
   tr->nx = nx;
   tr->npts = npts;
   tr->stream = (cudaStream_t)stream;
+  tr->loss_div = (double)npts * 2.0;
   tr->nblk = (int)std::min<int64_t>(tiles, 2 * (int64_t)device_sm_count());
   tr->nloss = 4 * device_sm_count();
   auto fail = [&](int rc) {
@@ -694,6 +776,23 @@ int helm6_cnn_train_step(helm6_cnn_trainer* tr, const float* x, const float* tar
   cnn_prepare(tr->net, tr->stream);
   if (cudaGetLastError() != cudaSuccess) return HELM6_ERR_CUDA;
   return read_loss(tr, loss);
+}
+
+int helm6_cnn_set_residual_loss(helm6_cnn_trainer* tr, helm6_c64 k, double h) {
+  if (!tr || !(h > 0) || !std::isfinite(k.re) || !std::isfinite(k.im)) return HELM6_ERR_INVALID;
+  if (tr->nz < 3 || tr->ny < 3 || tr->nx < 3) return HELM6_ERR_INVALID;
+  StencilCoef c;
+  stencil_coefficients(cd(k.re, k.im), h, c);
+  const c64d cls[4] = {c.interior.w[1][0], c.interior.w[1][1], c.interior.w[1][2], c.interior.w[0][2]};
+  for (int i = 0; i < 4; ++i) {
+    tr->w.re[i] = (float)cls[i].re;
+    tr->w.im[i] = (float)cls[i].im;
+    tr->wconj.re[i] = (float)cls[i].re;
+    tr->wconj.im[i] = -(float)cls[i].im;
+  }
+  tr->residual = true;
+  tr->loss_div = 2.0 * (double)tr->nb * (tr->nz - 2) * (tr->ny - 2) * (tr->nx - 2);
+  return HELM6_OK;
 }
 
 int helm6_cnn_get_params(helm6_cnn_trainer* tr, float* theta) {

@@ -29,7 +29,8 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", 
            "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
-           "helm6_cnn_train_step", "helm6_cnn_get_params", "helm6_cnn_trainer_destroy")
+           "helm6_cnn_train_step", "helm6_cnn_set_residual_loss", "helm6_cnn_get_params",
+           "helm6_cnn_trainer_destroy")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
           "gs_update", "gs_small", "resid64", "other", "cnn")
@@ -112,6 +113,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_cnn_gradient.restype = I
     lib.helm6_cnn_train_step.argtypes = [P, P, P, C.c_float, C.POINTER(D)]
     lib.helm6_cnn_train_step.restype = I
+    lib.helm6_cnn_set_residual_loss.argtypes = [P, C64, D]
+    lib.helm6_cnn_set_residual_loss.restype = I
     lib.helm6_cnn_get_params.argtypes = [P, F32P]
     lib.helm6_cnn_get_params.restype = I
     lib.helm6_cnn_trainer_destroy.argtypes = [P]
@@ -342,6 +345,12 @@ class Trainer:
                                               float(lr), C.byref(loss) if want_loss else None),
                "helm6_cnn_train_step")
         return loss.value if want_loss else None
+
+    def set_residual_loss(self, k, h):
+        """Loss mean |A_h N(x) - target|^2 over interior points (A_h: interior operator for k, h)."""
+        kk = complex(k)
+        _check(self._lib.helm6_cnn_set_residual_loss(self._tr, C64(kk.real, kk.imag), float(h)),
+               "helm6_cnn_set_residual_loss")
 
     def params(self):
         import numpy as np

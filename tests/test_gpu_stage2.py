@@ -132,7 +132,10 @@ def test_solve_with_learned_stage_matches_oracle(H, mode):
         u, st = s.solve(torch.from_numpy(F).cuda(), tol=1e-8, restart=10, maxit=400)
     assert st["rc"] == 0 and st["relres"] <= 1e-8, st["status"]
     assert rel2(u.cpu().numpy(), Uref) < 1e-6
-    assert st["cnn_cycles"] == st["outer"] if mode == "CNN_ON" else st["cnn_cycles"] >= min(2, st["outer"])
+    if mode == "CNN_ON":
+        assert st["cnn_cycles"] == st["outer"]
+    else:
+        assert st["cnn_cycles"] >= min(1, st["outer"] - 1)
 
 
 def test_learned_stage_argument_errors(H):
@@ -150,3 +153,70 @@ def test_learned_stage_argument_errors(H):
         s.set_cnn(th, 1.0, H.CNN_OFF)
         with pytest.raises(H.Helm6Error):
             s.apply_stage2(x)
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2])
+def test_residual_loss_gradient_matches_oracle(H, shape):
+    k, h = 40.0 + 0.4j, 1.0 / 129
+    th = _theta(13)
+    x = _batch(14, shape + (2,))
+    with H.Trainer(*shape, th) as tr:
+        tr.set_residual_loss(k, h)
+        xd = torch.from_numpy(x).cuda()
+        loss, g = tr.gradient(xd, xd)
+    g = g.cpu().numpy().astype(np.float64)
+    lref, gref = cnn.residual_loss_and_grad(th.astype(np.float64), x.astype(np.float64),
+                                            cnn.stencil_weights(k, h), bf16=True)
+    assert abs(loss - lref) < 1e-5 * lref, (loss, lref)
+    assert rel2(g, gref) < 1e-3, rel2(g, gref)
+
+
+def _weights():
+    import os
+    from paper_1212_1397_gb300 import weights_path
+    p = weights_path("stage2_kh031.npz")
+    if not os.path.exists(p):
+        pytest.skip("trained weights not present")
+    return np.load(p)
+
+
+def test_trained_network_gain(H, capsys):
+    """What the trained network (weights trained on the GPU by the library's own kernels on
+    kh = 0.31 workloads) gains over the direct preconditioner alone, at n = 48, k = 15 (kh =
+    0.31), mixed faces: (1) the one-step residual u - A z of the preconditioner applied to a
+    field u, z = A_p^-1 u alone versus the two-stage z, for u the residual of an iterate
+    (the training distribution; the stage must cut it) and for u the source itself
+    (reported); (2) iterations of mixed
+    FGMRES(30) to 1e-8 without the stage, with it on every cycle, and in AUTO mode.  All
+    three solutions must match the oracle's; the learned stage must cut the one-step
+    residual; AUTO may cost at most its one probe cycle over the plain solve."""
+    w = _weights()
+    theta, c = w["theta"], float(w["out_scale"])
+    assert w["val"][-1] < 0.35  # held-out patches: residual energy left, relative to N = 0
+    n, k, faces = 48, 15.0, "DDNNSS"
+    prob = O.Problem(n, k, faces)
+    src = inputs.gaussian_sources(1000, n, 1, margin_h=8)
+    F = O.rhs(prob, O.sources.gaussians(src)) + 1e-3 * (prob.h ** 2) * inputs.complex_normal(8919, prob.shape)
+    Uref, _ = O.solve(prob, F, tol=1e-12)
+    Fd = torch.from_numpy(F).cuda()
+    out = {}
+    with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=30) as s, \
+            H.Solver(n, k, faces, precision=H.FP64, method=H.GMRES, max_restart=1) as s64:
+        # fields the stage was trained on: the residual of an iterate (one plain cycle)
+        U1, _ = s.solve(Fd, tol=1e-12, restart=30, maxit=30)
+        s.set_cnn(theta, c, H.CNN_ON)
+        for name, v in (("iterate_residual", Fd - s64.apply_A(U1)), ("source", Fd)):
+            u = v / v.norm()
+            r1 = (u - s64.apply_A(s.apply_Pinv(u))).norm().item()
+            r2 = (u - s64.apply_A(s.apply_stage2(u))).norm().item()
+            out[name] = dict(direct=r1, two_stage=r2, ratio=r2 / r1)
+        for mode in ("CNN_OFF", "CNN_ON", "CNN_AUTO"):
+            s.set_cnn(theta, c, getattr(H, mode))
+            U, st = s.solve(Fd, tol=1e-8, restart=30, maxit=600)
+            assert st["rc"] == 0 and st["relres"] <= 1e-8, (mode, st["status"])
+            assert rel2(U.cpu().numpy(), Uref) < 1e-6, mode
+            out[mode] = dict(iters=st["iters"], cnn_cycles=st["cnn_cycles"], ms=st["t_total_ms"])
+    with capsys.disabled():
+        print("\nlearned stage gain:", out)
+    assert out["iterate_residual"]["ratio"] < 0.8
+    assert out["CNN_AUTO"]["iters"] <= out["CNN_OFF"]["iters"] + 30
