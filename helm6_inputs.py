@@ -136,3 +136,23 @@ WORKLOADS = {
     "mixed_n192_k60": dict(n=192, k=60.0, faces="DDNNSS", restart=30, tol=1e-8,
                            nsrc=1, noise=1e-3),
 }
+
+
+# Batched workload: independent problems of uneven size, wavenumber and faces.
+BATCH_SIZES = (48, 64, 96, 128, 160)
+
+
+def batch_problems(seed: int = 0, count: int = 64):
+    """`count` problem descriptions drawn from SplitMix64, one stream per attribute
+    (seed 16 seed + 1 ... + 8): n uniform over BATCH_SIZES, Re k uniform in [5, 60] with
+    Im k = 0.01 Re k, x faces and y faces each from {D, N}^2, z faces from {D, N, S}^2
+    (Sommerfeld-like faces on z only), one Gaussian source drawn with seed `src_seed`."""
+    u = [uniform01(16 * seed + 1 + a, count) for a in range(8)]
+    out = []
+    for i in range(count):
+        n = BATCH_SIZES[min(int(u[0][i] * len(BATCH_SIZES)), len(BATCH_SIZES) - 1)]
+        kr = 5.0 + 55.0 * float(u[1][i])
+        xy = "".join("DN"[min(int(u[2 + a][i] * 2), 1)] for a in range(4))
+        z = "".join("DNS"[min(int(u[6 + a][i] * 3), 2)] for a in range(2))
+        out.append(dict(n=n, k=complex(kr, 0.01 * kr), faces=xy + z, src_seed=1000 * seed + 17 * i + 5))
+    return out

@@ -79,6 +79,12 @@ typedef struct {
   double inner_tol;  /* MIXED only: relative reduction asked of each FP32 inner solve
                         (0 = default 1e-5) */
   void* stream;      /* cudaStream_t; NULL = default stream */
+  int use_graphs;    /* nonzero: each Arnoldi step is captured once as a CUDA graph (per
+                        step index) and replayed, one graph launch instead of about 15
+                        kernel launches per step; needs a non-NULL stream; results are
+                        identical to the eager path; no per-phase profiling while on */
+  int dot_blocks;    /* thread blocks of the Gram-Schmidt reduction pass (0 = 2 per SM) */
+  int update_blocks; /* thread blocks of the Gram-Schmidt update pass (0 = up to 8 per SM) */
 } helm6_opts;
 
 #define HELM6_MAX_HIST 1024
@@ -262,6 +268,18 @@ int helm6_cnn_set_residual_loss(helm6_cnn_trainer* tr, helm6_c64 k, double h);
 /* Copy the current FP32 parameters to theta (HOST, HELM6_CNN_NPARAMS floats). */
 int helm6_cnn_get_params(helm6_cnn_trainer* tr, float* theta);
 void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr);
+
+/* ---- Batched solve (the paper has no counterpart) ----
+ * Solve count independent problems, ctxs[i] with right side F[i] and initial guess /
+ * solution u[i] (DEVICE complex128 arrays as for helm6_solve), to the same tol, restart
+ * and maxit, on nthreads host threads (1 <= nthreads <= 256) that each take the next
+ * unsolved problem and run helm6_solve on its context.  Problems run concurrently on the
+ * GPU when their contexts have distinct non-NULL streams; contexts may differ in size,
+ * wavenumber, faces and options.  stats: HOST array of count (nullable); stats[i].t_total_ms
+ * is problem i's own wall time.  Returns a negative error of any problem (the others still
+ * finish), else the largest warning code (OK if every problem converged). */
+int helm6_solve_batch(helm6_ctx* const* ctxs, int count, const void* const* F, void* const* u,
+                      double tol, int restart, int maxit, int nthreads, helm6_stats* stats);
 
 /* Release the workspace and the context (NULL is allowed).  Synchronises its stream. */
 void helm6_destroy(helm6_ctx* ctx);

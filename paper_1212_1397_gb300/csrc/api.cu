@@ -11,6 +11,9 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <map>
+#include <thread>
 #include <vector>
 
 #include "helm6_internal.h"
@@ -66,6 +69,12 @@ struct helm6_ctx {
   uint16_t *cnn_a0 = nullptr, *cnn_a1 = nullptr;   // BF16 activations, 16 per point
   double* cnn_ss = nullptr;                        // ||u - A A_p^{-1} u||^2
   double cyc_rate[3] = {1.0, 1.0, 1.0};            // per-iteration reduction of mixed cycles 0-2
+  // CUDA graphs of the Arnoldi steps (opts.use_graphs): key (j, full, learned stage)
+  struct StepGraph {
+    cudaGraphExec_t exec;
+    int kernels;
+  };
+  std::map<int, StepGraph> step_graphs;
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
   struct Pending {
@@ -333,6 +342,16 @@ void precond_cnn32(helm6_ctx* c, const float* in, float* out) {
   prof_stop(c, HELM6_PH_CNN, e, (double)c->g.N * (24.0 + 8.0 + 3 * 32.0 + 32.0 + 3 * 32.0 + 16.0));
 }
 
+// The learned-stage preconditioner of precision T (null for FP64, which has none).
+template <typename T>
+void (*precond_cnn_ptr())(helm6_ctx*, const T*, T*) {
+  return nullptr;
+}
+template <>
+void (*precond_cnn_ptr<float>())(helm6_ctx*, const float*, float*) {
+  return precond_cnn32;
+}
+
 // ---- norms ----
 template <typename T>
 int norm2(helm6_ctx* c, const T* x, double* out) {
@@ -403,15 +422,15 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
     }
     return HELM6_OK;
   };
-  for (int j = 0;; ++j) {
-    const bool full = (j < m) && (applied < maxsteps);
+  // Enqueue step j: preconditioner and operator on u_j (full steps), the reduction pass,
+  // the FP64 step algebra, the estimate's readback and event, and the update pass.
+  auto enqueue = [&](int j, bool full) -> int {
     if (full) {
       T* zj = flexible ? Z + (int64_t)j * vs : zt;
       prec(c, u, zj);
       cudaEvent_t e = prof_start(c);
       launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
       prof_stop(c, HELM6_PH_STENCIL, e);
-      ++applied;
     }
     const double vb = 2.0 * sizeof(T) * (double)N;  // one complex field
     cudaEvent_t e = prof_start(c);
@@ -424,12 +443,50 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
     prof_stop(c, HELM6_PH_SMALL, e, 8.0 * c->ndot * (4 * j + 3));
     CK(cudaMemcpyAsync(&c->pinned[8 + (j & 1)], c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&c->pinned[10 + (j & 1)], c->brk, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaEventRecord(c->step_ev[j & 1], s));
+    // under stream capture the record must be external to become a graph node the host
+    // can wait on (the flag is valid only while capturing)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cap));
+    CK(cudaEventRecordWithFlags(c->step_ev[j & 1], s,
+                                cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u));
     if (full) {
       e = prof_start(c);
       launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
       prof_stop(c, HELM6_PH_UPDATE, e, vb * (j + 4));
     }
+    return HELM6_OK;
+  };
+  const bool graphs = c->opts.use_graphs && !c->prof_on;
+  for (int j = 0;; ++j) {
+    const bool full = (j < m) && (applied < maxsteps);
+    if (graphs) {
+      const int key = (j * 2 + (full ? 1 : 0)) * 2 + (prec == precond_cnn_ptr<T>() ? 1 : 0);
+      auto it = c->step_graphs.find(key);
+      if (it == c->step_graphs.end()) {
+        const long long l0 = launch_total();
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const int rc0 = enqueue(j, full);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+        if (rc0 != HELM6_OK || ce != cudaSuccess) {
+          if (gr) cudaGraphDestroy(gr);
+          return rc0 != HELM6_OK ? rc0 : HELM6_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ie);
+        const int kern = (int)(launch_total() - l0);
+        note_launch(-kern);  // counted when the graph runs
+        it = c->step_graphs.emplace(key, helm6_ctx::StepGraph{ex, kern}).first;
+      }
+      CK(cudaGraphLaunch(it->second.exec, s));
+      note_launch(it->second.kernels);
+    } else {
+      const int rc0 = enqueue(j, full);
+      if (rc0 != HELM6_OK) return rc0;
+    }
+    if (full) ++applied;
     bool stop = false;
     if (j >= 1) {
       int rc2 = finish(j - 1, &stop);
@@ -638,6 +695,7 @@ const char* helm6_status_string(int code) {
 void helm6_destroy(helm6_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (auto& kv : c->step_graphs) cudaGraphExecDestroy(kv.second.exec);
   for (void* p : c->allocs) cudaFree(p);
   cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
@@ -664,6 +722,9 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   if (o.max_restart < 1 || o.max_restart > 64) return HELM6_ERR_INVALID;
   if (o.inner_tol == 0) o.inner_tol = 1e-5;
   if (!(o.inner_tol > 0 && o.inner_tol < 1)) return HELM6_ERR_INVALID;
+  if (o.use_graphs && !o.stream) return HELM6_ERR_INVALID;
+  if (o.dot_blocks < 0 || o.dot_blocks > 64 * 1024 || o.update_blocks < 0 || o.update_blocks > 64 * 1024)
+    return HELM6_ERR_INVALID;
   if (!(std::isfinite(k.re) && std::isfinite(k.im))) return HELM6_ERR_INVALID;
 
   helm6_ctx* c = new helm6_ctx();
@@ -741,6 +802,8 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   c->nsten = stencil_blocks(c->g);
   c->ncgs = (o.precision == HELM6_FP64) ? cgs_blocks<double>(N) : cgs_blocks<float>(N);
   c->ndot = dot_blocks();
+  if (o.dot_blocks > 0) c->ndot = o.dot_blocks;
+  if (o.update_blocks > 0) c->ncgs = o.update_blocks;
   const int npart = std::max(c->nred, std::max(c->ncgs, c->ndot));
   const size_t ncol = (size_t)4 * (m + 1) + 3;
   if ((rc = dalloc(c, &c->partial, (size_t)npart * ncol)) || (rc = dalloc(c, &c->red, ncol)) ||
@@ -851,6 +914,7 @@ int helm6_set_cnn(helm6_ctx* c, const float* theta, double out_scale, int mode) 
         (rc = dalloc(c, &c->cnn_a1, 16 * N)) || (rc = dalloc(c, &c->cnn_ss, 1)))
       return rc;
   }
+  if (cnn_configure() != HELM6_OK) return HELM6_ERR_CUDA;
   CK(cudaMemcpy(c->cnn.theta, theta, sizeof(float) * HELM6_CNN_NPARAMS, cudaMemcpyHostToDevice));
   cnn_prepare(c->cnn, s);
   if (s) CK(cudaStreamSynchronize(s)); else CK(cudaDeviceSynchronize());
@@ -914,6 +978,34 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
   S->status = status;
   S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
+}
+
+int helm6_solve_batch(helm6_ctx* const* ctxs, int count, const void* const* F, void* const* u, double tol,
+                      int restart, int maxit, int nthreads, helm6_stats* stats) {
+  if (count < 0 || (count > 0 && (!ctxs || !F || !u)) || nthreads < 1 || nthreads > 256) return HELM6_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i] || !F[i] || !u[i]) return HELM6_ERR_INVALID;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::vector<int> rc(count, HELM6_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    if (cudaSetDevice(dev) != cudaSuccess) return;
+    for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1))
+      rc[i] = helm6_solve(ctxs[i], F[i], u[i], tol, restart, maxit, stats ? &stats[i] : nullptr);
+  };
+  const int nt = std::min(nthreads, std::max(count, 1));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  if (next.load() < count) return HELM6_ERR_CUDA;  // no worker could select the device
+  int worst = HELM6_OK;
+  for (int i = 0; i < count; ++i) {
+    if (rc[i] < 0) return rc[i];
+    worst = std::max(worst, rc[i]);
+  }
+  return worst;
 }
 
 int helm6_profile_enable(helm6_ctx* c, int enable) {

@@ -525,6 +525,19 @@ void cnn_free(CnnNet& net) {
   net = CnnNet{};
 }
 
+int cnn_configure() {
+  // the field kernels' shared-memory limits, set once before any launch (and so never
+  // inside a stream capture)
+  if (cudaFuncSetAttribute(conv_kernel<2, 16, IN_PLANAR, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem<2, 16>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_kernel<16, 16, IN_BF16, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem<16, 16>()) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_kernel<16, 2, IN_BF16, OUT_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem<16, 2>()) != cudaSuccess)
+    return HELM6_ERR_CUDA;
+  return HELM6_OK;
+}
+
 void cnn_prepare(const CnnNet& net, cudaStream_t s) {
   note_launch();
   prep_kernel<<<(27 * 16 * 16 + 255) / 256, 256, 0, s>>>(net.theta, net.wf, net.wb);

@@ -202,6 +202,7 @@ struct CnnNet {
 int cnn_alloc(CnnNet& net);
 void cnn_free(CnnNet& net);
 void cnn_prepare(const CnnNet& net, cudaStream_t s);  // wf, wb from theta
+int cnn_configure();  // kernel attributes of the field path (before any capture)
 // z += c s N(t / s) on planar complex FP32 fields of nz*ny*nx points, s = sqrt(*sumsq / N)
 // (z unchanged when *sumsq is 0); act0/act1: scratch of 16 BF16 per point each.
 int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq,

@@ -30,7 +30,7 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", 
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
            "helm6_cnn_train_step", "helm6_cnn_set_residual_loss", "helm6_cnn_get_params",
-           "helm6_cnn_trainer_destroy")
+           "helm6_cnn_trainer_destroy", "helm6_solve_batch")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
           "gs_update", "gs_small", "resid64", "other", "cnn")
@@ -42,7 +42,8 @@ class C64(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("xform_terms", C.c_int),
-                ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p)]
+                ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p),
+                ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -119,6 +120,9 @@ def load(path: str = LIB_PATH):
     lib.helm6_cnn_get_params.restype = I
     lib.helm6_cnn_trainer_destroy.argtypes = [P]
     lib.helm6_cnn_trainer_destroy.restype = None
+    lib.helm6_solve_batch.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), D, I, I, I,
+                                      C.POINTER(Stats)]
+    lib.helm6_solve_batch.restype = I
     lib.helm6_status_string.argtypes = [I]
     lib.helm6_status_string.restype = C.c_char_p
     _lib = lib
@@ -172,13 +176,15 @@ class Solver:
     """
 
     def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
-                 max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None):
+                 max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None, use_graphs=False,
+                 dot_blocks=0, update_blocks=0):
         lib = load()
         self._lib = lib
         o = Opts()
         lib.helm6_opts_default(C.byref(o))
         o.precision, o.method, o.max_restart = precision, method, max_restart
         o.inner_tol, o.xform_terms = inner_tol, xform_terms
+        o.use_graphs, o.dot_blocks, o.update_blocks = int(bool(use_graphs)), int(dot_blocks), int(update_blocks)
         if stream is not None:
             o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.stream = stream
@@ -358,3 +364,19 @@ class Trainer:
         _check(self._lib.helm6_cnn_get_params(self._tr, th.ctypes.data_as(C.POINTER(C.c_float))),
                "helm6_cnn_get_params")
         return th
+
+
+def solve_batch(solvers, Fs, us, tol=1e-8, restart=30, maxit=300, nthreads=8):
+    """helm6_solve_batch over Solver objects (each ideally on its own stream).  Returns
+    (return code, [stats dict per problem])."""
+    lib = load()
+    cnt = len(solvers)
+    if not (len(Fs) == cnt and len(us) == cnt):
+        raise ValueError("solvers, Fs and us must have the same length")
+    ctxs = (C.c_void_p * cnt)(*[s._ctx.value for s in solvers])
+    fp = (C.c_void_p * cnt)(*[_ptr(f).value for f in Fs])
+    up = (C.c_void_p * cnt)(*[_ptr(u).value for u in us])
+    st = (Stats * cnt)()
+    rc = _check(lib.helm6_solve_batch(ctxs, cnt, fp, up, float(tol), int(restart), int(maxit), int(nthreads), st),
+                "helm6_solve_batch")
+    return rc, [st[i].to_dict() for i in range(cnt)]

@@ -1,0 +1,94 @@
+"""Batched solves and CUDA-graph replay of the Arnoldi steps, through the C-ABI.
+
+* graph replay gives exactly the eager path's iterations and solution (same kernels, same
+  order, replayed);
+* helm6_solve_batch over heterogeneous problems (sizes, wavenumbers, faces, precisions) on
+  several host threads and streams matches the oracle's solution of every problem and the
+  one-by-one solves;
+* options that graph replay needs are checked.
+"""
+import numpy as np
+import pytest
+
+import helm6_inputs as inputs
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1212_1397_gb300 import build, helm6
+    build.build()
+    return helm6
+
+
+def rel2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _rhs(n, k, faces, seed):
+    prob = O.Problem(n, k, faces)
+    src = inputs.gaussian_sources(seed, n, 1, margin_h=3)
+    return prob, O.rhs(prob, O.sources.gaussians(src))
+
+
+@pytest.mark.parametrize("precision,method", [("MIXED", "FGMRES"), ("FP64", "GMRES"), ("FP64", "FGMRES")])
+def test_graph_replay_equals_eager(H, precision, method):
+    n, k, faces = 21, 9.0 + 0.09j, "DNNDSN"
+    _, F = _rhs(n, k, faces, 7)
+    out = {}
+    for graphs in (False, True):
+        st_ = torch.cuda.Stream()
+        with H.Solver(n, k, faces, precision=getattr(H, precision), method=getattr(H, method), max_restart=10,
+                      stream=st_, use_graphs=graphs) as s:
+            Fd = torch.from_numpy(F).cuda()
+            torch.cuda.synchronize()
+            u1, st1 = s.solve(Fd, tol=1e-9, restart=10, maxit=300)
+            u2, st2 = s.solve(Fd, tol=1e-9, restart=10, maxit=300)  # replays the graphs
+            out[graphs] = (u1.cpu().numpy(), st1, u2.cpu().numpy(), st2)
+    e, g = out[False], out[True]
+    assert e[1]["rc"] == 0 and g[1]["rc"] == 0
+    assert e[1]["iters"] == g[1]["iters"] == g[3]["iters"]
+    assert np.array_equal(e[0], g[0]) and np.array_equal(g[0], g[2])
+
+
+def test_batch_matches_oracle_and_single_solves(H):
+    specs = [(12, 6.0 + 0.06j, "DDDDDD"), (17, 9.5 + 0.1j, "NNDDSS"), (9, 4.0 + 0.04j, "DNNDDN"),
+             (20, 12.0 + 0.12j, "NDDNNS"), (14, 7.0 + 0.07j, "DDNNSD"), (11, 5.5 + 0.05j, "NNNNNN")]
+    solvers, Fs, us, refs = [], [], [], []
+    for i, (n, k, faces) in enumerate(specs):
+        prob, F = _rhs(n, k, faces, 20 + i)
+        refs.append(O.solve(prob, F, tol=1e-12)[0])
+        prec = H.MIXED if i % 2 == 0 else H.FP64
+        meth = H.FGMRES if prec == H.MIXED else H.GMRES
+        solvers.append(H.Solver(n, k, faces, precision=prec, method=meth, max_restart=20,
+                                stream=torch.cuda.Stream(), use_graphs=True))
+        Fs.append(torch.from_numpy(F).cuda())
+        us.append(solvers[-1].empty())
+    torch.cuda.synchronize()
+    try:
+        rc, stats = H.solve_batch(solvers, Fs, us, tol=1e-9, restart=20, maxit=400, nthreads=3)
+        assert rc == 0, [st["status"] for st in stats]
+        for u, ref, st in zip(us, refs, stats):
+            assert st["relres"] <= 1e-9
+            assert rel2(u.cpu().numpy(), ref) < 1e-6
+        # one by one, on the same contexts: the same solutions and iteration counts
+        for s, F, u, st in zip(solvers, Fs, us, stats):
+            u1, st1 = s.solve(F, tol=1e-9, restart=20, maxit=400)
+            assert st1["iters"] == st["iters"]
+            assert np.array_equal(u1.cpu().numpy(), u.cpu().numpy())
+    finally:
+        for s in solvers:
+            s.close()
+
+
+def test_graph_option_needs_a_stream(H):
+    with pytest.raises(H.Helm6Error):
+        H.Solver(8, 3.0, "DDDDDD", precision=H.MIXED, method=H.FGMRES, use_graphs=True)
+    with pytest.raises(H.Helm6Error):
+        H.Solver(8, 3.0, "DDDDDD", dot_blocks=-1)
