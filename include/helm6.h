@@ -80,11 +80,16 @@ typedef struct {
                         (0 = default 1e-5) */
   void* stream;      /* cudaStream_t; NULL = default stream */
   int use_graphs;    /* nonzero: each Arnoldi step is captured once as a CUDA graph (per
-                        step index) and replayed, one graph launch instead of about 15
-                        kernel launches per step; needs a non-NULL stream; results are
-                        identical to the eager path; no per-phase profiling while on */
+                        step index, on a private stream of the context) and replayed on the
+                        context's stream, one graph launch instead of about 15 kernel
+                        launches per step; results are identical to the eager path; no
+                        per-phase profiling while on */
   int dot_blocks;    /* thread blocks of the Gram-Schmidt reduction pass (0 = 2 per SM) */
   int update_blocks; /* thread blocks of the Gram-Schmidt update pass (0 = up to 8 per SM) */
+  int own_stream;    /* nonzero: ignore `stream`; the context creates (and destroys) its own
+                        stream, ordered with the legacy default stream like any blocking
+                        stream, so that contexts driven from several threads run
+                        concurrently while staying ordered with default-stream work */
 } helm6_opts;
 
 #define HELM6_MAX_HIST 1024

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -75,6 +76,8 @@ struct helm6_ctx {
     int kernels;
   };
   std::map<int, StepGraph> step_graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream the step graphs are captured on
+  bool own_stream = false;            // `stream` was created by the context
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
   struct Pending {
@@ -391,7 +394,7 @@ template <typename T>
 int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, int maxsteps, bool flexible,
             void (*prec)(helm6_ctx*, const T*, T*), const StencilCoef& coef, int* kout, double* beta,
             helm6_stats* st) {
-  cudaStream_t s = c->stream;
+  cudaStream_t s = c->stream;  // the stream enqueue() works on (the capture stream while capturing)
   const int64_t N = c->g.N, vs = 2 * N;
   const int ldh = c->mrest + 1;
   CK(cudaMemsetAsync(c->H, 0, sizeof(double) * 2 * ldh * c->mrest, s));
@@ -463,11 +466,21 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
       const int key = (j * 2 + (full ? 1 : 0)) * 2 + (prec == precond_cnn_ptr<T>() ? 1 : 0);
       auto it = c->step_graphs.find(key);
       if (it == c->step_graphs.end()) {
+        // first use of this step: capture and instantiate it, one thread at a time (the
+        // batched solver drives several contexts from several threads; replays run freely)
+        static std::mutex capture_mutex;
+        std::lock_guard<std::mutex> lock(capture_mutex);
         const long long l0 = launch_total();
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        const int rc0 = enqueue(j, full);
+        // capture on the context's private stream (never one another context may share);
+        // everything enqueue() and the preconditioner launch goes to c->stream, so point it
+        // there for the capture
+        cudaStream_t home = c->stream;
+        c->stream = s = c->cap_stream;
+        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        const int rc0 = ce == cudaSuccess ? enqueue(j, full) : HELM6_ERR_CUDA;
         cudaGraph_t gr = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+        if (ce == cudaSuccess) ce = cudaStreamEndCapture(s, &gr);
+        c->stream = s = home;
         if (rc0 != HELM6_OK || ce != cudaSuccess) {
           if (gr) cudaGraphDestroy(gr);
           return rc0 != HELM6_OK ? rc0 : HELM6_ERR_CUDA;
@@ -696,12 +709,14 @@ void helm6_destroy(helm6_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (auto& kv : c->step_graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (void* p : c->allocs) cudaFree(p);
   cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
   for (cudaEvent_t e : c->step_ev)
     if (e) cudaEventDestroy(e);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -722,7 +737,6 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   if (o.max_restart < 1 || o.max_restart > 64) return HELM6_ERR_INVALID;
   if (o.inner_tol == 0) o.inner_tol = 1e-5;
   if (!(o.inner_tol > 0 && o.inner_tol < 1)) return HELM6_ERR_INVALID;
-  if (o.use_graphs && !o.stream) return HELM6_ERR_INVALID;
   if (o.dot_blocks < 0 || o.dot_blocks > 64 * 1024 || o.update_blocks < 0 || o.update_blocks > 64 * 1024)
     return HELM6_ERR_INVALID;
   if (!(std::isfinite(k.re) && std::isfinite(k.im))) return HELM6_ERR_INVALID;
@@ -750,6 +764,13 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     helm6_destroy(c);
     return code;
   };
+  if (o.own_stream) {
+    c->stream = nullptr;
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) return fail(HELM6_ERR_CUDA);
+    c->own_stream = true;
+  }
+  if (o.use_graphs && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(HELM6_ERR_CUDA);
   // bases
   std::vector<double> Vx, Wx, lx, Vy, Wy, ly;
   basis(n, faces[0], faces[1], Vx, Wx, lx);

@@ -43,7 +43,8 @@ class C64(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("xform_terms", C.c_int),
                 ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int)]
+                ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int),
+                ("own_stream", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -177,7 +178,7 @@ class Solver:
 
     def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
                  max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None, use_graphs=False,
-                 dot_blocks=0, update_blocks=0):
+                 dot_blocks=0, update_blocks=0, own_stream=False):
         lib = load()
         self._lib = lib
         o = Opts()
@@ -185,6 +186,7 @@ class Solver:
         o.precision, o.method, o.max_restart = precision, method, max_restart
         o.inner_tol, o.xform_terms = inner_tol, xform_terms
         o.use_graphs, o.dot_blocks, o.update_blocks = int(bool(use_graphs)), int(dot_blocks), int(update_blocks)
+        o.own_stream = int(bool(own_stream))
         if stream is not None:
             o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.stream = stream

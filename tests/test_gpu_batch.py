@@ -87,8 +87,35 @@ def test_batch_matches_oracle_and_single_solves(H):
             s.close()
 
 
-def test_graph_option_needs_a_stream(H):
-    with pytest.raises(H.Helm6Error):
-        H.Solver(8, 3.0, "DDDDDD", precision=H.MIXED, method=H.FGMRES, use_graphs=True)
+def test_shared_streams_and_own_streams(H):
+    """Contexts that share one stream (graph capture happens on each context's private
+    stream) and contexts with their own streams give the one-by-one results."""
+    specs = [(10, 5.0 + 0.05j, "DDNNSS"), (13, 6.5 + 0.07j, "NNDDDD"), (8, 4.0 + 0.04j, "DNDNSN")]
+    shared = torch.cuda.Stream()
+    for mode in ("shared", "own"):
+        solvers, Fs, us, refs = [], [], [], []
+        for i, (n, k, faces) in enumerate(specs):
+            _, F = _rhs(n, k, faces, 40 + i)
+            kw = dict(stream=shared) if mode == "shared" else dict(own_stream=True)
+            solvers.append(H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=10,
+                                    use_graphs=True, **kw))
+            Fs.append(torch.from_numpy(F).cuda())
+            us.append(solvers[-1].empty())
+        torch.cuda.synchronize()
+        try:
+            rc, stats = H.solve_batch(solvers, Fs, us, tol=1e-9, restart=10, maxit=300, nthreads=3)
+            assert rc == 0
+            for s, F, u, st in zip(solvers, Fs, us, stats):
+                u1, st1 = s.solve(F, tol=1e-9, restart=10, maxit=300)
+                assert st1["iters"] == st["iters"]
+                assert np.array_equal(u1.cpu().numpy(), u.cpu().numpy())
+        finally:
+            for s in solvers:
+                s.close()
+
+
+def test_block_options_are_checked(H):
     with pytest.raises(H.Helm6Error):
         H.Solver(8, 3.0, "DDDDDD", dot_blocks=-1)
+    with pytest.raises(H.Helm6Error):
+        H.Solver(8, 3.0, "DDDDDD", update_blocks=-1)
