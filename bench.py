@@ -53,9 +53,11 @@ KERNEL_OF = {
     "resid64": "stencil_kernel<double,1>",
 }
 
-# ncu dram bytes (read + write) per launch of a kernel at this workload, from the captures
-# summarised under profiles/ (absent: not captured since the kernel last changed).
-NCU_TRAFFIC = {}
+# ncu DRAM bytes (read + write) per launch of a kernel over that launch's algorithmic bytes,
+# from the 128^3 capture summarised in profiles/dram_mixed_n128_k40.md (absent: not captured
+# since the kernel last changed).  The reduction pass reads its j + 2 fields once, so its
+# traffic grows with the fields it reads and the ratio carries to the 256^3 launches.
+NCU_TRAFFIC_RATIO = {"dcgs_dot_kernel<float,2>": 1.0075}
 
 
 def peaks():
@@ -177,6 +179,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GMRES solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-stage solve")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched workload")
     args = ap.parse_args()
     cfg = dict(inputs.WORKLOADS[args.workload])
 
@@ -272,6 +276,28 @@ def main():
     sync_all()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps)
 
+    # ---- mixed + learned second stage (AUTO: one probe cycle, then the better) ----
+    learned = None
+    if not args.no_learned:
+        from paper_1212_1397_gb300 import weights_path
+        wfile = weights_path("stage2_kh031.npz")
+        if os.path.exists(wfile):
+            w = np.load(wfile)
+            solver.set_cnn(w["theta"], float(w["out_scale"]), H.CNN_AUTO)
+            u.zero_()
+            solver.solve(F, u, tol=tol, restart=restart, maxit=1000)  # warm-up
+            u.zero_()
+            sync_all()
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            _, stl = solver.solve(F, u, tol=tol, restart=restart, maxit=1000)
+            l1.record(stream)
+            sync_all()
+            learned = {"ms": reduce_max(l0.elapsed_time(l1)), "iters": stl["iters"], "outer": stl["outer"],
+                       "learned_cycles": stl["cnn_cycles"], "relres": stl["relres"], "status": stl["status"],
+                       "mode": "auto", "weights": os.path.basename(wfile)}
+            solver.set_cnn(w["theta"], 1.0, H.CNN_OFF)
+
     # ---- plain FP64 GMRES(30) of the same problem ----
     plain = None
     if not args.no_plain:
@@ -294,6 +320,27 @@ def main():
         solver64.close()
         del u64
 
+    # ---- batched workload: 64 heterogeneous problems, tuned grids and schedule ----
+    batch = None
+    if not args.no_batch:
+        from paper_1212_1397_gb300 import batch as B
+        tfile = os.path.join(ROOT, "paper_1212_1397_gb300", "tuning", "batch_gb300.json")
+        tun = B.load_tuning(tfile)
+        items = B.make_batch(inputs.batch_problems(0, 64), tun)
+        try:
+            sch = tun["schedule"]
+            for _ in range(max(1, args.warmup)):
+                B.run_batch(items, sch["nthreads"], sch["order"])  # first run captures the graphs
+            runs = [B.run_batch(items, sch["nthreads"], sch["order"]) for _ in range(max(1, args.steps))]
+            wall, bstats = sorted(runs, key=lambda r: r[0])[len(runs) // 2]
+            batch = B.summary(items, wall, bstats)
+            batch.update({"metric": "solves/s, 64 problems n in {48..160}, Re k in [5,60], rel-res 1e-8",
+                          "runs": len(runs), "wall_s_all": [r[0] for r in runs],
+                          "tuning": os.path.basename(tfile) if os.path.exists(tfile) else "defaults",
+                          "schedule": sch})
+        finally:
+            B.close_batch(items)
+
     # ---- roofline of the dominant kernel (live per-phase events) ----
     hbm, bf16, peak_src = peaks()
     phases = prof["phases"]
@@ -305,7 +352,11 @@ def main():
     achieved = phases[dom]["bytes"] / (phases[dom]["ms"] * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_OF[dom], "phase": dom, "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": NCU_TRAFFIC.get(KERNEL_OF[dom]), "per_launch_ms": per_launch_ms,
+            "traffic": (NCU_TRAFFIC_RATIO[KERNEL_OF[dom]] * alg_bytes if KERNEL_OF[dom] in NCU_TRAFFIC_RATIO
+                        else None),
+            "traffic_source": ("ncu dram bytes at 128^3 (profiles/dram_mixed_n128_k40.md), per launch scaled "
+                               "by the algorithmic bytes" if KERNEL_OF[dom] in NCU_TRAFFIC_RATIO else None),
+            "per_launch_ms": per_launch_ms,
             "alg_bytes_per_launch": alg_bytes,
             "phase_frac": {p: (phases[p]["bytes"] / (phases[p]["ms"] * 1e-3) / 1e9) / hbm
                            for p in single}}
@@ -334,6 +385,8 @@ def main():
             "iters": last["iters"], "outer": last["outer"], "relres": last["relres"],
             "status": last["status"],
             "plain_fp64": plain,
+            "mixed_learned": learned,
+            "batch64": batch,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 16 * N},
             "roofline": roof,
