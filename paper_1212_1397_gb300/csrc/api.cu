@@ -339,7 +339,7 @@ void precond_cnn32(helm6_ctx* c, const float* in, float* out) {
   launch_stencil<float>(c->g, c->coef, out, c->cnn_t, in, nullptr, 1, c->spart, &nb, c->stream);
   launch_reduce_sum(c->spart, nb, c->cnn_ss, c->stream);
   cnn_apply_field(c->cnn, c->g.mz, c->g.my, c->g.mx, c->cnn_t, c->cnn_ss, c->cnn_a0, c->cnn_a1, c->cnn_scale, out,
-                  c->stream);
+                  c->tcerr, c->stream);
   // stencil pass (2 fields in, 1 out) and the four layers (2, 16, 16, 16 channels in; 16,
   // 16, 16 out in BF16; the last layer updates z in place)
   prof_stop(c, HELM6_PH_CNN, e, (double)c->g.N * (24.0 + 8.0 + 3 * 32.0 + 32.0 + 3 * 32.0 + 16.0));

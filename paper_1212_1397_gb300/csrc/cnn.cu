@@ -408,6 +408,223 @@ __global__ void resid_loss_kernel(int nb, int nz, int ny, int nx, const float* _
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Tensor-core layer for the field path (tcgen05, BF16 operands, FP32 accumulation in TMEM).
+// Implicit GEMM: per 128-point tile, D[128 x 16] = sum over the 27 taps of A_t W_t^T with
+// A_t the input rows shifted by the tap's offset (K = 16 input channels) and W_t the
+// 16 x 16 taps (layers with 2 channels are zero-padded to 16).  A CTA owns a brick of
+// 30 x 8 x 4 output points; its 32 x 10 x 6 input halo sits in shared memory as two
+// channel planes (channels 0-7 and 8-15, 16 bytes per point, points x fastest), the
+// no-swizzle K-major layout: a core matrix is 8 consecutive points of one plane (128 B),
+// the K step between the planes is the plane distance and the step between 8-row groups
+// is 128 B, so every tap's A operand is the same descriptor with its start address moved
+// by the tap offset.  The 8 tiles (4 halo rows x 32 points each: y rows 1-4 and 5-8 of
+// z planes 1-4) accumulate in 8 x 16 TMEM columns; outputs at halo columns are computed
+// and dropped.
+constexpr int BX = 30, BY = 8, BZ = 4;                       // output points of a brick
+constexpr int GX = BX + 2, GY = BY + 2, GZ = BZ + 2, GP = GX * GY * GZ;  // halo (GX = 32)
+constexpr int TC_TILES = BZ * BY / 4;                         // 128-point tiles of a brick
+constexpr int PLANE_B = (GP + 2) * 16;                        // one point of padding each end
+constexpr int TCW_TAP = 512;                                  // bytes of one tap's 16 x 16 BF16
+constexpr size_t TC_SMEM = 1024 + 2 * (size_t)PLANE_B + 27 * TCW_TAP + 256;
+constexpr int kConvPolls = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory descriptor, no swizzle: start, K-direction step (lbo), 8-row step (sbo).
+__device__ __forceinline__ uint64_t desc_noswz(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+struct TcConvArgs {
+  int nz, ny, nx;
+  int bx, by, bz;        // bricks per axis
+  const void* in;        // IN_BF16: [N][16] BF16; IN_PLANAR: planar FP32 complex field
+  const uint16_t* w;     // 27 taps of 16 x 16 BF16 in the canonical layout
+  const float* bias;     // [c_out] (c_out = 16, or 2 for the field output)
+  void* out;             // OUT_HIDDEN: [N][16] BF16; OUT_FIELD: planar FP32 z (updated)
+  const double* sumsq;   // IN_PLANAR / OUT_FIELD: sum |t|^2
+  float out_scale;
+  int* err;              // set if the MMA completion wait timed out
+};
+
+template <int IN, int OUT>
+__global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* plane0 = sm + 16;               // point -1 at sm, point 0 at sm + 16
+  uint8_t* plane1 = plane0 + PLANE_B;
+  uint8_t* wts = sm + 2 * PLANE_B;         // 27 x 512 B (1024-aligned base + 2 * PLANE_B: 16-aligned)
+  uint64_t* bar = (uint64_t*)(wts + 27 * TCW_TAP);
+  uint32_t* tslot = (uint32_t*)(bar + 1);
+  int* fail = (int*)(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t npts = (int64_t)a.nz * a.ny * a.nx;
+
+  int64_t b = blockIdx.x;
+  const int ibx = (int)(b % a.bx);
+  b /= a.bx;
+  const int iby = (int)(b % a.by);
+  const int ibz = (int)(b / a.by);
+  const int x0 = ibx * BX - 1, y0 = iby * BY - 1, z0 = ibz * BZ - 1;  // global coordinate of halo (0,0,0)
+
+  // weights: 27 x 512 B
+  for (int i = tid; i < 27 * TCW_TAP / 16; i += 128) cp16(smem_u32(wts) + 16u * i, (const uint4*)a.w + i, true);
+  // halo planes
+  float sc = 1.f;
+  if constexpr (IN == IN_PLANAR) {
+    const double ss = *a.sumsq;
+    sc = ss > 0.0 ? (float)(1.0 / sqrt(ss / (double)npts)) : 0.f;
+  }
+  for (int i = tid; i < GP; i += 128) {
+    const int hx = i % GX, r = i / GX, hy = r % GY, hz = r / GY;
+    const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+    const bool ok = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+    const int64_t p = ok ? ((int64_t)gz * a.ny + gy) * a.nx + gx : 0;
+    if constexpr (IN == IN_BF16) {
+      const uint4* src = (const uint4*)a.in + 2 * p;
+      cp16(smem_u32(plane0) + 16u * i, src, ok);
+      cp16(smem_u32(plane1) + 16u * i, src + 1, ok);
+    } else {
+      const float* f = (const float*)a.in;
+      const float re = ok ? f[p] * sc : 0.f, im = ok ? f[npts + p] * sc : 0.f;
+      *(uint4*)(plane0 + 16 * i) = make_uint4(pack_bf16(re, im), 0u, 0u, 0u);
+      *(uint4*)(plane1 + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  if (tid < 2) {  // the padding points before and after each plane
+    *(uint4*)(sm + tid * PLANE_B) = make_uint4(0u, 0u, 0u, 0u);
+    *(uint4*)(plane0 + tid * PLANE_B + 16 * GP) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    *fail = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+
+  if (tid == 0) {
+    // kind::f16, D = F32, A = B = BF16, K-major, M = 128, N = 16
+    const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | (2u << 17) | (8u << 24);
+    const uint32_t p0 = smem_u32(plane0);
+    for (int tile = 0; tile < TC_TILES; ++tile) {
+      const int hz = 1 + tile / (BY / 4), hy = 1 + 4 * (tile % (BY / 4));
+      const int q0 = (hz * GY + hy) * GX;
+      for (int t = 0; t < 27; ++t) {
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const int q = q0 + (dz * GY + dy) * GX + dx;  // in [-1, GP - 128]: the padding covers -1 and GP
+        const uint64_t ad = desc_noswz(p0 + (uint32_t)(q * 16), PLANE_B, 128);
+        const uint64_t bd = desc_noswz(smem_u32(wts) + (uint32_t)(t * TCW_TAP), 128, 256);
+        mma_bf16(tmem + 16u * tile, ad, bd, id, t > 0 ? 1u : 0u);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+  }
+  __syncthreads();
+  bool ok = false;
+  for (int it = 0; it < kConvPolls; ++it) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(r)
+        : "r"(smem_u32(bar)), "r"(0)
+        : "memory");
+    if (r) {
+      ok = true;
+      break;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!ok) {
+    *fail = 1;
+  } else {
+    float bias[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) bias[c] = (OUT == OUT_HIDDEN || c < 2) ? a.bias[c] : 0.f;
+    float cs = 0.f;
+    if constexpr (OUT == OUT_FIELD) {
+      const double ss = *a.sumsq;
+      cs = ss > 0.0 ? a.out_scale * (float)sqrt(ss / (double)npts) : 0.f;
+    }
+    for (int tile = 0; tile < TC_TILES; ++tile) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(32 * warp) << 16) + 16u * tile));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int r = 32 * warp + lane;  // row of the tile: halo x = r % 32, y = hy + r / 32
+      const int hx = r % GX, hz = 1 + tile / (BY / 4), hy = 1 + 4 * (tile % (BY / 4)) + r / GX;
+      const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+      if (hx < 1 || hx > BX || gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
+      const int64_t p = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+      if constexpr (OUT == OUT_HIDDEN) {
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          pk[q] = pack_bf16(gelu_f(__uint_as_float(v[2 * q]) + bias[2 * q]),
+                            gelu_f(__uint_as_float(v[2 * q + 1]) + bias[2 * q + 1]));
+        uint4* o4 = (uint4*)a.out + 2 * p;
+        o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      } else {
+        float* z = (float*)a.out;
+        z[p] = fmaf(cs, __uint_as_float(v[0]) + bias[0], z[p]);
+        z[npts + p] = fmaf(cs, __uint_as_float(v[1]) + bias[1], z[npts + p]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (tid == 0 && *fail) atomicExch(a.err, 1);
+}
+
+// Canonical tensor-core taps of every layer: layer l, tap t, 16 x 16 BF16 with c_out rows
+// and c_in columns zero-padded to 16, stored [c_out / 8][c_in / 8][c_out % 8][c_in % 8].
+__global__ void prep_tc_kernel(const float* __restrict__ theta, uint16_t* __restrict__ wtc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 4 layers x 27 taps x 256
+  if (i >= NL * 27 * 256) return;
+  const int l = i / (27 * 256), t = (i / 256) % 27, e = i % 256;
+  const int co = e / 16, ci = e % 16;
+  int toff = 0;
+  for (int q = 0; q < l; ++q) toff += 27 * ch(q) * ch(q + 1) + ch(q + 1);
+  const int cin = ch(l), cout = ch(l + 1);
+  const float w = (co < cout && ci < cin) ? theta[toff + (co * cin + ci) * 27 + t] : 0.f;
+  const __nv_bfloat16 b16 = __float2bfloat16_rn(w);
+  uint16_t u;
+  memcpy(&u, &b16, 2);
+  wtc[(l * 27 + t) * 256 + ((co / 8) * 2 + ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] = u;
+}
+
 struct LayerDims {
   int cin[NL], cout[NL], toff[NL], boff[NL], woff[NL];
 };
@@ -512,6 +729,7 @@ ConvArgs vol_args(int nb, int nz, int ny, int nx) {
 // ---------------------------------------------------------------------------------------
 
 int cnn_alloc(CnnNet& net) {
+  if (cudaMalloc((void**)&net.wtc, sizeof(uint16_t) * NL * 27 * 256) != cudaSuccess) return HELM6_ERR_NOMEM;
   if (cudaMalloc((void**)&net.theta, sizeof(float) * HELM6_CNN_NPARAMS) != cudaSuccess) return HELM6_ERR_NOMEM;
   if (cudaMalloc((void**)&net.wf, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
   if (cudaMalloc((void**)&net.wb, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
@@ -522,12 +740,20 @@ void cnn_free(CnnNet& net) {
   cudaFree(net.theta);
   cudaFree(net.wf);
   cudaFree(net.wb);
+  cudaFree(net.wtc);
   net = CnnNet{};
 }
 
 int cnn_configure() {
   // the field kernels' shared-memory limits, set once before any launch (and so never
   // inside a stream capture)
+  if (cudaFuncSetAttribute(conv_tc_kernel<IN_PLANAR, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TC_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_tc_kernel<IN_BF16, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TC_SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(conv_tc_kernel<IN_BF16, OUT_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)TC_SMEM) != cudaSuccess)
+    return HELM6_ERR_CUDA;
   if (cudaFuncSetAttribute(conv_kernel<2, 16, IN_PLANAR, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem<2, 16>()) != cudaSuccess ||
       cudaFuncSetAttribute(conv_kernel<16, 16, IN_BF16, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -539,37 +765,41 @@ int cnn_configure() {
 }
 
 void cnn_prepare(const CnnNet& net, cudaStream_t s) {
-  note_launch();
+  note_launch(net.wtc ? 2 : 1);
   prep_kernel<<<(27 * 16 * 16 + 255) / 256, 256, 0, s>>>(net.theta, net.wf, net.wb);
+  if (net.wtc) prep_tc_kernel<<<(NL * 27 * 256 + 255) / 256, 256, 0, s>>>(net.theta, net.wtc);
 }
 
 int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq, uint16_t* act0,
-                    uint16_t* act1, float out_scale, float* z, cudaStream_t s) {
+                    uint16_t* act1, float out_scale, float* z, int* err, cudaStream_t s) {
   const LayerDims d = layer_dims();
-  ConvArgs a = vol_args(1, nz, ny, nx);
+  TcConvArgs a{};
+  a.nz = nz;
+  a.ny = ny;
+  a.nx = nx;
+  a.bx = (nx + BX - 1) / BX;
+  a.by = (ny + BY - 1) / BY;
+  a.bz = (nz + BZ - 1) / BZ;
   a.sumsq = sumsq;
   a.out_scale = out_scale;
-  a.in = t;
-  a.w = net.wf + d.woff[0];
-  a.bias = net.theta + d.boff[0];
-  a.out = act0;
-  if ((launch_conv<2, 16, IN_PLANAR, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
-  a.in = act0;
-  a.w = net.wf + d.woff[1];
-  a.bias = net.theta + d.boff[1];
-  a.out = act1;
-  if ((launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
-  a.in = act1;
-  a.w = net.wf + d.woff[2];
-  a.bias = net.theta + d.boff[2];
-  a.out = act0;
-  if ((launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
-  a.in = act0;
-  a.w = net.wf + d.woff[3];
-  a.bias = net.theta + d.boff[3];
-  a.out = z;
-  if ((launch_conv<16, 2, IN_BF16, OUT_FIELD>(a, s)) != cudaSuccess) return HELM6_ERR_CUDA;
-  return HELM6_OK;
+  a.err = err;
+  const unsigned grid = (unsigned)((int64_t)a.bx * a.by * a.bz);
+  const uint16_t* in[4] = {nullptr, act0, act1, act0};
+  void* out[4] = {act0, act1, act0, z};
+  note_launch(4);
+  for (int l = 0; l < NL; ++l) {
+    a.in = l == 0 ? (const void*)t : (const void*)in[l];
+    a.w = net.wtc + (size_t)l * 27 * 256;
+    a.bias = net.theta + d.boff[l];
+    a.out = out[l];
+    if (l == 0)
+      conv_tc_kernel<IN_PLANAR, OUT_HIDDEN><<<grid, 128, TC_SMEM, s>>>(a);
+    else if (l < NL - 1)
+      conv_tc_kernel<IN_BF16, OUT_HIDDEN><<<grid, 128, TC_SMEM, s>>>(a);
+    else
+      conv_tc_kernel<IN_BF16, OUT_FIELD><<<grid, 128, TC_SMEM, s>>>(a);
+  }
+  return cudaGetLastError() == cudaSuccess ? HELM6_OK : HELM6_ERR_CUDA;
 }
 
 }  // namespace helm6

@@ -198,15 +198,17 @@ struct CnnNet {
   float* theta = nullptr;
   float* wf = nullptr;
   float* wb = nullptr;
+  uint16_t* wtc = nullptr;  // BF16 taps of every layer for the tensor-core field path
 };
 int cnn_alloc(CnnNet& net);
 void cnn_free(CnnNet& net);
 void cnn_prepare(const CnnNet& net, cudaStream_t s);  // wf, wb from theta
 int cnn_configure();  // kernel attributes of the field path (before any capture)
 // z += c s N(t / s) on planar complex FP32 fields of nz*ny*nx points, s = sqrt(*sumsq / N)
-// (z unchanged when *sumsq is 0); act0/act1: scratch of 16 BF16 per point each.
+// (z unchanged when *sumsq is 0); act0/act1: scratch of 16 BF16 per point each.  The four
+// layers run on the tensor cores; *err is set if a bounded wait timed out.
 int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq,
-                    uint16_t* act0, uint16_t* act1, float out_scale, float* z, cudaStream_t s);
+                    uint16_t* act0, uint16_t* act1, float out_scale, float* z, int* err, cudaStream_t s);
 
 int device_sm_count();
 
