@@ -67,34 +67,79 @@ __global__ void scale_copy_kernel(const T* __restrict__ x, T* __restrict__ y, in
     y[idx] = x[idx] * s;
 }
 
-// out (+)= scale * sum_i V_i y_i, y complex double
-template <typename TI, typename TO>
-__global__ void lincomb_kernel(const TI* __restrict__ V, int64_t vstride, int count,
-                               const double* __restrict__ y, double scale, TO* __restrict__ out,
-                               int64_t N, int accumulate) {
-  __shared__ double yr[64], yi[64];
-  if (threadIdx.x < count) {
-    yr[threadIdx.x] = y[2 * threadIdx.x] * scale;
-    yi[threadIdx.x] = y[2 * threadIdx.x + 1] * scale;
+template <typename T>
+struct V2;
+template <>
+struct V2<float> {
+  using t = float2;
+};
+template <>
+struct V2<double> {
+  using t = double2;
+};
+
+// out (+)= scale * sum_i V_i y_i, y complex double.  Two points per thread (vector loads
+// when the planes allow) and the basis read 8 vectors at a time, so that each thread has
+// 16 independent loads in flight; sums in the input precision, widened once.
+template <typename TI, typename TO, bool VEC>
+__global__ void __launch_bounds__(RB) lincomb_kernel(const TI* __restrict__ V, int64_t vstride, int count,
+                                                     const double* __restrict__ y, double scale,
+                                                     TO* __restrict__ out, int64_t N, int accumulate) {
+  __shared__ TI yr[64], yi[64];
+  for (int c = threadIdx.x; c < count; c += blockDim.x) {
+    yr[c] = (TI)(y[2 * c] * scale);
+    yi[c] = (TI)(y[2 * c + 1] * scale);
   }
   __syncthreads();
+  constexpr int P = VEC ? 2 : 1;
+  constexpr int UB = 8;
+  using TV = typename V2<TI>::t;
+  const int64_t npts = N / P;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
-    // sum in the input precision, widen once
-    TI sr = TI(0), si = TI(0);
-    for (int c = 0; c < count; ++c) {
-      const TI* v = V + (int64_t)c * vstride;
-      const TI vr = v[idx], vi = v[N + idx];
-      const TI a = (TI)yr[c], b = (TI)yi[c];
-      sr = fmx(vr, a, fmx(-vi, b, sr));
-      si = fmx(vr, b, fmx(vi, a, si));
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
+    TI sr[P], si[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) sr[k] = si[k] = TI(0);
+    for (int c0 = 0; c0 < count; c0 += UB) {
+      TI vr[UB][P], vi[UB][P];
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (c0 + u < count) {
+          const TI* v = V + (int64_t)(c0 + u) * vstride;
+          if constexpr (VEC) {
+            const TV a = ((const TV*)v)[q], b = ((const TV*)(v + N))[q];
+            vr[u][0] = a.x;
+            vr[u][1 % P] = a.y;
+            vi[u][0] = b.x;
+            vi[u][1 % P] = b.y;
+          } else {
+            vr[u][0] = v[q];
+            vi[u][0] = v[N + q];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (c0 + u < count) {
+          const TI a = yr[c0 + u], b = yi[c0 + u];
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            sr[k] = fmx(vr[u][k], a, fmx(-vi[u][k], b, sr[k]));
+            si[k] = fmx(vr[u][k], b, fmx(vi[u][k], a, si[k]));
+          }
+        }
+      }
     }
-    if (accumulate) {
-      out[idx] += (TO)sr;
-      out[N + idx] += (TO)si;
-    } else {
-      out[idx] = (TO)sr;
-      out[N + idx] = (TO)si;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const int64_t idx = q * P + k;
+      if (accumulate) {
+        out[idx] += (TO)sr[k];
+        out[N + idx] += (TO)si[k];
+      } else {
+        out[idx] = (TO)sr[k];
+        out[N + idx] = (TO)si[k];
+      }
     }
   }
 }
@@ -131,16 +176,6 @@ __global__ void reduce_sum_kernel(const double* __restrict__ partial, int n, dou
 
 // ---- Arnoldi with delayed classical Gram-Schmidt (one reduction + one update per step) ----
 // Vector traits for 2-point loads of a planar field.
-template <typename T>
-struct V2;
-template <>
-struct V2<float> {
-  using t = float2;
-};
-template <>
-struct V2<double> {
-  using t = double2;
-};
 
 constexpr int CHD = 8;  // basis vectors per chunk of the reduction pass
 
@@ -624,7 +659,10 @@ template <typename TI, typename TO>
 void launch_lincomb(const TI* V, int64_t vstride, int count, const double* y, double scale, TO* out,
                     int64_t N, int accumulate, cudaStream_t s) {
   note_launch();
-  lincomb_kernel<TI, TO><<<grid_for(N, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
+  if ((N & 1) == 0 && (vstride & 1) == 0)
+    lincomb_kernel<TI, TO, true><<<grid_for(N / 2, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
+  else
+    lincomb_kernel<TI, TO, false><<<grid_for(N, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
 }
 
 template <typename TI, typename TO>

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(TX* TY)
 // 16-byte chunks when mx % 4 == 0; the two edge columns, and everything when a chunk would
 // cross the field's x extent, are copied element by element with the ghost rules.
 constexpr int T4X = 32, T4Y = 16, T4R = 4, T4ROWS = T4Y + 2, T4LD = 40;
+constexpr int Z4CH = 32;  // z planes per block of the FP32 kernel (16 measured slower at 256^3)
 constexpr int T4SLOTS = 2 * T4ROWS * 10;  // components x rows x (8 chunks + 2 edges)
 
 __device__ __forceinline__ int ghost_index(int gi, int m, int lo_neumann, int hi_neumann) {
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * T4X + tx;
   const int x0 = blockIdx.x * T4X, y0 = blockIdx.y * T4Y;
   const int i = x0 + tx;
-  const int l0 = blockIdx.z * ZCH;
-  const int l1 = min(l0 + ZCH, g.mz);
+  const int l0 = blockIdx.z * Z4CH;
+  const int l1 = min(l0 + Z4CH, g.mz);
   const int64_t plane = (int64_t)g.mx * g.my;
   const bool xn0 = g.face[0] == HELM6_NEUMANN, xn1 = g.face[1] == HELM6_NEUMANN;
   const bool yn0 = g.face[2] == HELM6_NEUMANN, yn1 = g.face[3] == HELM6_NEUMANN;
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
   const cpx<float> c2 = cast<float>(coef.interior.w[1][2]);
   const cpx<float> c3 = cast<float>(coef.interior.w[0][2]);
   // Sommerfeld-like face rows of this block, if any (one z chunk holds at most one such
-  // face plane when ZCH < mz; both when the chunk spans the whole axis)
+  // face plane when Z4CH < mz; both when the chunk spans the whole axis)
   cpx<float> wlo[3][3], whi[3][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -432,7 +433,7 @@ void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const
   (void)r;
   if (sizeof(T) == 4) {
     dim3 block(T4X, T4Y / T4R);
-    dim3 grid((g.mx + T4X - 1) / T4X, (g.my + T4Y - 1) / T4Y, (g.mz + ZCH - 1) / ZCH);
+    dim3 grid((g.mx + T4X - 1) / T4X, (g.my + T4Y - 1) / T4Y, (g.mz + Z4CH - 1) / Z4CH);
     if (nblk) *nblk = (int)(grid.x * grid.y * grid.z);
     note_launch();
     const float* xf = (const float*)x;
