@@ -7,16 +7,23 @@
 // hi = bf16(x) and lo = bf16(x - hi); the basis is split the same way on the host, and
 // D accumulates hi*hi + lo*hi (+ hi*lo) in FP32 in tensor memory (1, 2 or 3 products).
 //
-// CTA = 128 data rows (one UMMA M) x all N modes.  K is streamed in 64-element stages
-// (one 128-byte swizzle row of BF16), double-buffered: the basis stage arrives by a bulk
-// copy completing on an mbarrier; the data stage is loaded, split and stored swizzled by
-// all threads; one thread issues the MMAs and commits them to a second mbarrier that
-// releases the stage.  Every mbarrier wait is bounded; a timeout sets *err, skips the
-// remaining work, and the CTA still frees its tensor memory.
+// CTA = 128 data rows (one MMA M) x one group of at most 256 output columns (P > 256 is
+// cut into two groups, interleaved in the grid so that the two CTAs of a row tile run
+// together and share its data in L2).  K is streamed in 32-element stages, double
+// buffered, in the no-swizzle K-major layout: a core matrix is 8 rows x 16 bytes stored
+// contiguously, core matrices 8 rows apart are 128 B apart and the K direction steps by
+// one whole column of core matrices.  The basis stage arrives by a bulk copy completing on
+// an mbarrier; the data stage is loaded, split and stored by all threads (each warp writes
+// whole core matrices, conflict-free); one thread issues the MMAs and commits them to a
+// second mbarrier that releases the stage.  At most 256 tensor-memory columns and about
+// 100 KB of shared memory per CTA let two CTAs share an SM.  Every mbarrier wait is
+// bounded; a timeout sets *err, skips the remaining work, and the CTA still frees its
+// tensor memory.
 //
 // Epilogue: each warp reads its 32 tensor-memory lanes (rows) and half of the columns and
-// stores either row-major (out[row*P + p]) or transposed within planes of R rows
-// (out[(row/R)*R*P + p*R + row%R]), which keeps consecutive lanes on consecutive addresses.
+// stores either transposed within planes of R rows (out[(row/R)*R*P + p*R + row%R], which
+// keeps consecutive lanes on consecutive addresses) or row-major (out[row*P + p]) through
+// shared memory, 64 rows at a time, so that rows are written coalesced.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -28,28 +35,31 @@ namespace helm6 {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_KT = 64;
+constexpr int TC_KT = 32;                   // K per stage
+constexpr int TC_KC = TC_KT / 8;            // core-matrix columns per stage
 constexpr int TC_THREADS = 256;
-constexpr int A_TILE = TC_M * TC_KT * 2;  // bytes of one BF16 term of the data stage
+constexpr int TC_GMAX = 256;                // output columns of one CTA (MMA N limit)
+constexpr int A_TILE = TC_M * TC_KT * 2;    // bytes of one BF16 term of the data stage
+constexpr int A_LBO = (TC_M / 8) * 128;     // K step of the data stage (one core-matrix column)
 constexpr int kMaxPolls = 1 << 22;
 
 struct TcArgs {
   const float* in;
   float* out;
-  const uint8_t* W;  // [kt][term][Npad rows][128 B] pre-swizzled
-  int M_total, K, P, Npad, nk, terms, transposed, R;
+  const uint8_t* W;  // per column group: [kt][term][kc][Npad_g / 8][8 rows][16 B]
+  int M_total, K, P, nk, terms, transposed, R;
+  int ngroups, gcols;  // column groups and columns per group (the last may have fewer)
   int* err;
 };
 
 __device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+// Shared-memory matrix descriptor, no swizzle: start, K step (lbo), 8-row step (sbo).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -79,16 +89,18 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
-constexpr int A_PER_THREAD = TC_M * TC_KT / 2 / TC_THREADS;  // float pairs per thread per stage
+constexpr int A_PER_THREAD = TC_M * TC_KT / 2 / TC_THREADS;  // float pairs per thread per stage (8)
 
-// Load the FP32 data of stage kt (rows m0.., k in [64 kt, 64 kt + 64)) into registers;
-// zero outside the field.  Pairs are 8-byte aligned when K is even.
-__device__ __forceinline__ void load_stage(const TcArgs& p, int m0, int kt, int tid, float2* xr) {
-  const int kp = (tid & 31) * 2;
-  const int k = kt * TC_KT + kp;
+// Stage kt of the data: core matrix cm = 8 warp + i holds rows 8 (cm % 16) .. + 7 and
+// k = 32 kt + 8 (cm / 16) .. + 7; lane l holds row l / 4 and the k pair 2 (l % 4).  Zero
+// outside the field.  Pairs are 8-byte aligned when K is even.
+__device__ __forceinline__ void load_stage(const TcArgs& p, int m0, int kt, int warp, int lane, float2* xr) {
+  const int r8 = lane >> 2, pr = lane & 3;
 #pragma unroll
   for (int i = 0; i < A_PER_THREAD; ++i) {
-    const int row = m0 + (tid >> 5) + 8 * i;
+    const int cm = warp * A_PER_THREAD + i;
+    const int row = m0 + 8 * (cm & 15) + r8;
+    const int k = kt * TC_KT + 8 * (cm >> 4) + 2 * pr;
     float2 v = make_float2(0.f, 0.f);
     if (row < p.M_total) {
       const float* src = p.in + (int64_t)row * p.K + k;
@@ -103,16 +115,15 @@ __device__ __forceinline__ void load_stage(const TcArgs& p, int m0, int kt, int 
   }
 }
 
-// Split the stage into BF16 hi / lo and store both in the 128-byte-swizzled K-major layout.
-__device__ __forceinline__ void store_stage(uint8_t* sA, int tid, const float2* xr) {
-  const int kp = (tid & 31) * 2;
+// Split the stage into BF16 hi / lo: core matrix cm at (cm / 16) * A_LBO + (cm % 16) * 128.
+__device__ __forceinline__ void store_stage(uint8_t* sA, int warp, int lane, const float2* xr) {
 #pragma unroll
   for (int i = 0; i < A_PER_THREAD; ++i) {
-    const int r = (tid >> 5) + 8 * i;
+    const int cm = warp * A_PER_THREAD + i;
+    const int off = (cm >> 4) * A_LBO + (cm & 15) * 128 + lane * 4;
     const __nv_bfloat16 h0 = __float2bfloat16_rn(xr[i].x), h1 = __float2bfloat16_rn(xr[i].y);
     const __nv_bfloat16 l0 = __float2bfloat16_rn(xr[i].x - __bfloat162float(h0));
     const __nv_bfloat16 l1 = __float2bfloat16_rn(xr[i].y - __bfloat162float(h1));
-    const int off = r * 128 + ((((kp >> 3) ^ (r & 7)) << 4)) + (kp & 7) * 2;
     __nv_bfloat162 hh, ll;
     hh.x = h0;
     hh.y = h1;
@@ -123,21 +134,30 @@ __device__ __forceinline__ void store_stage(uint8_t* sA, int tid, const float2* 
   }
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
+__host__ __device__ __forceinline__ int round16(int n) { return ((n + 15) / 16) * 16; }
+
+__global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int bstage = 2 * p.Npad * 128;  // basis bytes per stage (hi, lo)
-  const int stage_bytes = 2 * A_TILE + bstage;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int grp = (int)(blockIdx.x % p.ngroups);
+  const int m0 = (int)(blockIdx.x / p.ngroups) * TC_M;
+  const int c0 = grp * p.gcols;                   // first output column of this CTA
+  const int pc = min(p.gcols, p.P - c0);          // its columns
+  const int npad = round16(pc);                   // MMA N
+  const int gpad = round16(p.gcols);              // N of the groups before the last
+  const int bterm = TC_KC * npad * 16;            // basis bytes of one term of one stage
+  const int bstage = 2 * bterm;
+  const int stage_bytes = 2 * A_TILE + 2 * TC_KC * TC_GMAX * 16;  // fixed stride (largest group)
   uint64_t* bars = (uint64_t*)(smem + 2 * stage_bytes);  // full[0..1], done[0..1]
   uint32_t* tslot = (uint32_t*)(bars + 4);
   int* fail = (int*)(tslot + 1);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * TC_M;
-  const uint32_t ncols = p.Npad > 256 ? 512u : (p.Npad > 128 ? 256u : (p.Npad > 64 ? 128u : (p.Npad > 32 ? 64u : 32u)));
+  const uint32_t ncols = npad > 128 ? 256u : (npad > 64 ? 128u : (npad > 32 ? 64u : 32u));
   const uint32_t bar0 = s_addr(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto done = [&](int s) { return bar0 + 16u + 8u * s; };
+  // this group's basis: the groups before it hold nk stages of 2 terms of gpad rows each
+  const uint8_t* W = p.W + (size_t)grp * p.nk * 2 * TC_KC * gpad * 16;
 
   if (tid == 0) {
     for (int s = 0; s < 4; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s), "r"(1));
@@ -154,8 +174,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
 
-  const int btx = (p.terms == 3 ? 2 : 1) * p.Npad * 128;  // bytes the bulk copy brings
-  const int nchunk = p.Npad > 256 ? 2 : 1;
+  const int btx = (p.terms == 3 ? 2 : 1) * bterm;  // bytes the bulk copy brings
 
   // basis stages 0 and 1 are requested up front; stage kt + 1 is requested as soon as the
   // MMAs of step kt - 1 have released its buffer (right after step kt is committed)
@@ -165,16 +184,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(btx) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(sB)),
-        "l"(p.W + (size_t)kt * bstage), "r"(btx), "r"(full(st))
+        "l"(W + (size_t)kt * bstage), "r"(btx), "r"(full(st))
         : "memory");
   };
   if (tid == 0) {
     issue_b(0);
     if (p.nk > 1) issue_b(1);
   }
-  // data stage in registers: thread t holds rows (t >> 5) + 8 i, k pair (t & 31) * 2
   float2 xr[A_PER_THREAD];
-  load_stage(p, m0, 0, tid, xr);
+  load_stage(p, m0, 0, warp, lane, xr);
+  const uint32_t id = idesc(npad);
 
   for (int kt = 0; kt < p.nk; ++kt) {
     const int st = kt & 1;
@@ -185,8 +204,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     }
     __syncthreads();
     if (*fail) break;
-    store_stage(sA, tid, xr);
-    if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, tid, xr);  // in flight during the MMAs
+    store_stage(sA, warp, lane, xr);
+    if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, warp, lane, xr);  // in flight during the MMAs
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -194,20 +213,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
         *fail = 1;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t aHi = s_addr(sA), aLo = aHi + A_TILE, bHi = s_addr(sB), bLo = bHi + p.Npad * 128;
+        const uint32_t aHi = s_addr(sA), aLo = aHi + A_TILE, bHi = s_addr(sB), bLo = bHi + bterm;
+        const uint32_t b_lbo = (uint32_t)npad * 16;
 #pragma unroll
         for (int kk = 0; kk < TC_KT / 16; ++kk) {
-          for (int c = 0; c < nchunk; ++c) {
-            const int n0 = c * 128;
-            const int nc = (nchunk == 1) ? p.Npad : (c == 0 ? 128 : p.Npad - 128);
-            const uint32_t id = idesc(nc);
-            const uint32_t t = tmem + (uint32_t)n0;
-            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-            const uint64_t ah = sdesc(aHi + kk * 32), bh = sdesc(bHi + n0 * 128 + kk * 32);
-            mma(t, ah, bh, id, acc);
-            if (p.terms >= 2) mma(t, sdesc(aLo + kk * 32), bh, id, 1u);
-            if (p.terms >= 3) mma(t, ah, sdesc(bLo + n0 * 128 + kk * 32), id, 1u);
-          }
+          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t ah = sdesc(aHi + kk * 2 * A_LBO, A_LBO, 128);
+          const uint64_t bh = sdesc(bHi + kk * 2 * b_lbo, b_lbo, 128);
+          mma(tmem, ah, bh, id, acc);
+          if (p.terms >= 2) mma(tmem, sdesc(aLo + kk * 2 * A_LBO, A_LBO, 128), bh, id, 1u);
+          if (p.terms >= 3) mma(tmem, ah, sdesc(bLo + kk * 2 * b_lbo, b_lbo, 128), id, 1u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
                      : "memory");
@@ -232,56 +247,64 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!*fail) {
     const int g = warp & 3, h = warp >> 2;
-    const int half = p.Npad / 2;
+    const int half = ((npad / 8 + 1) / 2) * 8;  // columns of warp half 0 (multiple of 8)
+    const int cbeg = h ? half : 0, cend = h ? npad : half;
     const int r = 32 * g + lane;  // row within the tile = tensor-memory lane
     const int row = m0 + r;
     const bool live = row < p.M_total;
-    // row-major output goes through shared memory (stride P + 1) so that the tile, one
-    // contiguous chunk of rows * P floats in global memory, is written coalesced
-    float* stile = (float*)smem;
-    const int sld = p.P + 1;
-    int64_t obase = 0;
     if (p.transposed) {
       const int plane = row / p.R, rr = row - plane * p.R;
-      obase = (int64_t)plane * p.R * p.P + rr;
-    }
-    for (int c0 = h * half; c0 < (h + 1) * half; c0 += 8) {
-      uint32_t v[8];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-          : "r"(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int64_t obase = (int64_t)plane * p.R * p.P + rr;
+      for (int cc = cbeg; cc < cend; cc += 8) {
+        uint32_t v[8];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+            : "r"(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)cc));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int col = c0 + j;
-        if (col >= p.P) continue;
-        if (p.transposed) {
-          if (live) p.out[obase + (int64_t)col * p.R] = __uint_as_float(v[j]);
-        } else {
-          stile[r * sld + col] = __uint_as_float(v[j]);
-        }
+        for (int j = 0; j < 8; ++j)
+          if (cc + j < pc && live) p.out[obase + (int64_t)(c0 + cc + j) * p.R] = __uint_as_float(v[j]);
       }
-    }
-    if (!p.transposed) {
-      __syncthreads();
-      const int rows = min(TC_M, p.M_total - m0);
-      float* dst = p.out + (int64_t)m0 * p.P;
-      if ((p.P & 3) == 0) {
-        // rows of P floats, 16-byte aligned: one warp per row, float4 stores
-        const int q4 = p.P >> 2;
-        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
-          const float* srow = stile + rr * sld;
-          float4* drow = (float4*)(dst + (int64_t)rr * p.P);
-          for (int c4 = lane; c4 < q4; c4 += 32)
-            drow[c4] = make_float4(srow[4 * c4], srow[4 * c4 + 1], srow[4 * c4 + 2], srow[4 * c4 + 3]);
+    } else {
+      // row-major: 64 rows at a time through shared memory (stride pc + 1), then each warp
+      // copies whole rows of pc floats to out[row * P + c0 ..]
+      float* stile = (float*)smem;
+      const int sld = pc + 1;
+      for (int pass = 0; pass < 2; ++pass) {
+        if ((g >> 1) == pass) {
+          const int rl = r - 64 * pass;
+          for (int cc = cbeg; cc < cend; cc += 8) {
+            uint32_t v[8];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                : "r"(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)cc));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (cc + j < pc) stile[rl * sld + cc + j] = __uint_as_float(v[j]);
+          }
         }
-      } else {
-        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
-          const float* srow = stile + rr * sld;
-          float* drow = dst + (int64_t)rr * p.P;
-          for (int cc = lane; cc < p.P; cc += 32) drow[cc] = srow[cc];
+        __syncthreads();
+        const int rows = min(64, p.M_total - (m0 + 64 * pass));
+        float* dst = p.out + (int64_t)(m0 + 64 * pass) * p.P + c0;
+        if ((p.P & 3) == 0 && (pc & 3) == 0 && (c0 & 3) == 0) {
+          const int q4 = pc >> 2;
+          for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
+            const float* srow = stile + rr * sld;
+            float4* drow = (float4*)(dst + (int64_t)rr * p.P);
+            for (int c4 = lane; c4 < q4; c4 += 32)
+              drow[c4] = make_float4(srow[4 * c4], srow[4 * c4 + 1], srow[4 * c4 + 2], srow[4 * c4 + 3]);
+          }
+        } else {
+          for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
+            const float* srow = stile + rr * sld;
+            float* drow = dst + (int64_t)rr * p.P;
+            for (int cc = lane; cc < pc; cc += 32) drow[cc] = srow[cc];
+          }
         }
+        __syncthreads();
       }
     }
   } else if (tid == 0) {
@@ -307,47 +330,52 @@ float from_bf16(uint16_t b) {
   return f;
 }
 
+int tc_groups(int P) { return (P + TC_GMAX - 1) / TC_GMAX; }
+int tc_gcols(int P) { return round16((P + tc_groups(P) - 1) / tc_groups(P)); }
+
 }  // namespace
 
-int tc_npad(int P) {
-  int n = ((P + 15) / 16) * 16;
-  return n < 16 ? 16 : n;
-}
+int tc_npad(int P) { return round16(P < 16 ? 16 : P); }
 
 int tc_nk(int K) { return (K + TC_KT - 1) / TC_KT; }
 
-size_t tc_smem_bytes(int Npad) { return 2 * (size_t)(2 * A_TILE + 2 * Npad * 128) + 64 + 1024; }
+// two stages of data (2 x 8 KB) and basis (2 terms x 4 core-matrix columns x 256 rows x 16 B)
+size_t tc_smem_bytes(int) { return 2 * (size_t)(2 * A_TILE + 2 * TC_KC * TC_GMAX * 16) + 64 + 1024; }
 
-// Basis B (P x K, row-major, FP64) as BF16 hi/lo tiles in the swizzled K-major layout the
-// kernel's shared memory uses: tile (kt, term) holds rows n < Npad, k in [64 kt, 64 kt+64).
+// Basis B (P x K, row-major, FP64) as BF16 hi/lo tiles in the kernel's shared-memory
+// layout, per column group g (columns [g G, g G + G), G = tc_gcols(P), rows padded to a
+// multiple of 16): stage kt, term, core-matrix column kc, row n: 16 bytes at
+// ((kt * 2 + term) * 4 + kc) * npad_g * 16 + n * 16.
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out) {
-  const int Npad = tc_npad(P), nk = tc_nk(K);
-  out.assign((size_t)nk * 2 * Npad * 128, 0);
-  for (int kt = 0; kt < nk; ++kt) {
-    for (int n = 0; n < Npad; ++n) {
-      for (int kl = 0; kl < TC_KT; ++kl) {
-        const int k = kt * TC_KT + kl;
-        double w = (n < P && k < K) ? B[(size_t)n * K + k] : 0.0;
-        const uint16_t hi = to_bf16((float)w);
-        const uint16_t lo = to_bf16((float)(w - (double)from_bf16(hi)));
-        const size_t off = (size_t)n * 128 + ((((kl >> 3) ^ (n & 7)) << 4)) + (kl & 7) * 2;
-        uint8_t* base = out.data() + (size_t)kt * 2 * Npad * 128;
-        std::memcpy(base + off, &hi, 2);
-        std::memcpy(base + (size_t)Npad * 128 + off, &lo, 2);
-      }
-    }
+  const int nk = tc_nk(K), ng = tc_groups(P), G = tc_gcols(P);
+  out.assign((size_t)ng * nk * 2 * TC_KC * G * 16, 0);
+  for (int grp = 0; grp < ng; ++grp) {
+    const int c0 = grp * G, pc = std::min(G, P - c0), npad = round16(pc);
+    uint8_t* gbase = out.data() + (size_t)grp * nk * 2 * TC_KC * G * 16;
+    for (int kt = 0; kt < nk; ++kt)
+      for (int n = 0; n < npad; ++n)
+        for (int kl = 0; kl < TC_KT; ++kl) {
+          const int k = kt * TC_KT + kl;
+          const double w = (n < pc && k < K) ? B[(size_t)(c0 + n) * K + k] : 0.0;
+          const uint16_t hi = to_bf16((float)w);
+          const uint16_t lo = to_bf16((float)(w - (double)from_bf16(hi)));
+          const int kc = kl / 8, e = kl % 8;
+          const size_t off_hi = ((size_t)(kt * 2 + 0) * TC_KC + kc) * npad * 16 + (size_t)n * 16 + e * 2;
+          const size_t off_lo = ((size_t)(kt * 2 + 1) * TC_KC + kc) * npad * 16 + (size_t)n * 16 + e * 2;
+          std::memcpy(gbase + off_hi, &hi, 2);
+          std::memcpy(gbase + off_lo, &lo, 2);
+        }
   }
 }
 
-// Largest axis length the tensor-core transform takes: two stages of data (32 KB) and
-// basis (2 x Npad x 128 B) must fit in 227 KB of shared memory.
-int tc_max_axis() { return 320; }
+// Largest axis length the tensor-core transform takes (two column groups of 256).
+int tc_max_axis() { return 2 * TC_GMAX; }
 
 int tc_configure() {
   static int done = 0;
   if (done) return HELM6_OK;
-  const size_t maxs = tc_smem_bytes(tc_npad(tc_max_axis()));
-  if (cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxs) != cudaSuccess)
+  if (cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(0)) !=
+      cudaSuccess)
     return HELM6_ERR_CUDA;
   done = 1;
   return HELM6_OK;
@@ -362,15 +390,16 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   a.M_total = M_total;
   a.K = K;
   a.P = P;
-  a.Npad = tc_npad(P);
   a.nk = tc_nk(K);
   a.terms = terms;
   a.transposed = transposed;
   a.R = R;
+  a.ngroups = tc_groups(P);
+  a.gcols = tc_gcols(P);
   a.err = err;
-  const unsigned grid = (unsigned)((M_total + TC_M - 1) / TC_M);
+  const unsigned grid = (unsigned)(((M_total + TC_M - 1) / TC_M) * a.ngroups);
   note_launch();
-  xform_tc_kernel<<<grid, TC_THREADS, tc_smem_bytes(a.Npad), s>>>(a);
+  xform_tc_kernel<<<grid, TC_THREADS, tc_smem_bytes(0), s>>>(a);
 }
 
 }  // namespace helm6

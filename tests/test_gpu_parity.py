@@ -76,6 +76,18 @@ def test_apply_Pinv_mixed(H, n, k, faces):
     assert rel2(y, ref) < 1e-4
 
 
+def test_apply_Pinv_mixed_two_column_groups(H):
+    """Axes longer than 256 points: the tensor-core transform splits its output columns
+    into two groups (here every axis has 257 points)."""
+    n, k, faces = 257, 30.0 + 0.3j, "DDDDDD"
+    prob = O.Problem(n, k, faces)
+    x = inputs.complex_normal(401, prob.shape)
+    with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES) as s:
+        y = s.apply_Pinv(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = O.Preconditioner(prob)(x)
+    assert rel2(y, ref) < 1e-4
+
+
 @pytest.mark.parametrize("n,k,faces", [(37, 9.0 + 0.3j, "DDNNSS"), (30, 11.0, "NNNNNN"),
                                        (26, 8.0, "DNNDSN")])
 def test_rhs_gaussians(H, n, k, faces):
