@@ -289,20 +289,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
         __syncthreads();
         const int rows = min(64, p.M_total - (m0 + 64 * pass));
         float* dst = p.out + (int64_t)(m0 + 64 * pass) * p.P + c0;
-        if ((p.P & 3) == 0 && (pc & 3) == 0 && (c0 & 3) == 0) {
-          const int q4 = pc >> 2;
-          for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
-            const float* srow = stile + rr * sld;
-            float4* drow = (float4*)(dst + (int64_t)rr * p.P);
-            for (int c4 = lane; c4 < q4; c4 += 32)
-              drow[c4] = make_float4(srow[4 * c4], srow[4 * c4 + 1], srow[4 * c4 + 2], srow[4 * c4 + 3]);
-          }
-        } else {
-          for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
-            const float* srow = stile + rr * sld;
-            float* drow = dst + (int64_t)rr * p.P;
-            for (int cc = lane; cc < pc; cc += 32) drow[cc] = srow[cc];
-          }
+        // consecutive lanes on consecutive words: conflict-free reads, 128-byte stores
+        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
+          const float* srow = stile + rr * sld;
+          float* drow = dst + (int64_t)rr * p.P;
+          for (int cc = lane; cc < pc; cc += 32) drow[cc] = srow[cc];
         }
         __syncthreads();
       }
