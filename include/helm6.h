@@ -152,6 +152,18 @@ int helm6_solve(helm6_ctx* ctx, const void* F, void* u, double tol, int restart,
 int helm6_rhs_gaussians(helm6_ctx* ctx, int nsrc, const double* centers,
                         const helm6_c64* amps, double sigma, const void* noise, void* F);
 
+/* Compact right side F (Eq. scheme right side with the Eq. 3DN / Eq. 3DDISCS face terms of
+ * homogeneous face data, as helm6_rhs_gaussians) for a separable source
+ *     f(x, y, z) = sum_t coef[t] X_t(x) Y_t(y) Z_t(z),
+ * given by its factors' derivatives of order 0..4 at the unknown nodes: tables is a HOST
+ * array of complex values [nterms][3 axes x, y, z][5 orders][mmax], mmax = the largest of
+ * the three unknown counts of helm6_dims; entry p of an axis is the factor's derivative at
+ * that axis' p-th unknown, which lies at x = (p + 1) h if the axis' lower face is
+ * Dirichlet and at x = p h otherwise (entries beyond the axis length are ignored).  F:
+ * DEVICE complex128 output.  0 <= nterms <= 4096.  Returns OK, INVALID, NOMEM or CUDA. */
+int helm6_rhs_separable(helm6_ctx* ctx, int nterms, const helm6_c64* coef, const helm6_c64* tables,
+                        void* F);
+
 /* ---- Measurement (not part of the method) ----
  * Per-phase device time of helm6_solve / helm6_apply_* measured with CUDA events on the
  * context's stream, and the number of kernels the library launched.  Off by default;

@@ -1072,4 +1072,10 @@ int helm6_rhs_gaussians(helm6_ctx* c, int nsrc, const double* centers, const hel
                        (double*)F, c->stream);
 }
 
+int helm6_rhs_separable(helm6_ctx* c, int nterms, const helm6_c64* coef, const helm6_c64* tables, void* F) {
+  if (!c || !F || nterms < 0 || nterms > 4096) return HELM6_ERR_INVALID;
+  if (nterms > 0 && (!coef || !tables)) return HELM6_ERR_INVALID;
+  return rhs_separable(c->g, c->h, c->k, nterms, (const double*)coef, (const double*)tables, (double*)F, c->stream);
+}
+
 }  // extern "C"

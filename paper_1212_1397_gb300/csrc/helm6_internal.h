@@ -165,6 +165,10 @@ void launch_backsolve(const double* H, int ldh, int j, const double* g, double* 
 // centers: host nsrc*3, amps: host nsrc*2 (re, im); noise: device complex128 or nullptr.
 int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
                   double sigma, const double* noise, double* F, cudaStream_t s);
+// Compact right side for f = sum_t coef_t X_t Y_t Z_t from complex host tables
+// [nterm][3][5][max(mx, my, mz)] of the factors' derivatives 0..4 at the unknown nodes.
+int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, const double* tables, double* F,
+                  cudaStream_t s);
 
 // y += alpha x (planar, 2N reals), mixed input/output precision.
 template <typename TI, typename TO>

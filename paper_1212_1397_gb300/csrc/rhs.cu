@@ -1,4 +1,5 @@
-// Compact right side F of the sixth-order scheme for sums of Gaussian sources (FP64).
+// Compact right side F of the sixth-order scheme for separable sources (FP64): sums of
+// Gaussian sources, or any f = sum_t c_t X_t(x) Y_t(y) Z_t(z) given by 1D derivative tables.
 //
 // Interior (Eq. scheme right side, h^2-scaled; the mixed fourth derivatives carry the
 // total weight h^4/90 that makes the scheme sixth order):
@@ -8,8 +9,8 @@
 //   F -= D_N,  D_N = dn1 f_n + dn3 f_nnn + dnm (f_ntt + f_nss)
 // Sommerfeld-like face rows (Eq. 3DDISCS), fbar = exp(ik n) f in the inward normal n:
 //   F -= D_S,  D_S = -e^{ikh} mu3 [ 2h Fbar + mu1 (h^5/3)(fbar_ntt + fbar_nss) ].
-// A Gaussian is separable, so each source contributes products of 1D derivatives
-// G_a^(m)(x_a), m = 0..4, tabulated per axis by the host.
+// Each separable term contributes products of its factors' 1D derivatives X^(m)(x),
+// m = 0..4, tabulated (complex) per axis at the unknown nodes by the host.
 #include <algorithm>
 #include <cmath>
 
@@ -34,15 +35,19 @@ using Z = cpx<double>;
 
 __device__ __forceinline__ Z zc(c64d a) { return Z{a.re, a.im}; }
 
-// Source-summed derivative f^(ox, oy, oz) at node (i, j, l).
-__device__ __forceinline__ Z deriv(const double* tab, const double* amps, int nsrc, int mmax, int i, int j,
+// Complex table entry: term k, axis a, derivative order m, unknown node p.
+__device__ __forceinline__ Z tv(const double* tab, int mmax, int k, int a, int m, int p) {
+  const int64_t o = (((int64_t)k * 3 + a) * 5 + m) * mmax + p;
+  return Z{tab[2 * o], tab[2 * o + 1]};
+}
+
+// Term-summed derivative f^(ox, oy, oz) at node (i, j, l).
+__device__ __forceinline__ Z deriv(const double* tab, const double* coef, int nterm, int mmax, int i, int j,
                                    int l, int ox, int oy, int oz) {
   Z s = Z{0.0, 0.0};
-  for (int k = 0; k < nsrc; ++k) {
-    const double* t = tab + (int64_t)k * 15 * mmax;
-    const double v = t[(0 * 5 + ox) * mmax + i] * t[(1 * 5 + oy) * mmax + j] * t[(2 * 5 + oz) * mmax + l];
-    s.re += amps[2 * k] * v;
-    s.im += amps[2 * k + 1] * v;
+  for (int k = 0; k < nterm; ++k) {
+    const Z v = tv(tab, mmax, k, 0, ox, i) * tv(tab, mmax, k, 1, oy, j) * tv(tab, mmax, k, 2, oz, l);
+    s = s + Z{coef[2 * k], coef[2 * k + 1]} * v;
   }
   return s;
 }
@@ -57,23 +62,22 @@ __global__ void rhs_kernel(Geom g, RhsCoef c, int nsrc, int mmax, const double* 
   const int l = (int)(idx / ((int64_t)g.mx * g.my));
   Z S0{0, 0}, S1{0, 0}, S2{0, 0}, S3{0, 0};
   for (int k = 0; k < nsrc; ++k) {
-    const double* t = tab + (int64_t)k * 15 * mmax;
-    double gx[5], gy[5], gz[5];
+    Z gx[5], gy[5], gz[5];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-      gx[m] = t[(0 * 5 + m) * mmax + i];
-      gy[m] = t[(1 * 5 + m) * mmax + j];
-      gz[m] = t[(2 * 5 + m) * mmax + l];
+      gx[m] = tv(tab, mmax, k, 0, m, i);
+      gy[m] = tv(tab, mmax, k, 1, m, j);
+      gz[m] = tv(tab, mmax, k, 2, m, l);
     }
-    const double f0 = gx[0] * gy[0] * gz[0];
-    const double lap = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2];
-    const double p4 = gx[4] * gy[0] * gz[0] + gx[0] * gy[4] * gz[0] + gx[0] * gy[0] * gz[4];
-    const double m4 = gx[2] * gy[2] * gz[0] + gx[2] * gy[0] * gz[2] + gx[0] * gy[2] * gz[2];
+    const Z f0 = gx[0] * gy[0] * gz[0];
+    const Z lap = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2];
+    const Z p4 = gx[4] * gy[0] * gz[0] + gx[0] * gy[4] * gz[0] + gx[0] * gy[0] * gz[4];
+    const Z m4 = gx[2] * gy[2] * gz[0] + gx[2] * gy[0] * gz[2] + gx[0] * gy[2] * gz[2];
     const Z a = Z{amps[2 * k], amps[2 * k + 1]};
-    S0 = S0 + f0 * a;
-    S1 = S1 + lap * a;
-    S2 = S2 + p4 * a;
-    S3 = S3 + m4 * a;
+    S0 = S0 + a * f0;
+    S1 = S1 + a * lap;
+    S2 = S2 + a * p4;
+    S3 = S3 + a * m4;
   }
   const double h = c.h, h2 = h * h, h4 = h2 * h2;
   Z Fv = zc(c.cf) * S0 + zc(c.q1) * S1 + (h4 / 360.0) * S2 + (h4 / 90.0) * S3;
@@ -123,41 +127,18 @@ __global__ void rhs_kernel(Geom g, RhsCoef c, int nsrc, int mmax, const double* 
 
 }  // namespace
 
-// Host side: 1D derivative tables G^(m)(x) = (-1/sigma)^m He_m(t) exp(-t^2/2), t = (x-c)/sigma,
-// with He the probabilists' Hermite polynomials, at the unknown nodes of each axis.
-int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
-                  double sigma, const double* noise, double* F, cudaStream_t s) {
-  const int mmax = std::max(g.mx, std::max(g.my, g.mz));
-  const int mdim[3] = {g.mx, g.my, g.mz};
-  std::vector<double> tab((size_t)std::max(nsrc, 1) * 15 * mmax, 0.0);
-  for (int src = 0; src < nsrc; ++src) {
-    for (int ax = 0; ax < 3; ++ax) {
-      const int start = (g.face[2 * ax] == HELM6_DIRICHLET) ? 1 : 0;
-      for (int p = 0; p < mdim[ax]; ++p) {
-        const double x = (start + p) * h;
-        const double t = (x - centers[3 * src + ax]) / sigma;
-        const double e = std::exp(-0.5 * t * t);
-        double he[5];
-        he[0] = 1.0;
-        he[1] = t;
-        for (int m = 1; m < 4; ++m) he[m + 1] = t * he[m] - m * he[m - 1];
-        double sc = 1.0;
-        for (int m = 0; m < 5; ++m) {
-          tab[((size_t)src * 15 + ax * 5 + m) * mmax + p] = sc * he[m] * e;
-          sc *= -1.0 / sigma;
-        }
-      }
-    }
-  }
-  double *dtab = nullptr, *damps = nullptr;
+// Upload the complex tables [nterm][3][5][mmax] and coefficients, launch, free.
+int launch_rhs(const Geom& g, double h, cd k, int nterm, int mmax, const std::vector<double>& tab,
+               const double* coef, const double* noise, double* F, cudaStream_t s) {
+  double *dtab = nullptr, *dcoef = nullptr;
   if (cudaMallocAsync((void**)&dtab, tab.size() * sizeof(double), s) != cudaSuccess) return HELM6_ERR_NOMEM;
-  if (cudaMallocAsync((void**)&damps, (size_t)std::max(nsrc, 1) * 2 * sizeof(double), s) != cudaSuccess) {
+  if (cudaMallocAsync((void**)&dcoef, (size_t)std::max(nterm, 1) * 2 * sizeof(double), s) != cudaSuccess) {
     cudaFreeAsync(dtab, s);
     return HELM6_ERR_NOMEM;
   }
   cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (nsrc > 0)
-    cudaMemcpyAsync(damps, amps, (size_t)nsrc * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (nterm > 0)
+    cudaMemcpyAsync(dcoef, coef, (size_t)nterm * 2 * sizeof(double), cudaMemcpyHostToDevice, s);
 
   RhsCoef c;
   const cd I(0.0, 1.0);
@@ -181,10 +162,50 @@ int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers
 
   const int bs = 256;
   note_launch();
-  rhs_kernel<<<(unsigned)((g.N + bs - 1) / bs), bs, 0, s>>>(g, c, nsrc, mmax, dtab, damps, noise, F);
+  rhs_kernel<<<(unsigned)((g.N + bs - 1) / bs), bs, 0, s>>>(g, c, nterm, mmax, dtab, dcoef, noise, F);
   cudaFreeAsync(dtab, s);
-  cudaFreeAsync(damps, s);
+  cudaFreeAsync(dcoef, s);
   return cudaGetLastError() == cudaSuccess ? HELM6_OK : HELM6_ERR_CUDA;
+}
+
+// Gaussian sources: 1D derivative tables G^(m)(x) = (-1/sigma)^m He_m(t) exp(-t^2/2),
+// t = (x-c)/sigma, with He the probabilists' Hermite polynomials, at the unknown nodes of
+// each axis (real, stored as complex with zero imaginary part).
+int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers, const double* amps,
+                  double sigma, const double* noise, double* F, cudaStream_t s) {
+  const int mmax = std::max(g.mx, std::max(g.my, g.mz));
+  const int mdim[3] = {g.mx, g.my, g.mz};
+  std::vector<double> tab((size_t)std::max(nsrc, 1) * 15 * mmax * 2, 0.0);
+  for (int src = 0; src < nsrc; ++src) {
+    for (int ax = 0; ax < 3; ++ax) {
+      const int start = (g.face[2 * ax] == HELM6_DIRICHLET) ? 1 : 0;
+      for (int p = 0; p < mdim[ax]; ++p) {
+        const double x = (start + p) * h;
+        const double t = (x - centers[3 * src + ax]) / sigma;
+        const double e = std::exp(-0.5 * t * t);
+        double he[5];
+        he[0] = 1.0;
+        he[1] = t;
+        for (int m = 1; m < 4; ++m) he[m + 1] = t * he[m] - m * he[m - 1];
+        double sc = 1.0;
+        for (int m = 0; m < 5; ++m) {
+          tab[2 * (((size_t)src * 3 + ax) * 5 + m) * mmax + 2 * (size_t)p] = sc * he[m] * e;
+          sc *= -1.0 / sigma;
+        }
+      }
+    }
+  }
+  return launch_rhs(g, h, k, nsrc, mmax, tab, amps, noise, F, s);
+}
+
+// Separable source given by the caller's complex tables [nterm][3][5][mmax] (mmax the
+// largest axis length), entry p of an axis = the factor's derivative at its p-th unknown.
+int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, const double* tables, double* F,
+                  cudaStream_t s) {
+  const int mmax = std::max(g.mx, std::max(g.my, g.mz));
+  std::vector<double> tab((size_t)std::max(nterm, 1) * 15 * mmax * 2, 0.0);
+  if (nterm > 0) std::copy(tables, tables + (size_t)nterm * 15 * mmax * 2, tab.begin());
+  return launch_rhs(g, h, k, nterm, mmax, tab, coef, nullptr, F, s);
 }
 
 }  // namespace helm6

@@ -30,7 +30,7 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", 
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
            "helm6_cnn_train_step", "helm6_cnn_set_residual_loss", "helm6_cnn_get_params",
-           "helm6_cnn_trainer_destroy", "helm6_solve_batch")
+           "helm6_cnn_trainer_destroy", "helm6_solve_batch", "helm6_rhs_separable")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
           "gs_update", "gs_small", "resid64", "other", "cnn")
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_cnn_get_params.restype = I
     lib.helm6_cnn_trainer_destroy.argtypes = [P]
     lib.helm6_cnn_trainer_destroy.restype = None
+    lib.helm6_rhs_separable.argtypes = [P, I, C.POINTER(C64), C.POINTER(C64), P]
+    lib.helm6_rhs_separable.restype = I
     lib.helm6_solve_batch.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), D, I, I, I,
                                       C.POINTER(Stats)]
     lib.helm6_solve_batch.restype = I
@@ -270,6 +272,20 @@ class Solver:
         p = Profile()
         _check(self._lib.helm6_profile_read(self._ctx, C.byref(p)), "helm6_profile_read")
         return p.to_dict()
+
+    def rhs_separable(self, coef, tables, F=None):
+        """Compact right side of f = sum_t coef[t] X_t Y_t Z_t; tables: complex array
+        [nterms, 3, 5, max(dims)] of the factors' derivatives 0..4 at the unknown nodes."""
+        import numpy as np
+        F = self.empty() if F is None else F
+        cf = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128).ravel())
+        tb = np.ascontiguousarray(np.asarray(tables, dtype=np.complex128))
+        nt = cf.size
+        if tb.shape != (nt, 3, 5, max(self.dims)):
+            raise ValueError(f"tables must have shape {(nt, 3, 5, max(self.dims))}, got {tb.shape}")
+        _check(self._lib.helm6_rhs_separable(self._ctx, nt, cf.ctypes.data_as(C.POINTER(C64)),
+                                             tb.ctypes.data_as(C.POINTER(C64)), _ptr(F)), "helm6_rhs_separable")
+        return F
 
     def rhs_gaussians(self, sources, noise=None, F=None):
         """Compact right side for helm6_inputs.GaussianSources (+ optional noise tensor)."""
