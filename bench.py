@@ -147,6 +147,33 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+# ---- replicas over ranks (N > 1: one independent problem per rank, no data-path collective) ----
+
+def replica_seeds(rank):
+    """Seeds of rank `rank`'s replica: its Gaussian sources and its noise field."""
+    return 1000 + rank, 2000 + rank
+
+
+def sync_all(dist, cuda=True):
+    """Device synchronisation, then a barrier over the ranks (when there are several)."""
+    if cuda:
+        import torch
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+
+def reduce_max(x, dist):
+    """Largest value of x over the ranks (the slowest rank's time)."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, cfg, rank, world):
     """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -215,24 +242,13 @@ def main():
     solver = H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=restart,
                       stream=stream)
     N = solver.shape[0] * solver.shape[1] * solver.shape[2]
-    src = inputs.gaussian_sources(1000 + rank, n, cfg.get("nsrc", 8))
+    src_seed, noise_seed = replica_seeds(rank)
+    src = inputs.gaussian_sources(src_seed, n, cfg.get("nsrc", 8))
     noise = None
     if cfg.get("noise", 0.0) > 0:
-        noise = torch.from_numpy(cfg["noise"] * inputs.complex_normal(2000 + rank, solver.shape)).cuda()
+        noise = torch.from_numpy(cfg["noise"] * inputs.complex_normal(noise_seed, solver.shape)).cuda()
     F = solver.rhs_gaussians(src, noise=noise)
     u = solver.empty()
-
-    def sync_all():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-
-    def reduce_max(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- warm-up ----
     st = None
@@ -242,7 +258,7 @@ def main():
 
     # ---- timed region: device-resident F ----
     clocks = ClockSampler(local)
-    sync_all()
+    sync_all(dist)
     clocks.start()
     solver.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -253,18 +269,18 @@ def main():
         _, st = solver.solve(F, u, tol=tol, restart=restart, maxit=1000)
         stats.append(st)
     ev1.record(stream)
-    sync_all()
+    sync_all(dist)
     clk = clocks.stop()
     prof = solver.profile_read()
     solver.profile(False)
-    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps)
+    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist)
 
     # ---- e2e: host buffers through the same public API ----
     F_host = F.cpu().pin_memory()
     u_host = torch.empty_like(F_host).pin_memory()
     u_dev = solver.empty()
     F_dev = solver.empty()
-    sync_all()
+    sync_all(dist)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -273,8 +289,8 @@ def main():
         solver.solve(F_dev, u_dev, tol=tol, restart=restart, maxit=1000)
         u_host.copy_(u_dev, non_blocking=True)
     e1.record(stream)
-    sync_all()
-    e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps)
+    sync_all(dist)
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist)
 
     # ---- mixed + learned second stage (AUTO: one probe cycle, then the better) ----
     learned = None
@@ -287,13 +303,13 @@ def main():
             u.zero_()
             solver.solve(F, u, tol=tol, restart=restart, maxit=1000)  # warm-up
             u.zero_()
-            sync_all()
+            sync_all(dist)
             l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             l0.record(stream)
             _, stl = solver.solve(F, u, tol=tol, restart=restart, maxit=1000)
             l1.record(stream)
-            sync_all()
-            learned = {"ms": reduce_max(l0.elapsed_time(l1)), "iters": stl["iters"], "outer": stl["outer"],
+            sync_all(dist)
+            learned = {"ms": reduce_max(l0.elapsed_time(l1), dist), "iters": stl["iters"], "outer": stl["outer"],
                        "learned_cycles": stl["cnn_cycles"], "relres": stl["relres"], "status": stl["status"],
                        "mode": "auto", "weights": os.path.basename(wfile)}
             solver.set_cnn(w["theta"], 1.0, H.CNN_OFF)
@@ -307,14 +323,14 @@ def main():
         u64 = solver64.empty()
         solver64.solve(F, u64, tol=tol, restart=restart, maxit=1000)  # warm-up
         u64.zero_()
-        sync_all()
+        sync_all(dist)
         p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         p0.record(stream)
         _, st64 = solver64.solve(F, u64, tol=tol, restart=restart, maxit=1000)
         p1.record(stream)
-        sync_all()
+        sync_all(dist)
         diff = float(torch.linalg.vector_norm(u_mixed - u64) / torch.linalg.vector_norm(u64))
-        plain = {"ms": reduce_max(p0.elapsed_time(p1)), "iters": st64["iters"],
+        plain = {"ms": reduce_max(p0.elapsed_time(p1), dist), "iters": st64["iters"],
                  "relres": st64["relres"], "status": st64["status"],
                  "mixed_vs_fp64_rel_l2": diff}
         solver64.close()
