@@ -135,6 +135,7 @@ __device__ __forceinline__ void store_stage(uint8_t* sA, int warp, int lane, con
 }
 
 __host__ __device__ __forceinline__ int round16(int n) { return ((n + 15) / 16) * 16; }
+int tc_nk_(int K) { return (K + TC_KT - 1) / TC_KT; }
 
 __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
@@ -321,8 +322,76 @@ float from_bf16(uint16_t b) {
   return f;
 }
 
-int tc_groups(int P) { return (P + TC_GMAX - 1) / TC_GMAX; }
-int tc_gcols(int P) { return round16((P + tc_groups(P) - 1) / tc_groups(P)); }
+// Columns beyond the first 256 computed by the FP32 tail kernel (a few only; more take a
+// second tensor-core column group).
+constexpr int TC_TAILMAX = 32;
+constexpr int TC_TAILK = TC_GMAX + TC_TAILMAX;  // longest row on the tail path (square bases: K = P)
+int tc_tail(int P, int K) { return (P > TC_GMAX && P - TC_GMAX <= TC_TAILMAX && K <= TC_TAILK) ? P - TC_GMAX : 0; }
+int tc_groups(int P, int K) { return tc_tail(P, K) ? 1 : (P + TC_GMAX - 1) / TC_GMAX; }
+int tc_gcols(int P, int K) {
+  return tc_tail(P, K) ? TC_GMAX : round16((P + tc_groups(P, K) - 1) / tc_groups(P, K));
+}
+// Bytes of the tensor-core basis tiles (the tail basis, FP32 rows, follows them).
+size_t tc_tile_bytes(int P, int K) {
+  return (size_t)tc_groups(P, K) * tc_nk_(K) * 2 * TC_KC * tc_gcols(P, K) * 16;
+}
+
+// The last P - 256 output columns: out(row, 256 + c) = sum_k in(row, k) Bt(c, k) in FP32, one
+// warp per row (lanes stride over k, shuffle reduction), Bt staged in shared memory.  TT > 0:
+// that many columns, known at compile time; TT = 0: any T <= TC_TAILMAX.
+template <int TT>
+__global__ void __launch_bounds__(256) xform_tail_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                         const float* __restrict__ Bt, int M_total, int K, int P,
+                                                         int T_rt, int transposed, int R) {
+  constexpr int TM = TT > 0 ? TT : TC_TAILMAX;
+  const int T = TT > 0 ? TT : T_rt;
+  extern __shared__ float sbt[];
+  for (int i = threadIdx.x; i < T * K; i += blockDim.x) sbt[i] = Bt[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t row = (int64_t)blockIdx.x * 8 + warp; row < M_total; row += (int64_t)gridDim.x * 8) {
+    const float* r = in + row * K;
+    float acc[TM];
+#pragma unroll
+    for (int c = 0; c < TM; ++c) acc[c] = 0.f;
+    // the whole row first (K <= 288 on this path: at most 9 values per lane), so that all
+    // of a warp's loads are in flight together
+    float v[TC_TAILK / 32];
+#pragma unroll
+    for (int q = 0; q < TC_TAILK / 32; ++q) {
+      const int k = lane + 32 * q;
+      v[q] = k < K ? __ldg(r + k) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < TC_TAILK / 32; ++q) {
+      const int k = lane + 32 * q;
+      if (k >= K) break;
+      if constexpr (TT > 0) {
+#pragma unroll
+        for (int c = 0; c < TT; ++c) acc[c] = fmaf(v[q], sbt[c * K + k], acc[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < TM; ++c)
+          if (c < T) acc[c] = fmaf(v[q], sbt[c * K + k], acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < TM; ++c) {
+      if (c >= T) break;
+      float x = acc[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == c) {
+        const int col = TC_GMAX + c;
+        if (transposed) {
+          const int64_t plane = row / R, rr = row - plane * R;
+          out[plane * R * P + (int64_t)col * R + rr] = x;
+        } else {
+          out[row * P + col] = x;
+        }
+      }
+    }
+  }
+}
 
 }  // namespace
 
@@ -338,8 +407,14 @@ size_t tc_smem_bytes(int) { return 2 * (size_t)(2 * A_TILE + 2 * TC_KC * TC_GMAX
 // multiple of 16): stage kt, term, core-matrix column kc, row n: 16 bytes at
 // ((kt * 2 + term) * 4 + kc) * npad_g * 16 + n * 16.
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out) {
-  const int nk = tc_nk(K), ng = tc_groups(P), G = tc_gcols(P);
-  out.assign((size_t)ng * nk * 2 * TC_KC * G * 16, 0);
+  const int nk = tc_nk(K), ng = tc_groups(P, K), G = tc_gcols(P, K), T = tc_tail(P, K);
+  const size_t tiles = tc_tile_bytes(P, K);
+  out.assign(tiles + (size_t)T * K * sizeof(float), 0);
+  for (int c = 0; c < T; ++c)
+    for (int k = 0; k < K; ++k) {
+      const float w = (float)B[(size_t)(TC_GMAX + c) * K + k];
+      std::memcpy(out.data() + tiles + ((size_t)c * K + k) * sizeof(float), &w, sizeof(float));
+    }
   for (int grp = 0; grp < ng; ++grp) {
     const int c0 = grp * G, pc = std::min(G, P - c0), npad = round16(pc);
     uint8_t* gbase = out.data() + (size_t)grp * nk * 2 * TC_KC * G * 16;
@@ -385,12 +460,29 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   a.terms = terms;
   a.transposed = transposed;
   a.R = R;
-  a.ngroups = tc_groups(P);
-  a.gcols = tc_gcols(P);
+  a.ngroups = tc_groups(P, K);
+  a.gcols = tc_gcols(P, K);
   a.err = err;
+  a.P = P;
   const unsigned grid = (unsigned)(((M_total + TC_M - 1) / TC_M) * a.ngroups);
   note_launch();
   xform_tc_kernel<<<grid, TC_THREADS, tc_smem_bytes(0), s>>>(a);
+  const int T = tc_tail(P, K);
+  if (T > 0) {
+    static int sms = 0;
+    if (!sms) sms = device_sm_count();
+    const float* Bt = (const float*)(W + tc_tile_bytes(P, K));
+    note_launch();
+    const size_t sm = (size_t)T * K * sizeof(float);
+    const int g = 8 * sms;
+    switch (T) {
+      case 1: xform_tail_kernel<1><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 2: xform_tail_kernel<2><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 3: xform_tail_kernel<3><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 4: xform_tail_kernel<4><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      default: xform_tail_kernel<0><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+    }
+  }
 }
 
 }  // namespace helm6

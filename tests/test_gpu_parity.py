@@ -76,10 +76,12 @@ def test_apply_Pinv_mixed(H, n, k, faces):
     assert rel2(y, ref) < 1e-4
 
 
-def test_apply_Pinv_mixed_two_column_groups(H):
-    """Axes longer than 256 points: the tensor-core transform splits its output columns
-    into two groups (here every axis has 257 points)."""
-    n, k, faces = 257, 30.0 + 0.3j, "DDDDDD"
+@pytest.mark.parametrize("n,faces", [(257, "DDDDDD"), (256, "NNNNDD"), (300, "DDDDDD")])
+def test_apply_Pinv_mixed_long_axes(H, n, faces):
+    """Axes longer than 256 points: up to 288 the tensor-core transform computes 256 output
+    columns and an FP32 tail kernel the rest (257 and 258 points here); beyond, the
+    columns are split into two tensor-core groups (300 points)."""
+    k = 30.0 + 0.3j
     prob = O.Problem(n, k, faces)
     x = inputs.complex_normal(401, prob.shape)
     with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES) as s:
