@@ -77,6 +77,8 @@ struct helm6_ctx {
   };
   std::map<int, StepGraph> step_graphs;
   cudaStream_t cap_stream = nullptr;  // private stream the step graphs are captured on
+  cudaStream_t aux_stream = nullptr;  // side stream of the transforms' FP32 tail columns
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   bool own_stream = false;            // `stream` was created by the context
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
@@ -307,19 +309,19 @@ void precond_tc(helm6_ctx* c, const float* in, float* out) {
   const int terms = c->opts.xform_terms;
   const int rows_x = 2 * g.mz * g.my, rows_y = 2 * g.mz * g.mx;
   cudaEvent_t e = prof_start(c);
-  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s);
+  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
   prof_stop(c, HELM6_PH_XFWD, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s);
+  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
   prof_stop(c, HELM6_PH_YFWD, e);
   e = prof_start(c);
   launch_ztri_apply<float>(g, c->zrinv32, c->zcp32, c->tB32, c->tA32, s);
   prof_stop(c, HELM6_PH_ZTRI, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s);
+  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
   prof_stop(c, HELM6_PH_YINV, e);
   e = prof_start(c);
-  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s);
+  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
   prof_stop(c, HELM6_PH_XINV, e);
 }
 
@@ -710,6 +712,9 @@ void helm6_destroy(helm6_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (auto& kv : c->step_graphs) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->aux_fork) cudaEventDestroy(c->aux_fork);
+  if (c->aux_join) cudaEventDestroy(c->aux_join);
   for (void* p : c->allocs) cudaFree(p);
   cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
@@ -852,6 +857,10 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
         (rc = upt(&c->Wy_tc, Wy, c->g.my)) || (rc = upt(&c->Vy_tc, Vy, c->g.my)))
       return fail(rc);
     if ((rc = dalloc(c, &c->zrinv32, v)) || (rc = dalloc(c, &c->zcp32, v))) return fail(rc);
+    if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(HELM6_ERR_CUDA);
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
     launch_ztri_table<float>(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zrinv32, c->zcp32, c->status, 0, 1);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);

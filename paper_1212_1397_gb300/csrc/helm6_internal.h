@@ -116,8 +116,11 @@ int tc_nk(int K);
 int tc_max_axis();
 int tc_configure();
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out);
+// aux, fork, join (all non-null, or null): a stream and two events that let the FP32 tail
+// columns (257 to 288 output columns) run beside the tensor-core kernel; s waits for them.
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s);
+                     int transposed, int R, int* err, cudaStream_t s, cudaStream_t aux = nullptr,
+                     cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 
 // Tridiagonal solve along z for every (x, y) mode pair, Thomas algorithm started at the
 // Sommerfeld-like end (if any).  x: input, y: output (may alias x), cw: scratch of 2N T.

@@ -448,7 +448,8 @@ int tc_configure() {
 }
 
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s) {
+                     int transposed, int R, int* err, cudaStream_t s, cudaStream_t aux, cudaEvent_t fork,
+                     cudaEvent_t join) {
   TcArgs a;
   a.in = in;
   a.out = out;
@@ -465,6 +466,11 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   a.err = err;
   a.P = P;
   const unsigned grid = (unsigned)(((M_total + TC_M - 1) / TC_M) * a.ngroups);
+  const bool side = tc_tail(P, K) > 0 && aux && fork && join;
+  if (side) {  // fork before the tensor-core kernel so that the tail can start with it
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(aux, fork, 0);
+  }
   note_launch();
   xform_tc_kernel<<<grid, TC_THREADS, tc_smem_bytes(0), s>>>(a);
   const int T = tc_tail(P, K);
@@ -475,12 +481,19 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
     note_launch();
     const size_t sm = (size_t)T * K * sizeof(float);
     const int g = 8 * sms;
+    // with an auxiliary stream the tail runs beside the tensor-core kernel (both only read
+    // `in`, and write disjoint columns of `out`); s waits for it before any later work
+    cudaStream_t ts = side ? aux : s;
     switch (T) {
-      case 1: xform_tail_kernel<1><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 2: xform_tail_kernel<2><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 3: xform_tail_kernel<3><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 4: xform_tail_kernel<4><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      default: xform_tail_kernel<0><<<g, 256, sm, s>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 1: xform_tail_kernel<1><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 2: xform_tail_kernel<2><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 3: xform_tail_kernel<3><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      case 4: xform_tail_kernel<4><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+      default: xform_tail_kernel<0><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
+    }
+    if (ts != s) {
+      cudaEventRecord(join, ts);
+      cudaStreamWaitEvent(s, join, 0);
     }
   }
 }
