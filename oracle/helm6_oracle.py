@@ -532,6 +532,58 @@ def sks(A, M, F, tol=1e-10, maxit=100, diverge=1e3):
                    history=hist)
 
 
+def chebyshev(A, M, F, lo, hi, tol=1e-10, maxit=100, diverge=1e3):
+    """Chebyshev acceleration on A M^{-1} Y = F, U = M^{-1} Y, for a spectrum of A M^{-1} in
+    the real interval [lo, hi], 0 < lo < hi (the theorem of Section 2 with the exact bounds
+    of Eq. 1DEGV / Eq. 3DEGV).  With theta = (hi + lo)/2, delta = (hi - lo)/2 the residual
+    after n steps is T_n((theta - A M^{-1})/delta) r_0 / T_n(theta/delta), built by the
+    three-term recurrence of the Chebyshev polynomials:
+        d_0 = M^{-1} r_0 / theta,  rho_0 = delta/theta;  U += d_n;  r = F - A U;
+        rho_{n+1} = 1 / (2 theta/delta - rho_n),  d_{n+1} = rho_{n+1} rho_n d_n + (2 rho_{n+1}/delta) M^{-1} r.
+    Stops when ||F - A U|| / ||F|| <= tol (or flags divergence like `sks`)."""
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    nF = _norm(F)
+    U = np.zeros_like(F)
+    r = F.copy()
+    rho = delta / theta
+    d = M(r) / theta
+    hist = []
+    eps, it, diverged = np.inf, 0, False
+    while it < maxit:
+        U = U + d
+        r = F - A(U)
+        it += 1
+        eps = _norm(r) / nF
+        hist.append(eps)
+        if eps <= tol:
+            break
+        if not np.isfinite(eps) or eps > diverge:
+            diverged = True
+            break
+        rho_new = 1.0 / (2.0 * theta / delta - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * M(r)
+        rho = rho_new
+    return U, dict(iters=it, relres=eps, converged=eps <= tol, diverged=diverged, history=hist)
+
+
+def dirichlet_ratio_bounds(prob: Problem):
+    """Smallest and largest eigenvalue of A A_p^{-1} on the all-Dirichlet cube (real k).
+
+    Both operators are diagonal on the sine modes (i, j, l): with D_a = -4 sin^2(p_a pi h / 2)
+    the eigenvalue of the sixth-order operator (Eq. scheme in operator form) is
+    sum D_a + a sum_{a<b} D_a D_b + b D_x D_y D_z + kappa, that of the 7-point operator
+    sum D_a + k^2 h^2 (Section 3.4, Eq. 3DEGV)."""
+    assert prob.faces == "DDDDDD" and prob.k.imag == 0.0
+    h, k = prob.h, prob.k.real
+    c = scheme_coefficients(k, h)
+    D = -4.0 * np.sin(np.arange(1, prob.n + 1) * np.pi * h / 2) ** 2
+    Dx, Dy, Dz = D[None, None, :], D[None, :, None], D[:, None, None]
+    lam_a = (Dx + Dy + Dz) + c["a"].real * (Dx * Dy + Dx * Dz + Dy * Dz) + c["b"] * Dx * Dy * Dz + c["kappa"].real
+    lam_p = (Dx + Dy + Dz) + (k * h) ** 2
+    ratio = lam_a / lam_p
+    return float(ratio.min()), float(ratio.max())
+
+
 def psi_order(eps_h: float, eps_gh: float, gamma: float) -> float:
     """Order of the preconditioned matrix from SKS residual ratios on two grids, Eq. PSI.
 
@@ -563,9 +615,13 @@ def solve_dense(prob: Problem, F: np.ndarray) -> np.ndarray:
 
 
 def solve(prob: Problem, F: np.ndarray, tol=1e-12, restart=30, maxit=500, method="gmres"):
-    """Reference discrete solution of A U = F (GMRES or SKS with the direct A_p^{-1})."""
+    """Reference discrete solution of A U = F (GMRES, SKS or, on the all-Dirichlet cube,
+    Chebyshev acceleration with the exact bounds, all with the direct A_p^{-1})."""
     M = Preconditioner(prob)
     A = lambda U: apply_A(prob, U)
     if method == "sks":
         return sks(A, M, F, tol=tol, maxit=maxit)
+    if method == "cheb":
+        lo, hi = dirichlet_ratio_bounds(prob)
+        return chebyshev(A, M, F, lo, hi, tol=tol, maxit=maxit)
     return gmres(A, M, F, tol=tol, restart=restart, maxit=maxit)

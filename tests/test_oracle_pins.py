@@ -397,3 +397,41 @@ def test_gaussian_sources_stay_inside():
     assert np.all(src.centers >= 16 * h - 1e-12) and np.all(src.centers <= 1 - 16 * h + 1e-12)
     np.testing.assert_allclose(np.abs(src.amps), 1.0)
     assert inputs.dims(n, "DDNNSS") == (128, 130, 130)
+
+
+def test_chebyshev_table3_table4_h64():
+    """Chebyshev acceleration with the exact bounds of Eq. 3DEGV (Table 3 / 4, column CA,
+    h = 1/64): 14 (k = 10) and 23 (k = 20) iterations as printed; k = 40, where A A_p^-1 has
+    eigenvalues of both signs, does not converge in 100 (printed "> 100")."""
+    for k, ca in ((10.0, 14), (20.0, 23), (40.0, None)):
+        prob = O.Problem(63, k, "DDDDDD")
+        u = table_u(k, S.sin1d(k * np.pi))
+        F = O.rhs(prob, S.helmholtz_source(u, k))
+        lo, hi = O.dirichlet_ratio_bounds(prob)
+        _, info = O.solve(prob, F, tol=1e-10, maxit=100, method="cheb")
+        if ca is None:
+            assert lo < 0 < hi and not info["converged"]
+        else:
+            assert 0 < lo < hi and info["iters"] == ca, (k, info["iters"])
+
+
+def test_chebyshev_residual_is_the_scaled_chebyshev_polynomial():
+    """On a diagonal operator the residual after n steps is T_n((theta - lam)/delta) /
+    T_n(theta/delta) times r_0, component by component."""
+    lam = np.linspace(0.6, 1.7, 40) + 0j
+    F = inputs.complex_normal(61, (40,))
+    lo, hi = 0.6, 1.7
+    theta, delta = (hi + lo) / 2, (hi - lo) / 2
+    for n in (1, 2, 5, 9):
+        U, info = O.chebyshev(lambda v: lam * v, lambda v: v, F, lo, hi, tol=0.0, maxit=n)
+        T = np.polynomial.chebyshev.Chebyshev.basis(n)
+        ref = T((theta - lam.real) / delta) / T(theta / delta) * F
+        assert np.allclose(F - lam * U, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_dirichlet_ratio_bounds_against_closed_form():
+    prob = O.Problem(11, 7.0, "DDDDDD")
+    lo, hi = O.dirichlet_ratio_bounds(prob)
+    r = [lambda_3d(i, j, l, prob.h, 7.0) for i in range(1, 12) for j in range(1, 12) for l in range(1, 12)]
+    ratio = np.array([la / lp for la, lp in r]).real
+    assert abs(lo - ratio.min()) < 1e-12 and abs(hi - ratio.max()) < 1e-12
