@@ -54,7 +54,10 @@ enum { HELM6_FP64 = 0,   /* everything in FP64 complex */
 /* method */
 enum { HELM6_GMRES = 0,  /* right-preconditioned GMRES(m): U += A_p^{-1}(V y) per cycle */
        HELM6_FGMRES = 1, /* flexible GMRES(m): keeps Z_j = A_p^{-1} v_j, U += Z y */
-       HELM6_SKS = 2     /* Algorithm 1 (no inner products except the residual norm) */ };
+       HELM6_SKS = 2,    /* Algorithm 1 (no inner products except the residual norm) */
+       HELM6_CHEB = 3    /* Chebyshev acceleration (the theorem of Section 2) on the real
+                            interval [cheb_lo, cheb_hi] holding the spectrum of A A_p^{-1}:
+                            no inner products except the residual norm */ };
 
 /* return codes */
 enum {
@@ -86,6 +89,10 @@ typedef struct {
                         per-phase profiling while on */
   int dot_blocks;    /* thread blocks of the Gram-Schmidt reduction pass (0 = 2 per SM) */
   int update_blocks; /* thread blocks of the Gram-Schmidt update pass (0 = up to 8 per SM) */
+  double cheb_lo, cheb_hi;  /* HELM6_CHEB: 0 < cheb_lo < cheb_hi bounding the (real) eigenvalues
+                               of A A_p^{-1}; both 0 = the exact bounds, computed on the sine
+                               modes, for a real k on the all-Dirichlet cube (Eq. 3DEGV), else
+                               UNSUPPORTED */
   int own_stream;    /* nonzero: ignore `stream`; the context creates (and destroys) its own
                         stream, ordered with the legacy default stream like any blocking
                         stream, so that contexts driven from several threads run

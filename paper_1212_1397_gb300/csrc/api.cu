@@ -51,6 +51,8 @@ struct helm6_ctx {
   float *zrinv32 = nullptr, *zcp32 = nullptr;  // z-line pivot tables (tensor-core path)
   // FP64 vectors (2N doubles each)
   double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
+  double* D64 = nullptr;           // Chebyshev direction
+  double cheb_lo = 0, cheb_hi = 0;  // spectral interval of A A_p^{-1} (HELM6_CHEB)
   double *V64 = nullptr, *Z64 = nullptr, *w64 = nullptr, *zt64 = nullptr, *tA64 = nullptr,
          *tB64 = nullptr, *cw64 = nullptr;
   // FP32 vectors (MIXED)
@@ -675,6 +677,88 @@ int solve_sks(helm6_ctx* c, double normF, double tol, int maxit, helm6_stats* st
   }
 }
 
+// Extremes of the eigenvalues of A A_p^{-1} on the all-Dirichlet cube (real k): both
+// operators are diagonal on the sine modes; with c_a = cos(p_a pi h) the 27-point operator's
+// eigenvalue is w0 + 2 w1 (cx + cy + cz) + 4 w2 (cx cy + cx cz + cy cz) + 8 w3 cx cy cz
+// (w0..w3 its centre, face, edge and corner weights) and the 7-point operator's
+// -6 + 2 (cx + cy + cz) + k^2 h^2.  The ratio is symmetric in the three axes, so only
+// i <= j <= l are visited.
+void dirichlet_ratio_bounds(const helm6_ctx* c, double* lo, double* hi) {
+  const int n = c->n;
+  const double w0 = c->coef.interior.w[1][0].re, w1 = c->coef.interior.w[1][1].re,
+               w2 = c->coef.interior.w[1][2].re, w3 = c->coef.interior.w[0][2].re;
+  const double kh2 = (c->k * c->k * c->h * c->h).real();
+  std::vector<double> cs(n);
+  for (int p = 0; p < n; ++p) cs[p] = std::cos((p + 1) * M_PI * c->h);
+  double mn = INFINITY, mx = -INFINITY;
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j)
+      for (int l = j; l < n; ++l) {
+        const double x = cs[i], y = cs[j], z = cs[l];
+        const double s1 = x + y + z, s2 = x * y + x * z + y * z, s3 = x * y * z;
+        const double la = w0 + 2 * w1 * s1 + 4 * w2 * s2 + 8 * w3 * s3;
+        const double lp = -6.0 + 2 * s1 + kh2;
+        const double r = la / lp;
+        mn = std::min(mn, r);
+        mx = std::max(mx, r);
+      }
+  *lo = mn;
+  *hi = mx;
+}
+
+// Chebyshev acceleration on A A_p^{-1} for the interval [lo, hi] (the theorem of Section 2):
+// d_0 = A_p^{-1} r_0 / theta, U += d_n, r = F - A U (FP64), rho_{n+1} = 1/(2 theta/delta - rho_n),
+// d_{n+1} = rho_{n+1} rho_n d_n + (2 rho_{n+1}/delta) A_p^{-1} r; MIXED applies A_p^{-1} in FP32
+// to r/||r||.  Divergence as for SKS.
+int solve_cheb(helm6_ctx* c, double normF, double tol, int maxit, helm6_stats* st) {
+  const double theta = 0.5 * (c->cheb_hi + c->cheb_lo), delta = 0.5 * (c->cheb_hi - c->cheb_lo);
+  const int64_t N = c->g.N;
+  cudaStream_t s = c->stream;
+  double beta;
+  int rc = residual64(c, &beta);
+  if (rc) return rc;
+  const double beta0 = beta;
+  // E = A_p^{-1} r (FP64 result in both precisions)
+  auto prec_r = [&]() {
+    if (c->opts.precision == HELM6_FP64) {
+      precond64(c, c->R64, c->E64);
+    } else {
+      launch_convert<double, float>(c->R64, c->w32, N, 1.0 / beta, s);
+      precond32(c, c->w32, c->zt32);
+      launch_convert<float, double>(c->zt32, c->E64, N, beta, s);
+    }
+  };
+  if (!std::isfinite(beta)) return HELM6_NONFINITE;
+  if (beta <= tol * normF) return HELM6_OK;
+  double rho = delta / theta;
+  prec_r();
+  CK(cudaMemsetAsync(c->D64, 0, sizeof(double) * 2 * N, s));
+  launch_axpby(c->E64, c->D64, N, 0.0, 1.0 / theta, s);
+  int iters = 0;
+  while (true) {
+    if (iters >= maxit) return HELM6_NOT_CONVERGED;
+    launch_axpy<double, double>(c->D64, c->U64, N, 1.0, s);
+    ++iters;
+    rc = residual64(c, &beta);
+    if (rc) return rc;
+    if (st) {
+      st->iters++;
+      push_hist(st, beta / normF);
+    }
+    {
+      const int cs = check_status(c);
+      if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
+    }
+    if (!std::isfinite(beta)) return HELM6_NONFINITE;
+    if (beta <= tol * normF) return HELM6_OK;
+    if (beta > kDiverge * std::max(beta0, normF)) return HELM6_DIVERGED;
+    const double rho_new = 1.0 / (2.0 * theta / delta - rho);
+    prec_r();
+    launch_axpby(c->E64, c->D64, N, rho_new * rho, 2.0 * rho_new / delta, s);
+    rho = rho_new;
+  }
+}
+
 bool valid_face(int f) { return f == HELM6_DIRICHLET || f == HELM6_NEUMANN || f == HELM6_SOMMERFELD; }
 
 }  // namespace
@@ -735,7 +819,16 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   helm6_opts_default(&o);
   if (opts) o = *opts;
   if (o.precision != HELM6_FP64 && o.precision != HELM6_MIXED) return HELM6_ERR_INVALID;
-  if (o.method < HELM6_GMRES || o.method > HELM6_SKS) return HELM6_ERR_INVALID;
+  if (o.method < HELM6_GMRES || o.method > HELM6_CHEB) return HELM6_ERR_INVALID;
+  if (o.method == HELM6_CHEB) {
+    const bool given = o.cheb_lo != 0.0 || o.cheb_hi != 0.0;
+    if (given && !(o.cheb_lo > 0.0 && o.cheb_hi > o.cheb_lo && std::isfinite(o.cheb_hi))) return HELM6_ERR_INVALID;
+    if (!given) {
+      for (int i = 0; i < 6; ++i)
+        if (faces[i] != HELM6_DIRICHLET) return HELM6_ERR_UNSUPPORTED;
+      if (k.im != 0.0) return HELM6_ERR_UNSUPPORTED;
+    }
+  }
   if (o.xform_terms == 0) o.xform_terms = 3;
   if (o.xform_terms < 1 || o.xform_terms > 3) return HELM6_ERR_INVALID;
   if (o.max_restart == 0) o.max_restart = 30;
@@ -806,7 +899,7 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     return fail(rc);
   if (o.precision == HELM6_FP64) {
     const bool needZ = o.method == HELM6_FGMRES;
-    const bool krylov = o.method != HELM6_SKS;
+    const bool krylov = o.method == HELM6_GMRES || o.method == HELM6_FGMRES;
     if (krylov && (rc = dalloc(c, &c->V64, v * (m + 1)))) return fail(rc);
     if (needZ && (rc = dalloc(c, &c->Z64, v * m))) return fail(rc);
     if (krylov && (rc = dalloc(c, &c->u64, v))) return fail(rc);
@@ -814,7 +907,7 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
         (rc = dalloc(c, &c->tB64, v)) || (rc = dalloc(c, &c->cw64, v)))
       return fail(rc);
   } else {
-    const bool krylov = o.method != HELM6_SKS;
+    const bool krylov = o.method == HELM6_GMRES || o.method == HELM6_FGMRES;
     if (krylov && ((rc = dalloc(c, &c->V32, v * (m + 1))) || (rc = dalloc(c, &c->Z32, v * m)) ||
                    (rc = dalloc(c, &c->u32, v))))
       return fail(rc);
@@ -823,6 +916,16 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
       return fail(rc);
     // FP64 scratch used by apply_Pinv in FP64 layout conversions
     if ((rc = dalloc(c, &c->tA64, v))) return fail(rc);
+  }
+  if (o.method == HELM6_CHEB) {
+    if ((rc = dalloc(c, &c->D64, v))) return fail(rc);
+    if (o.cheb_lo != 0.0 || o.cheb_hi != 0.0) {
+      c->cheb_lo = o.cheb_lo;
+      c->cheb_hi = o.cheb_hi;
+    } else {
+      dirichlet_ratio_bounds(c, &c->cheb_lo, &c->cheb_hi);
+      if (!(c->cheb_lo > 0.0 && c->cheb_hi > c->cheb_lo)) return fail(HELM6_ERR_UNSUPPORTED);  // indefinite
+    }
   }
   c->nred = std::max(1, device_sm_count() * 4);
   c->nsten = stencil_blocks(c->g);
@@ -972,7 +1075,8 @@ int helm6_apply_stage2(helm6_ctx* c, const void* x, void* y) {
 
 int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, int maxit, helm6_stats* st) {
   if (!c || !F || !u || !(tol > 0) || maxit < 0) return HELM6_ERR_INVALID;
-  if (c->opts.method != HELM6_SKS && (restart < 1 || restart > c->mrest)) return HELM6_ERR_INVALID;
+  const bool krylov = c->opts.method == HELM6_GMRES || c->opts.method == HELM6_FGMRES;
+  if (krylov && (restart < 1 || restart > c->mrest)) return HELM6_ERR_INVALID;
   const auto t0 = std::chrono::steady_clock::now();
   helm6_stats local;
   helm6_stats* S = st ? st : &local;
@@ -996,6 +1100,8 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
     launch_interleaved_to_planar((const double*)u, c->U64, N, s);
     if (c->opts.method == HELM6_SKS)
       status = solve_sks(c, normF, tol, maxit, S);
+    else if (c->opts.method == HELM6_CHEB)
+      status = solve_cheb(c, normF, tol, maxit, S);
     else if (c->opts.precision == HELM6_FP64)
       status = solve_fp64(c, normF, tol, restart, maxit, S);
     else

@@ -176,6 +176,8 @@ int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, 
 // y += alpha x (planar, 2N reals), mixed input/output precision.
 template <typename TI, typename TO>
 void launch_axpy(const TI* x, TO* y, int64_t N, double alpha, cudaStream_t s);
+// y = a y + b x (planar FP64, 2N reals).
+void launch_axpby(const double* x, double* y, int64_t N, double a, double b, cudaStream_t s);
 // p[0] = re, p[1] = im on the device (stream-ordered).
 void launch_set_complex(double* p, double re, double im, cudaStream_t s);
 

@@ -713,6 +713,16 @@ void launch_backsolve(const double* H, int ldh, int j, const double* g, double* 
   backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y);
 }
 
+__global__ void axpby_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n, double a, double b) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, y[i], b * x[i]);
+}
+
+void launch_axpby(const double* x, double* y, int64_t N, double a, double b, cudaStream_t s) {
+  note_launch();
+  axpby_kernel<<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, a, b);
+}
+
 template <typename TI, typename TO>
 void launch_axpy(const TI* x, TO* y, int64_t N, double alpha, cudaStream_t s) {
   note_launch();

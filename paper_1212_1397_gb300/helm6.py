@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(_PKG, "libhelm6.so")
 
 DIRICHLET, NEUMANN, SOMMERFELD = 0, 1, 2
 FP64, MIXED = 0, 1
-GMRES, FGMRES, SKS = 0, 1, 2
+GMRES, FGMRES, SKS, CHEB = 0, 1, 2, 3
 MAX_HIST = 1024
 CNN_NPARAMS = 15602
 CNN_OFF, CNN_ON, CNN_AUTO = 0, 1, 2
@@ -44,7 +44,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("xform_terms", C.c_int),
                 ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int),
-                ("own_stream", C.c_int)]
+                ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("own_stream", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -180,7 +180,7 @@ class Solver:
 
     def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
                  max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None, use_graphs=False,
-                 dot_blocks=0, update_blocks=0, own_stream=False):
+                 dot_blocks=0, update_blocks=0, own_stream=False, cheb_bounds=(0.0, 0.0)):
         lib = load()
         self._lib = lib
         o = Opts()
@@ -189,6 +189,7 @@ class Solver:
         o.inner_tol, o.xform_terms = inner_tol, xform_terms
         o.use_graphs, o.dot_blocks, o.update_blocks = int(bool(use_graphs)), int(dot_blocks), int(update_blocks)
         o.own_stream = int(bool(own_stream))
+        o.cheb_lo, o.cheb_hi = float(cheb_bounds[0]), float(cheb_bounds[1])
         if stream is not None:
             o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.stream = stream

@@ -197,3 +197,17 @@ def test_table8_sommerfeld_h512(H, capsys, k, g_p, sks_p):
     assert res["gmres64"]["status"] == "OK" and abs(res["gmres64"]["iters"] - g_p) <= 2
     assert res["sks64"]["status"] == "OK" and abs(res["sks64"]["iters"] - sks_p) <= 2
     assert res["mixed"]["status"] == "OK"
+
+
+@pytest.mark.parametrize("hinv,k,ca_p", [(128, 10.0, 14), (128, 20.0, 15), (128, 30.0, 17),
+                                         (256, 10.0, 12), (256, 20.0, 14), (256, 30.0, 13)])
+def test_table3_table4_chebyshev(H, capsys, hinv, k, ca_p):
+    """The CA column of Tables 3 and 4: Chebyshev acceleration with the exact bounds of
+    Eq. 3DEGV (computed by the library on the sine modes), FP64, stop at 1e-10."""
+    prob, u, F = dirichlet(hinv - 1, k)
+    with H.Solver(prob.n, k, prob.faces, precision=H.FP64, method=H.CHEB) as s:
+        U, st = s.solve(torch.from_numpy(F).cuda(), tol=1e-10, maxit=200)
+        U = U.cpu().numpy()
+    report(capsys, table="3/4 CA", hinv=hinv, k=k, ca=st["iters"], printed=ca_p, ms=st["t_total_ms"],
+           err6=err6(prob, u, U))
+    assert st["rc"] == 0 and abs(st["iters"] - ca_p) <= 1, st["iters"]

@@ -192,3 +192,35 @@ def test_initial_guess_is_used(H):
         u0 = torch.from_numpy(Uref).cuda().clone()
         u, st = s.solve(torch.from_numpy(F).cuda(), u=u0, tol=1e-10, restart=10)
     assert st["iters"] == 0 and st["relres"] < 1e-10
+
+
+def test_chebyshev_matches_oracle(H):
+    """Chebyshev acceleration with the library's exact bounds (all-Dirichlet cube, real k):
+    the oracle's iteration count (within one) and solution; the mixed variant converges to
+    the same solution."""
+    n, k, faces = 23, 8.0, "DDDDDD"
+    prob, F = _gauss_problem(n, k, faces)
+    Uref, info = O.solve(prob, F, tol=1e-10, maxit=200, method="cheb")
+    lo, hi = O.dirichlet_ratio_bounds(prob)
+    for prec in (H.FP64, H.MIXED):
+        with H.Solver(n, k, faces, precision=prec, method=H.CHEB) as s:
+            u, st = s.solve(torch.from_numpy(F).cuda(), tol=1e-10, maxit=200)
+        assert st["rc"] == 0 and st["relres"] <= 1e-10
+        assert rel2(u.cpu().numpy(), Uref) < 1e-7
+        if prec == H.FP64:
+            assert abs(st["iters"] - info["iters"]) <= 1, (st["iters"], info["iters"])
+    # the same bounds given explicitly: the same iterations
+    with H.Solver(n, k, faces, precision=H.FP64, method=H.CHEB, cheb_bounds=(lo, hi)) as s:
+        _, st2 = s.solve(torch.from_numpy(F).cuda(), tol=1e-10, maxit=200)
+    assert abs(st2["iters"] - info["iters"]) <= 1
+
+
+def test_chebyshev_arguments(H):
+    with pytest.raises(H.Helm6Error):  # no exact bounds for Neumann faces
+        H.Solver(10, 5.0, "DDNNDD", method=H.CHEB)
+    with pytest.raises(H.Helm6Error):  # complex k
+        H.Solver(10, 5.0 + 1j, "DDDDDD", method=H.CHEB)
+    with pytest.raises(H.Helm6Error):  # bad interval
+        H.Solver(10, 5.0, "DDNNDD", method=H.CHEB, cheb_bounds=(1.5, 0.5))
+    with H.Solver(10, 5.0, "DDNNDD", method=H.CHEB, cheb_bounds=(0.5, 1.5)) as s:
+        assert s.dims == (10, 12, 10)
