@@ -150,18 +150,21 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
   const int bterm = TC_KC * npad * 16;            // basis bytes of one term of one stage
   const int bstage = 2 * bterm;
   const int stage_bytes = 2 * A_TILE + 2 * TC_KC * TC_GMAX * 16;  // fixed stride (largest group)
-  uint64_t* bars = (uint64_t*)(smem + 2 * stage_bytes);  // full[0..1], done[0..1]
-  uint32_t* tslot = (uint32_t*)(bars + 4);
+  uint64_t* bars = (uint64_t*)(smem + 2 * stage_bytes);  // full[0..1], done[0..1], afull[0..1]
+  uint32_t* tslot = (uint32_t*)(bars + 6);
   int* fail = (int*)(tslot + 1);
   const uint32_t ncols = npad > 128 ? 256u : (npad > 64 ? 128u : (npad > 32 ? 64u : 32u));
   const uint32_t bar0 = s_addr(bars);
-  auto full = [&](int s) { return bar0 + 8u * s; };
-  auto done = [&](int s) { return bar0 + 16u + 8u * s; };
+  auto full = [&](int s) { return bar0 + 8u * s; };          // basis stage arrived (bulk copy)
+  auto done = [&](int s) { return bar0 + 16u + 8u * s; };    // MMAs of the stage completed
+  auto afull = [&](int s) { return bar0 + 32u + 8u * s; };   // every thread stored its data part
   // this group's basis: the groups before it hold nk stages of 2 terms of gpad rows each
   const uint8_t* W = p.W + (size_t)grp * p.nk * 2 * TC_KC * gpad * 16;
 
   if (tid == 0) {
     for (int s = 0; s < 4; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s), "r"(1));
+    for (int s = 4; s < 6; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s), "r"(TC_THREADS));
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
     *fail = 0;
@@ -196,44 +199,47 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
   load_stage(p, m0, 0, warp, lane, xr);
   const uint32_t id = idesc(npad);
 
+  // No block-wide barrier in the loop: each thread waits only for the MMAs that last read
+  // the stage buffer it is about to overwrite, stores its part of the data stage and
+  // arrives on afull; thread 0 alone waits for afull and the basis before issuing.
   for (int kt = 0; kt < p.nk; ++kt) {
     const int st = kt & 1;
     uint8_t* sA = smem + st * stage_bytes;
     uint8_t* sB = sA + 2 * A_TILE;
-    if (kt >= 2 && !*fail) {
-      if (!poll(done(st), ((kt - 2) >> 1) & 1)) *fail = 1;
+    if (kt >= 2 && !poll(done(st), ((kt - 2) >> 1) & 1)) {
+      *fail = 1;
+      break;
     }
-    __syncthreads();
-    if (*fail) break;
     store_stage(sA, warp, lane, xr);
-    if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, warp, lane, xr);  // in flight during the MMAs
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(afull(st)) : "memory");
+    if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, warp, lane, xr);  // in flight during the MMAs
     if (tid == 0) {
-      if (!poll(full(st), (kt >> 1) & 1)) {
+      if (!poll(afull(st), (kt >> 1) & 1) || !poll(full(st), (kt >> 1) & 1)) {
         *fail = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t aHi = s_addr(sA), aLo = aHi + A_TILE, bHi = s_addr(sB), bLo = bHi + bterm;
-        const uint32_t b_lbo = (uint32_t)npad * 16;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t aHi = s_addr(sA), aLo = aHi + A_TILE, bHi = s_addr(sB), bLo = bHi + bterm;
+      const uint32_t b_lbo = (uint32_t)npad * 16;
 #pragma unroll
-        for (int kk = 0; kk < TC_KT / 16; ++kk) {
-          const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-          const uint64_t ah = sdesc(aHi + kk * 2 * A_LBO, A_LBO, 128);
-          const uint64_t bh = sdesc(bHi + kk * 2 * b_lbo, b_lbo, 128);
-          mma(tmem, ah, bh, id, acc);
-          if (p.terms >= 2) mma(tmem, sdesc(aLo + kk * 2 * A_LBO, A_LBO, 128), bh, id, 1u);
-          if (p.terms >= 3) mma(tmem, ah, sdesc(bLo + kk * 2 * b_lbo, b_lbo, 128), id, 1u);
+      for (int kk = 0; kk < TC_KT / 16; ++kk) {
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t ah = sdesc(aHi + kk * 2 * A_LBO, A_LBO, 128);
+        const uint64_t bh = sdesc(bHi + kk * 2 * b_lbo, b_lbo, 128);
+        mma(tmem, ah, bh, id, acc);
+        if (p.terms >= 2) mma(tmem, sdesc(aLo + kk * 2 * A_LBO, A_LBO, 128), bh, id, 1u);
+        if (p.terms >= 3) mma(tmem, ah, sdesc(bLo + kk * 2 * b_lbo, b_lbo, 128), id, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
+                   : "memory");
+      // stage (kt + 1) & 1 was last read by the MMAs of step kt - 1
+      if (kt >= 1 && kt + 1 < p.nk) {
+        if (!poll(done(st ^ 1), ((kt - 1) >> 1) & 1)) {
+          *fail = 1;
+          break;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
-                     : "memory");
-        // stage (kt + 1) & 1 was last read by the MMAs of step kt - 1
-        if (kt >= 1 && kt + 1 < p.nk) {
-          if (!poll(done(st ^ 1), ((kt - 1) >> 1) & 1))
-            *fail = 1;
-          else
-            issue_b(kt + 1);
-        }
+        issue_b(kt + 1);
       }
     }
   }
