@@ -419,43 +419,6 @@ __global__ void givens_kernel(double* H, int ldh, int j, double* cs, double* sn,
   *res = zabs(ld(g + 2 * (j + 1)));
 }
 
-// Apply rotations 0..jj-1 to column jj of R (rows 0..jj+1), make rotation jj, update g;
-// *res = |g_{jj+1}|.  Rotation i acts on rows (i, i+1): [c s; -conj(s) c], c real.
-__device__ void givens_column(double* col, int jj, double* cs, double* sn, double* g, double* res) {
-  for (int i = 0; i < jj; ++i) {
-    const zc hi = ld(col + 2 * i), hn = ld(col + 2 * (i + 1));
-    const double c = cs[2 * i];
-    const zc s = ld(sn + 2 * i);
-    const zc t = zadd(zc{c * hi.re, c * hi.im}, zmul(s, hn));
-    const zc u = zadd(zmul(zc{-s.re, s.im}, hi), zc{c * hn.re, c * hn.im});
-    st(col + 2 * i, t);
-    st(col + 2 * (i + 1), u);
-  }
-  const zc a = ld(col + 2 * jj), b = ld(col + 2 * (jj + 1));
-  const double aa = zabs(a), bb = zabs(b);
-  const double den = hypot(aa, bb);
-  double c;
-  zc s;
-  if (den == 0.0) {
-    c = 1.0;
-    s = zc{0.0, 0.0};
-  } else if (aa == 0.0) {
-    c = 0.0;
-    s = zc{1.0, 0.0};
-  } else {
-    c = aa / den;
-    s = zmul(zc{a.re / aa, a.im / aa}, zc{b.re / den, -b.im / den});
-  }
-  cs[2 * jj] = c;
-  cs[2 * jj + 1] = 0.0;
-  st(sn + 2 * jj, s);
-  st(col + 2 * jj, zadd(zc{c * a.re, c * a.im}, zmul(s, b)));
-  st(col + 2 * (jj + 1), zc{0.0, 0.0});
-  const zc gj = ld(g + 2 * jj);
-  st(g + 2 * (jj + 1), zmul(zc{-s.re, s.im}, gj));
-  st(g + 2 * jj, zc{c * gj.re, c * gj.im});
-  *res = zabs(ld(g + 2 * (jj + 1)));
-}
 
 // Small FP64 algebra of one delayed Gram-Schmidt Arnoldi step j (one thread).
 // red: reduced sums s_i = V_i^H u_j, t_i = V_i^H w (i < j), a = ||u_j||^2, b = u_j^H w.
@@ -468,51 +431,128 @@ __device__ void givens_column(double* col, int jj, double* cs, double* sn, doubl
 //   * coef = [s, t, c_j, 1/alpha] for the update pass v_j = (u - V s)/alpha,
 //     u_{j+1} = (w - V t - v_j c_j)/alpha.
 // *brk = 1 when alpha^2 <= 1e-28 a (u_j in the span of the basis: breakdown).
-__global__ void dcgs_step_kernel(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T,
-                                 int ldt, double* cs, double* sn, double* g, double* coef, double* est, int* brk) {
-  // one warp: lane r handles rows r, r + 32, ...; the Givens sweep runs on lane 0
-  const int lane = threadIdx.x & 31;
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+constexpr int STEP_T = 128;   // threads of the step kernel
+constexpr int STEP_MAXJ = 64;  // largest restart length (helm6_opts.max_restart <= 64)
+
+// Sums of three doubles over the block; every thread receives them.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double* sh) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sh[3 * w] = a;
+    sh[3 * w + 1] = b;
+    sh[3 * w + 2] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int i = 0; i < STEP_T / 32; ++i) {
+    a += sh[3 * i];
+    b += sh[3 * i + 1];
+    c += sh[3 * i + 2];
+  }
+  __syncthreads();
+}
+
+// One block of STEP_T threads; the rotation sweep runs on thread 0 over shared-memory copies
+// of the column and of the previous rotations, the O(j^2) products warp per row.
+__global__ void __launch_bounds__(STEP_T) dcgs_step_kernel(int j, int has_w, const double* red, double* Hr, double* R,
+                                                           int ldh, double* T, int ldt, double* cs, double* sn,
+                                                           double* g, double* coef, double* est, int* brk) {
+  __shared__ double shr[3 * STEP_T / 32];
+  __shared__ double scol[2 * (STEP_MAXJ + 2)], scs[STEP_MAXJ + 1], ssn[2 * (STEP_MAXJ + 1)];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double* sv = red;
   const double* tv = red + 2 * j;
   const double a = red[4 * j];
   const zc b = zc{red[4 * j + 1], red[4 * j + 2]};
-  double s2 = 0.0;
-  for (int i = lane; i < j; i += 32) s2 += sv[2 * i] * sv[2 * i] + sv[2 * i + 1] * sv[2 * i + 1];
-  s2 = warp_sum(s2);
+  double s2 = 0.0, pr = 0.0, pi = 0.0;
+  for (int i = tid; i < j; i += STEP_T) {
+    s2 += sv[2 * i] * sv[2 * i] + sv[2 * i + 1] * sv[2 * i + 1];
+    if (has_w) {
+      const zc q = zmul(zc{sv[2 * i], -sv[2 * i + 1]}, ld(tv + 2 * i));
+      pr += q.re;
+      pi += q.im;
+    }
+  }
+  block_sum3(s2, pr, pi, shr);
   const double al2 = a - s2;
   const bool bd = !(al2 > 1e-28 * fmax(a, 1e-300)) || !isfinite(al2);
   const double al = bd ? 0.0 : sqrt(al2);
   const double inv = bd ? 0.0 : 1.0 / al;
-  if (lane == 0) *brk = bd ? 1 : 0;
-  if (j >= 1) {
-    double* hc = Hr + 2 * (int64_t)(j - 1) * ldh;
-    double* rc = R + 2 * (int64_t)(j - 1) * ldh;
-    for (int i = lane; i < j; i += 32) {
-      hc[2 * i] += sv[2 * i];
-      hc[2 * i + 1] += sv[2 * i + 1];
-    }
-    if (lane == 0) {
-      hc[2 * j] = al;
-      hc[2 * j + 1] = 0.0;
-    }
-    __syncwarp();
-    for (int r = lane; r <= 2 * j + 1; r += 32) rc[r] = hc[r];
-    __syncwarp();
-    if (lane == 0) givens_column(rc, j - 1, cs, sn, g, est);
-  } else if (lane == 0) {
-    g[0] = al;
-    g[1] = 0.0;
-    *est = al;
-  }
-  for (int i = lane; i < j; i += 32) {
+  if (tid == 0) *brk = bd ? 1 : 0;
+  for (int i = tid; i < j; i += STEP_T) {
     coef[2 * i] = sv[2 * i];
     coef[2 * i + 1] = sv[2 * i + 1];
     coef[2 * j + 2 * i] = tv[2 * i];
     coef[2 * j + 2 * i + 1] = tv[2 * i + 1];
   }
+  if (j >= 1) {
+    // lagged correction of column j - 1 and its subdiagonal
+    double* hc = Hr + 2 * (int64_t)(j - 1) * ldh;
+    for (int i = tid; i < j; i += STEP_T) {
+      hc[2 * i] += sv[2 * i];
+      hc[2 * i + 1] += sv[2 * i + 1];
+    }
+    if (tid == 0) {
+      hc[2 * j] = al;
+      hc[2 * j + 1] = 0.0;
+    }
+    __syncthreads();
+    for (int r = tid; r <= 2 * j + 1; r += STEP_T) scol[r] = hc[r];
+    for (int i = tid; i < j - 1; i += STEP_T) {
+      scs[i] = cs[2 * i];
+      ssn[2 * i] = sn[2 * i];
+      ssn[2 * i + 1] = sn[2 * i + 1];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // previous rotations on the column, then the rotation that zeroes its subdiagonal
+      const int jj = j - 1;
+      for (int i = 0; i < jj; ++i) {
+        const zc hi = ld(scol + 2 * i), hn = ld(scol + 2 * (i + 1));
+        const double c = scs[i];
+        const zc s = ld(ssn + 2 * i);
+        st(scol + 2 * i, zadd(zc{c * hi.re, c * hi.im}, zmul(s, hn)));
+        st(scol + 2 * (i + 1), zadd(zmul(zc{-s.re, s.im}, hi), zc{c * hn.re, c * hn.im}));
+      }
+      const zc x = ld(scol + 2 * jj), y = ld(scol + 2 * (jj + 1));
+      const double ax = zabs(x), ay = zabs(y);
+      const double den = hypot(ax, ay);
+      double c;
+      zc s;
+      if (den == 0.0) {
+        c = 1.0;
+        s = zc{0.0, 0.0};
+      } else if (ax == 0.0) {
+        c = 0.0;
+        s = zc{1.0, 0.0};
+      } else {
+        c = ax / den;
+        s = zmul(zc{x.re / ax, x.im / ax}, zc{y.re / den, -y.im / den});
+      }
+      cs[2 * jj] = c;
+      cs[2 * jj + 1] = 0.0;
+      st(sn + 2 * jj, s);
+      st(scol + 2 * jj, zadd(zc{c * x.re, c * x.im}, zmul(s, y)));
+      st(scol + 2 * (jj + 1), zc{0.0, 0.0});
+      const zc gj = ld(g + 2 * jj);
+      const zc gn = zmul(zc{-s.re, s.im}, gj);
+      st(g + 2 * (jj + 1), gn);
+      st(g + 2 * jj, zc{c * gj.re, c * gj.im});
+      *est = zabs(gn);
+    }
+    __syncthreads();
+    double* rc = R + 2 * (int64_t)(j - 1) * ldh;
+    for (int r = tid; r <= 2 * j + 1; r += STEP_T) rc[r] = scol[r];
+  } else if (tid == 0) {
+    g[0] = al;
+    g[1] = 0.0;
+    *est = al;
+  }
   if (!has_w || bd) {
-    if (lane == 0) {
+    if (tid == 0) {
       coef[4 * j] = 0.0;
       coef[4 * j + 1] = 0.0;
       coef[4 * j + 2] = inv;
@@ -520,41 +560,46 @@ __global__ void dcgs_step_kernel(int j, int has_w, const double* red, double* Hr
     return;
   }
   // c_j = (b - s^H t) / alpha
-  double pr = 0.0, pi = 0.0;
-  for (int i = lane; i < j; i += 32) {
-    const zc p = zmul(zc{sv[2 * i], -sv[2 * i + 1]}, ld(tv + 2 * i));
-    pr += p.re;
-    pi += p.im;
-  }
-  pr = warp_sum(pr);
-  pi = warp_sum(pi);
   const zc cj = zc{(b.re - pr) * inv, (b.im - pi) * inv};
-  // column j: ([t; c_j] - Hr[:, 0..j-1] s) / alpha, rows 0..j
+  // column j of Hr: ([t; c_j] - Hr[:, 0..j-1] s) / alpha, rows 0..j (Hessenberg: i >= r - 1)
   double* hj = Hr + 2 * (int64_t)j * ldh;
-  for (int r = lane; r <= j; r += 32) {
-    zc acc = (r < j) ? ld(tv + 2 * r) : cj;
-    for (int i = (r > 0 ? r - 1 : 0); i < j; ++i) {
-      const zc p = zmul(ld(Hr + 2 * ((int64_t)i * ldh + r)), ld(sv + 2 * i));
-      acc.re -= p.re;
-      acc.im -= p.im;
+  for (int r = warp; r <= j; r += STEP_T / 32) {
+    double qr = 0.0, qi = 0.0;
+    for (int i = (r > 0 ? r - 1 : 0) + lane; i < j; i += 32) {
+      const zc q = zmul(ld(Hr + 2 * ((int64_t)i * ldh + r)), ld(sv + 2 * i));
+      qr += q.re;
+      qi += q.im;
     }
-    hj[2 * r] = acc.re * inv;
-    hj[2 * r + 1] = acc.im * inv;
-  }
-  // T column j: (e_j - T s) / alpha
-  if (T) {
-    for (int r = lane; r < j; r += 32) {
-      zc acc = zc{0.0, 0.0};
-      for (int i = r; i < j; ++i) acc = zadd(acc, zmul(ld(T + 2 * ((int64_t)i * ldt + r)), ld(sv + 2 * i)));
-      T[2 * ((int64_t)j * ldt + r)] = -acc.re * inv;
-      T[2 * ((int64_t)j * ldt + r) + 1] = -acc.im * inv;
-    }
+    qr = warp_sum(qr);
+    qi = warp_sum(qi);
     if (lane == 0) {
+      const zc base = (r < j) ? ld(tv + 2 * r) : cj;
+      hj[2 * r] = (base.re - qr) * inv;
+      hj[2 * r + 1] = (base.im - qi) * inv;
+    }
+  }
+  // T column j: (e_j - T s) / alpha (T upper triangular)
+  if (T) {
+    for (int r = warp; r < j; r += STEP_T / 32) {
+      double qr = 0.0, qi = 0.0;
+      for (int i = r + lane; i < j; i += 32) {
+        const zc q = zmul(ld(T + 2 * ((int64_t)i * ldt + r)), ld(sv + 2 * i));
+        qr += q.re;
+        qi += q.im;
+      }
+      qr = warp_sum(qr);
+      qi = warp_sum(qi);
+      if (lane == 0) {
+        T[2 * ((int64_t)j * ldt + r)] = -qr * inv;
+        T[2 * ((int64_t)j * ldt + r) + 1] = -qi * inv;
+      }
+    }
+    if (tid == 0) {
       T[2 * ((int64_t)j * ldt + j)] = inv;
       T[2 * ((int64_t)j * ldt + j) + 1] = 0.0;
     }
   }
-  if (lane == 0) {
+  if (tid == 0) {
     coef[4 * j] = cj.re;
     coef[4 * j + 1] = cj.im;
     coef[4 * j + 2] = inv;
@@ -695,7 +740,7 @@ void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g,
 void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T, int ldt,
                       double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s) {
   note_launch();
-  dcgs_step_kernel<<<1, 32, 0, s>>>(j, has_w, red, Hr, R, ldh, T, ldt, cs, sn, g, coef, est, brk);
+  dcgs_step_kernel<<<1, STEP_T, 0, s>>>(j, has_w, red, Hr, R, ldh, T, ldt, cs, sn, g, coef, est, brk);
 }
 
 void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s) {
