@@ -10,6 +10,9 @@ unit-modulus random phases, solved from u = 0 to ||F - A u|| / ||F|| <= 1e-8 (FP
 residual) by FP64 refinement around FP32 FGMRES(30) with BF16-split tensor-core / FP32
 transforms.  `value` is the device time per solve with F resident in HBM; `e2e` adds the
 host->device copy of F and the device->host copy of u (pinned buffers) to every step.
+The per-phase times, the roofline of the dominant kernel and the launch count come from a
+repeat of the timed solves with the library's phase events on (the events stay out of the
+timed region: recording them serialises the transform's side stream).
 The plain FP64 GMRES(30) solve of the same problem is timed beside it, and the CPU oracle
 on a bounded sample gives `cpu_baseline`.
 
@@ -260,7 +263,6 @@ def main():
     clocks = ClockSampler(local)
     sync_all(dist)
     clocks.start()
-    solver.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
     ev0.record(stream)
@@ -271,9 +273,17 @@ def main():
     ev1.record(stream)
     sync_all(dist)
     clk = clocks.stop()
+    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist)
+
+    # ---- the same solves again with the library's per-phase events on (their records
+    # serialise the side-stream work, so they stay out of the timed region above) ----
+    solver.profile(True)
+    for _ in range(args.steps):
+        u.zero_()
+        _, st = solver.solve(F, u, tol=tol, restart=restart, maxit=1000)
+    torch.cuda.synchronize()
     prof = solver.profile_read()
     solver.profile(False)
-    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, dist)
 
     # ---- e2e: host buffers through the same public API ----
     F_host = F.cpu().pin_memory()
