@@ -51,8 +51,8 @@ KERNEL_OF = {
     "ztri": "ztri_apply_kernel<float>",
     "xform_y_inv": "xform_tc_kernel (y inverse)",
     "xform_x_inv": "xform_tc_kernel (x inverse)",
-    "gs_dot": "dcgs_dot_kernel<float,2>",
-    "gs_update": "dcgs_update_kernel<float,1>",
+    "gs_dot": "dcgs_dot_kernel<float,{p},{tv}>",
+    "gs_update": "dcgs_update_kernel<float,{p},{tv}>",
     "resid64": "stencil_kernel<double,1>",
 }
 
@@ -60,7 +60,7 @@ KERNEL_OF = {
 # from the 128^3 capture summarised in profiles/dram_mixed_n128_k40.md (absent: not captured
 # since the kernel last changed).  The reduction pass reads its j + 2 fields once, so its
 # traffic grows with the fields it reads and the ratio carries to the 256^3 launches.
-NCU_TRAFFIC_RATIO = {"dcgs_dot_kernel<float,2>": 1.0075}
+NCU_TRAFFIC_RATIO = {}
 
 
 def peaks():
@@ -211,6 +211,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-learned", action="store_true", help="skip the mixed + learned-stage solve")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched workload")
+    ap.add_argument("--basis", default="auto", choices=["auto", "f32", "f16"],
+                    help="storage of the inner solve's Krylov basis (auto: the library default)")
     args = ap.parse_args()
     cfg = dict(inputs.WORKLOADS[args.workload])
 
@@ -242,8 +244,9 @@ def main():
     n, k, faces = cfg["n"], cfg["k"], cfg["faces"]
     restart, tol = cfg["restart"], cfg["tol"]
     stream = torch.cuda.current_stream()
+    basis = {"auto": H.BASIS_AUTO, "f32": H.BASIS_F32, "f16": H.BASIS_F16}[args.basis]
     solver = H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=restart,
-                      stream=stream)
+                      stream=stream, basis=basis)
     N = solver.shape[0] * solver.shape[1] * solver.shape[2]
     src_seed, noise_seed = replica_seeds(rank)
     src = inputs.gaussian_sources(src_seed, n, cfg.get("nsrc", 8))
@@ -290,6 +293,10 @@ def main():
     u_host = torch.empty_like(F_host).pin_memory()
     u_dev = solver.empty()
     F_dev = solver.empty()
+    F_dev.copy_(F_host, non_blocking=True)  # one untimed pass over the fresh buffers
+    u_dev.zero_()
+    solver.solve(F_dev, u_dev, tol=tol, restart=restart, maxit=1000)
+    u_host.copy_(u_dev, non_blocking=True)
     sync_all(dist)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -370,18 +377,21 @@ def main():
     # ---- roofline of the dominant kernel (live per-phase events) ----
     hbm, bf16, peak_src = peaks()
     phases = prof["phases"]
-    single = [p for p in phases if p in KERNEL_OF and phases[p]["count"] > 0]
+    f16 = solver.basis == H.BASIS_F16
+    kernel_of = {ph: name.format(p=4 if f16 and N % 4 == 0 else 2, tv="__half" if f16 else "float")
+                 for ph, name in KERNEL_OF.items()}
+    single = [p for p in phases if p in kernel_of and phases[p]["count"] > 0]
     dom = max(single, key=lambda p: phases[p]["ms"])
     cnt = max(phases[dom]["count"], 1)
     per_launch_ms = phases[dom]["ms"] / cnt
     alg_bytes = phases[dom]["bytes"] / cnt        # algorithmic bytes per launch (mean)
     achieved = phases[dom]["bytes"] / (phases[dom]["ms"] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": KERNEL_OF[dom], "phase": dom, "achieved": achieved, "peak": hbm,
+    roof = {"bound": "hbm", "kernel": kernel_of[dom], "phase": dom, "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": (NCU_TRAFFIC_RATIO[KERNEL_OF[dom]] * alg_bytes if KERNEL_OF[dom] in NCU_TRAFFIC_RATIO
+            "traffic": (NCU_TRAFFIC_RATIO[kernel_of[dom]] * alg_bytes if kernel_of[dom] in NCU_TRAFFIC_RATIO
                         else None),
             "traffic_source": ("ncu dram bytes at 128^3 (profiles/dram_mixed_n128_k40.md), per launch scaled "
-                               "by the algorithmic bytes" if KERNEL_OF[dom] in NCU_TRAFFIC_RATIO else None),
+                               "by the algorithmic bytes" if kernel_of[dom] in NCU_TRAFFIC_RATIO else None),
             "per_launch_ms": per_launch_ms,
             "alg_bytes_per_launch": alg_bytes,
             "phase_frac": {p: (phases[p]["bytes"] / (phases[p]["ms"] * 1e-3) / 1e9) / hbm
@@ -407,6 +417,7 @@ def main():
             "config": {"workload": args.workload, "n": n, "k": str(k), "faces": faces,
                        "unknowns": N, "restart": restart, "tol": tol,
                        "sources": len(src), "l2": "inputs larger than L2 (17M-unknown vectors)",
+                       "basis": {H.BASIS_F16: "f16", H.BASIS_F32: "f32"}.get(solver.basis, "fp64"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "iters": last["iters"], "outer": last["outer"], "relres": last["relres"],
             "status": last["status"],

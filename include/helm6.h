@@ -59,6 +59,16 @@ enum { HELM6_GMRES = 0,  /* right-preconditioned GMRES(m): U += A_p^{-1}(V y) pe
                             interval [cheb_lo, cheb_hi] holding the spectrum of A A_p^{-1}:
                             no inner products except the residual norm */ };
 
+/* storage of the Krylov basis V_0..V_m of the MIXED inner solve (its arithmetic stays FP32
+   and its reductions FP64) */
+enum { HELM6_BASIS_AUTO = 0, /* the default below */
+       HELM6_BASIS_F32 = 1,  /* FP32 complex, 8 bytes per unknown and vector */
+       HELM6_BASIS_F16 = 2   /* FP16 complex holding 2^e V_i (2^e the power of two near
+                                sqrt(N)/4, so unit vectors stay inside the FP16 range), 4 bytes
+                                per unknown and vector: the Gram-Schmidt passes read half the
+                                bytes; each v_i is rounded once, when written, and later steps
+                                orthogonalise against the rounded vectors */ };
+
 /* return codes */
 enum {
   HELM6_OK = 0,
@@ -97,6 +107,8 @@ typedef struct {
                         stream, ordered with the legacy default stream like any blocking
                         stream, so that contexts driven from several threads run
                         concurrently while staying ordered with default-stream work */
+  int basis;         /* MIXED Krylov methods: HELM6_BASIS_*; AUTO = F16 from 2^23 unknowns
+                        (mx*my*mz), F32 below.  F16 with FP64 is INVALID */
 } helm6_opts;
 
 #define HELM6_MAX_HIST 1024
@@ -128,6 +140,11 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
 
 /* Unknowns per axis: dims = {mx, my, mz}. */
 int helm6_dims(const helm6_ctx* ctx, int64_t dims[3]);
+
+/* Storage of the context's Krylov basis as resolved at creation: HELM6_BASIS_F32 or
+ * HELM6_BASIS_F16 for a MIXED GMRES/FGMRES context, HELM6_BASIS_AUTO (0) where the basis is
+ * FP64 or there is none (SKS, Chebyshev); INVALID if ctx is NULL. */
+int helm6_basis(const helm6_ctx* ctx);
 
 /* y = A x, the h^2-scaled sixth-order compact operator (Eq. scheme; face rows per Eq. 3DN
  * with the ghost eliminated by even reflection, and Eq. 3DDISCS).  x and y are device

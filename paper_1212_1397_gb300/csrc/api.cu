@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "helm6_internal.h"
@@ -58,6 +59,8 @@ struct helm6_ctx {
   // FP32 vectors (MIXED)
   float *V32 = nullptr, *Z32 = nullptr, *w32 = nullptr, *zt32 = nullptr, *tA32 = nullptr,
         *tB32 = nullptr, *cw32 = nullptr;
+  __half* V16 = nullptr;  // FP16 basis (HELM6_BASIS_F16) in place of V32, holding vscale V_i
+  double vscale = 1.0;
   // small device arrays
   double *partial = nullptr, *spart = nullptr, *H = nullptr, *cs = nullptr, *sn = nullptr,
          *gv = nullptr, *yv = nullptr, *h2 = nullptr, *scal = nullptr;
@@ -394,8 +397,8 @@ void push_hist(helm6_stats* st, double v);
 // of u_m completes column m-1), when the estimate of the last completed column is
 // <= abs_tol, at a breakdown, or after maxsteps operator applications.  On return y holds
 // the least-squares coefficients of its *kout columns and *beta = ||u_0||.
-template <typename T>
-int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, int maxsteps, bool flexible,
+template <typename T, typename TV>
+int arnoldi(helm6_ctx* c, TV* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, int maxsteps, bool flexible,
             void (*prec)(helm6_ctx*, const T*, T*), const StencilCoef& coef, int* kout, double* beta,
             helm6_stats* st) {
   cudaStream_t s = c->stream;  // the stream enqueue() works on (the capture stream while capturing)
@@ -439,10 +442,12 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
       launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
       prof_stop(c, HELM6_PH_STENCIL, e);
     }
-    const double vb = 2.0 * sizeof(T) * (double)N;  // one complex field
+    const double vb = 2.0 * sizeof(T) * (double)N;    // one complex field
+    const double vbb = 2.0 * sizeof(TV) * (double)N;  // one basis vector
+    const double vsc = std::is_same<TV, T>::value ? 1.0 : c->vscale;
     cudaEvent_t e = prof_start(c);
-    launch_dcgs_dot<T>(V, vs, j, u, full ? w : nullptr, N, c->partial, c->ndot, s);
-    prof_stop(c, HELM6_PH_DOT, e, vb * (j + (full ? 2 : 1)));
+    launch_dcgs_dot<T, TV>(V, vs, j, u, full ? w : nullptr, N, c->partial, c->ndot, vsc, s);
+    prof_stop(c, HELM6_PH_DOT, e, vbb * j + vb * (full ? 2 : 1));
     e = prof_start(c);
     launch_reduce_cols(c->partial, c->ndot, 4 * j + 3, c->red, 0, s);
     launch_dcgs_step(j, full ? 1 : 0, c->red, c->Hr, c->H, ldh, flexible ? c->Tm : nullptr, c->mrest, c->cs, c->sn,
@@ -458,8 +463,8 @@ int arnoldi(helm6_ctx* c, T* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol, 
                                 cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u));
     if (full) {
       e = prof_start(c);
-      launch_dcgs_update<T>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, s);
-      prof_stop(c, HELM6_PH_UPDATE, e, vb * (j + 4));
+      launch_dcgs_update<T, TV>(V, vs, j, u, w, V + (int64_t)j * vs, N, c->coefv, c->ncgs, vsc, s);
+      prof_stop(c, HELM6_PH_UPDATE, e, vbb * (j + 1) + vb * 3);
     }
     return HELM6_OK;
   };
@@ -561,7 +566,7 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
     int k = 0;
     double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    rc = arnoldi<double>(c, c->V64, c->Z64, c->u64, c->w64, c->zt64, m, tol * normF, maxit - iters, flex, precond64,
+    rc = arnoldi<double, double>(c, c->V64, c->Z64, c->u64, c->w64, c->zt64, m, tol * normF, maxit - iters, flex, precond64,
                          c->coef, &k, &b0, st);
     if (rc) return rc;
     fix_hist(st, h0, 1.0 / normF);
@@ -617,8 +622,11 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     double b0 = 0;
     const int h0 = st ? st->nhist : 0;
     const bool use_cnn = cnn_cycle(c, cyc);
-    rc = arnoldi<float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
-                        use_cnn ? precond_cnn32 : precond32, c->coef, &k, &b0, st);
+    auto* prec = use_cnn ? precond_cnn32 : precond32;
+    rc = c->V16 ? arnoldi<float, __half>(c, c->V16, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
+                                         prec, c->coef, &k, &b0, st)
+                : arnoldi<float, float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
+                                        prec, c->coef, &k, &b0, st);
     if (rc) return rc;
     if (st && use_cnn) st->cnn_cycles++;
     fix_hist(st, h0, beta / normF);
@@ -829,6 +837,8 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
       if (k.im != 0.0) return HELM6_ERR_UNSUPPORTED;
     }
   }
+  if (o.basis < HELM6_BASIS_AUTO || o.basis > HELM6_BASIS_F16) return HELM6_ERR_INVALID;
+  if (o.basis == HELM6_BASIS_F16 && o.precision != HELM6_MIXED) return HELM6_ERR_INVALID;
   if (o.xform_terms == 0) o.xform_terms = 3;
   if (o.xform_terms < 1 || o.xform_terms > 3) return HELM6_ERR_INVALID;
   if (o.max_restart == 0) o.max_restart = 30;
@@ -908,9 +918,18 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
       return fail(rc);
   } else {
     const bool krylov = o.method == HELM6_GMRES || o.method == HELM6_FGMRES;
-    if (krylov && ((rc = dalloc(c, &c->V32, v * (m + 1))) || (rc = dalloc(c, &c->Z32, v * m)) ||
-                   (rc = dalloc(c, &c->u32, v))))
+    // AUTO: FP16 from 2^23 unknowns, where the Gram-Schmidt passes are the bulk of a step;
+    // below, an easy problem's inner cycles converge deep enough that the rounded basis can
+    // cost an extra refinement step, more than the halved basis traffic saves
+    if (o.basis == HELM6_BASIS_AUTO) o.basis = (krylov && N >= (int64_t(1) << 23)) ? HELM6_BASIS_F16 : HELM6_BASIS_F32;
+    c->opts.basis = o.basis;
+    const bool f16 = o.basis == HELM6_BASIS_F16;
+    if (krylov && ((rc = f16 ? dalloc(c, &c->V16, v * (m + 1)) : dalloc(c, &c->V32, v * (m + 1))) ||
+                   (rc = dalloc(c, &c->Z32, v * m)) || (rc = dalloc(c, &c->u32, v))))
       return fail(rc);
+    // 2^e near sqrt(N)/4: a unit vector's entries stay below 2^e <= sqrt(N)/2 (far inside the
+    // FP16 range up to N = 2^32) while its mean square is 2^(2e)/N, about 1/16
+    c->vscale = std::ldexp(1.0, std::max(0, std::min(14, (int)std::floor(0.5 * std::log2((double)N)) - 2)));
     if ((rc = dalloc(c, &c->w32, v)) || (rc = dalloc(c, &c->zt32, v)) || (rc = dalloc(c, &c->tA32, v)) ||
         (rc = dalloc(c, &c->tB32, v)) || (rc = dalloc(c, &c->cw32, v)))
       return fail(rc);
@@ -986,6 +1005,12 @@ int helm6_dims(const helm6_ctx* c, int64_t dims[3]) {
   dims[1] = c->g.my;
   dims[2] = c->g.mz;
   return HELM6_OK;
+}
+
+int helm6_basis(const helm6_ctx* c) {
+  if (!c) return HELM6_ERR_INVALID;
+  if (c->opts.precision != HELM6_MIXED || !(c->V16 || c->V32)) return HELM6_BASIS_AUTO;
+  return c->V16 ? HELM6_BASIS_F16 : HELM6_BASIS_F32;
 }
 
 int helm6_apply_A(helm6_ctx* c, const void* x, void* y) {

@@ -6,6 +6,7 @@
 // Krylov vectors are float.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -190,12 +191,14 @@ void launch_set_complex(double* p, double re, double im, cudaStream_t s);
 template <typename T>
 int cgs_blocks(int64_t N);
 int dot_blocks();
-template <typename T>
-void launch_dcgs_dot(const T* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
-                     int nblocks, cudaStream_t s);
-template <typename T>
-void launch_dcgs_update(const T* V, int64_t vs, int count, T* u, const T* w, T* v_out, int64_t N,
-                        const double* coef, int nblocks, cudaStream_t s);
+// The basis is stored in TV: T, or __half for T = float holding vscale V_i (vscale a power
+// of two chosen so that unit vectors stay well inside the FP16 range).
+template <typename T, typename TV>
+void launch_dcgs_dot(const TV* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
+                     int nblocks, double vscale, cudaStream_t s);
+template <typename T, typename TV>
+void launch_dcgs_update(const TV* V, int64_t vs, int count, T* u, const T* w, TV* v_out, int64_t N,
+                        const double* coef, int nblocks, double vscale, cudaStream_t s);
 void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T, int ldt,
                       double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s);
 void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s);

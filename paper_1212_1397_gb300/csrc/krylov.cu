@@ -2,8 +2,11 @@
 // norms, linear combinations, precision conversions, and the FP64 Givens least-squares
 // update of GMRES, all on the device.  Dot products accumulate per thread in the vector
 // precision and combine block partials in FP64.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "helm6_internal.h"
 
@@ -177,31 +180,126 @@ __global__ void reduce_sum_kernel(const double* __restrict__ partial, int n, dou
 // ---- Arnoldi with delayed classical Gram-Schmidt (one reduction + one update per step) ----
 // Vector traits for 2-point loads of a planar field.
 
-constexpr int CHD = 8;  // basis vectors per chunk of the reduction pass
+constexpr int CHD = 8;  // basis vectors per chunk of the reduction pass (each chunk re-reads u and w)
 
-// Loads of PTS consecutive points (PTS = 2: one 2-vector; PTS = 1: a scalar).
-template <typename T, int PTS>
-__device__ __forceinline__ void ldp(const T* p, int64_t q, T* o) {
-  if (PTS == 2) {
-    const typename V2<T>::t v = ((const typename V2<T>::t*)p)[q];
-    o[0] = v.x;
-    o[1] = v.y;
+// P consecutive values of one plane, starting at point q * P, widened to the arithmetic
+// type T.  S is the storage type: T itself (P = 1, 2, or 4 for float) or __half (P = 1, 2
+// or 4).
+template <typename T, int P, typename S>
+__device__ __forceinline__ void ldpts(const S* p, int64_t q, T* o) {
+  if constexpr (std::is_same<S, T>::value) {
+    if constexpr (P == 1) {
+      o[0] = p[q];
+    } else if constexpr (P == 2) {
+      const typename V2<T>::t v = ((const typename V2<T>::t*)p)[q];
+      o[0] = v.x;
+      o[1] = v.y;
+    } else {
+      static_assert(P == 4 && std::is_same<T, float>::value, "4-point loads are FP32 or FP16");
+      const float4 v = ((const float4*)p)[q];
+      o[0] = v.x;
+      o[1] = v.y;
+      o[2] = v.z;
+      o[3] = v.w;
+    }
   } else {
-    o[0] = p[q];
+    static_assert(std::is_same<S, __half>::value && std::is_same<T, float>::value, "FP16 storage, FP32 arithmetic");
+    if constexpr (P == 1) {
+      o[0] = __half2float(p[q]);
+    } else if constexpr (P == 2) {
+      const float2 a = __half22float2(((const __half2*)p)[q]);
+      o[0] = a.x;
+      o[1] = a.y;
+    } else {
+      static_assert(P == 4, "FP16 loads are 1, 2 or 4 points");
+      const uint2 raw = ((const uint2*)p)[q];
+      const float2 a = __half22float2(*(const __half2*)&raw.x), b = __half22float2(*(const __half2*)&raw.y);
+      o[0] = a.x;
+      o[1] = a.y;
+      o[2] = b.x;
+      o[3] = b.y;
+    }
   }
+}
+
+// The store matching ldpts: values rounded to S (round to nearest even).
+template <typename T, int P, typename S>
+__device__ __forceinline__ void stpts(S* p, int64_t q, const T* v) {
+  if constexpr (std::is_same<S, T>::value) {
+    if constexpr (P == 1) {
+      p[q] = v[0];
+    } else if constexpr (P == 2) {
+      ((typename V2<T>::t*)p)[q] = typename V2<T>::t{v[0], v[1]};
+    } else {
+      ((float4*)p)[q] = float4{v[0], v[1], v[2], v[3]};
+    }
+  } else {
+    if constexpr (P == 1) {
+      p[q] = __float2half_rn(v[0]);
+    } else if constexpr (P == 2) {
+      ((__half2*)p)[q] = __floats2half2_rn(v[0], v[1]);
+    } else {
+      const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+      uint2 raw;
+      raw.x = *(const uint32_t*)&a;
+      raw.y = *(const uint32_t*)&b;
+      ((uint2*)p)[q] = raw;
+    }
+  }
+}
+
+// P points of one plane held in registers as loaded: widened on use (get), so that an FP16
+// basis takes one register per two points.
+template <typename T, int P, typename S>
+struct PtsReg {
+  T v[P];
+  __device__ __forceinline__ void load(const S* p, int64_t q) { ldpts<T, P, S>(p, q, v); }
+  __device__ __forceinline__ T get(int k) const { return v[k]; }
+};
+template <>
+struct PtsReg<float, 1, __half> {
+  __half r;
+  __device__ __forceinline__ void load(const __half* p, int64_t q) { r = p[q]; }
+  __device__ __forceinline__ float get(int) const { return __half2float(r); }
+};
+template <>
+struct PtsReg<float, 4, __half> {
+  uint2 r;
+  __device__ __forceinline__ void load(const __half* p, int64_t q) { r = ((const uint2*)p)[q]; }
+  __device__ __forceinline__ float get(int k) const {
+    const __half2 h = *(const __half2*)(k < 2 ? &r.x : &r.y);
+    return (k & 1) ? __high2float(h) : __low2float(h);
+  }
+};
+template <>
+struct PtsReg<float, 2, __half> {
+  __half2 r;
+  __device__ __forceinline__ void load(const __half* p, int64_t q) { r = ((const __half2*)p)[q]; }
+  __device__ __forceinline__ float get(int k) const { return k == 0 ? __low2float(r) : __high2float(r); }
+};
+
+// x rounded to the storage type S and back (x itself when S is the arithmetic type).
+template <typename T, typename S>
+__device__ __forceinline__ T round_to(T x) {
+  if constexpr (std::is_same<S, T>::value)
+    return x;
+  else
+    return __half2float(__float2half_rn(x));
 }
 
 // One reduction pass over the basis V_0..V_{count-1}, u and (optionally) w.  Per block:
 //   s_i = sum conj(V_i) u,  t_i = sum conj(V_i) w  (i < count),
 //   a = sum |u|^2,  b = sum conj(u) w.
 // Partial layout per block (ncol = 4 count + 3 doubles): s (2 count), t (2 count), a, b (2).
-// Chunks of CHD basis vectors: the loads of a point's chunk are issued together; at the end
-// of a chunk every accumulator is reduced by warp shuffles and one shared-memory exchange
-// (a single barrier), so the per-block epilogue stays short.
-template <typename T, int PTS>
-__global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, int64_t vs, int count,
-                                                      const T* __restrict__ u, const T* __restrict__ w,
-                                                      int64_t N, double* __restrict__ partial) {
+// The basis is stored in TV (T, or FP16 holding vscale V_i with vscale a power of two), so
+// the s and t sums are multiplied by vinv = 1 / vscale in the block epilogue.  Chunks of CHD
+// basis vectors: the loads of a point's chunk are issued together; at the end of a chunk
+// every accumulator is reduced by warp shuffles and one shared-memory exchange (a single
+// barrier), so the per-block epilogue stays short.
+template <typename T, int PTS, typename TV>
+__global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(const TV* __restrict__ V, int64_t vs, int count,
+                                                         const T* __restrict__ u, const T* __restrict__ w,
+                                                         int64_t N, double* __restrict__ partial, double vinv) {
   constexpr int NACC = 4 * CHD + 3;
   __shared__ T sh[RB / 32][NACC];
   const int ncol = 4 * count + 3;
@@ -219,21 +317,21 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
     for (int c = 0; c < NACC; ++c) acc[c] = T(0);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
       T ur[PTS], ui[PTS], wr[PTS], wi[PTS];
-      ldp<T, PTS>(u, q, ur);
-      ldp<T, PTS>(u + N, q, ui);
+      ldpts<T, PTS, T>(u, q, ur);
+      ldpts<T, PTS, T>(u + N, q, ui);
 #pragma unroll
       for (int k = 0; k < PTS; ++k) wr[k] = wi[k] = T(0);
       if (hw) {
-        ldp<T, PTS>(w, q, wr);
-        ldp<T, PTS>(w + N, q, wi);
+        ldpts<T, PTS, T>(w, q, wr);
+        ldpts<T, PTS, T>(w + N, q, wi);
       }
-      T vr[CHD][PTS], vi[CHD][PTS];
+      PtsReg<T, PTS, TV> vr[CHD], vi[CHD];
 #pragma unroll
       for (int c = 0; c < CHD; ++c) {
         if (c < nc) {
-          const T* v = V + (int64_t)(base + c) * vs;
-          ldp<T, PTS>(v, q, vr[c]);
-          ldp<T, PTS>(v + N, q, vi[c]);
+          const TV* v = V + (int64_t)(base + c) * vs;
+          vr[c].load(v, q);
+          vi[c].load(v + N, q);
         }
       }
       if (ch == 0) {
@@ -249,10 +347,11 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
         if (c < nc) {
 #pragma unroll
           for (int k = 0; k < PTS; ++k) {
-            acc[4 * c] = fmx(vr[c][k], ur[k], fmx(vi[c][k], ui[k], acc[4 * c]));
-            acc[4 * c + 1] = fmx(vr[c][k], ui[k], fmx(-vi[c][k], ur[k], acc[4 * c + 1]));
-            acc[4 * c + 2] = fmx(vr[c][k], wr[k], fmx(vi[c][k], wi[k], acc[4 * c + 2]));
-            acc[4 * c + 3] = fmx(vr[c][k], wi[k], fmx(-vi[c][k], wr[k], acc[4 * c + 3]));
+            const T a = vr[c].get(k), b = vi[c].get(k);
+            acc[4 * c] = fmx(a, ur[k], fmx(b, ui[k], acc[4 * c]));
+            acc[4 * c + 1] = fmx(a, ui[k], fmx(-b, ur[k], acc[4 * c + 1]));
+            acc[4 * c + 2] = fmx(a, wr[k], fmx(b, wi[k], acc[4 * c + 2]));
+            acc[4 * c + 3] = fmx(a, wi[k], fmx(-b, wr[k], acc[4 * c + 3]));
           }
         }
       }
@@ -269,7 +368,7 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
       for (int ww = 0; ww < RB / 32; ++ww) sum += (double)sh[ww][c];
       if (c < 4 * CHD) {
         const int cc = c >> 2, kind = c & 3;
-        if (cc < nc) out[(kind < 2 ? 0 : 2 * count) + 2 * (base + cc) + (kind & 1)] = sum;
+        if (cc < nc) out[(kind < 2 ? 0 : 2 * count) + 2 * (base + cc) + (kind & 1)] = sum * vinv;
       } else if (ch == 0) {
         out[4 * count + (c - 4 * CHD)] = sum;
       }
@@ -281,18 +380,22 @@ __global__ void __launch_bounds__(RB) dcgs_dot_kernel(const T* __restrict__ V, i
 // One update pass.  coef (complex double unless noted): s[count], t[count], c, inv (real).
 //   v_new = (u - sum_i V_i s_i) inv          -> written to v_out (the basis slot `count`)
 //   u     = (w - sum_i V_i t_i - v_new c) inv -> written over u (in place)
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(RB) dcgs_update_kernel(const T* __restrict__ V, int64_t vs, int count,
-                                                         T* u, const T* __restrict__ w, T* __restrict__ v_out,
-                                                         int64_t N, const double* __restrict__ coef) {
+// With the basis stored in FP16 as vscale V_i, the coefficients are divided by vscale, v_out
+// receives vscale v_new rounded to FP16, and the correction of u uses that rounded vector,
+// so that u is orthogonalised against the basis as stored.  PTS points per thread; the basis
+// is read UB vectors at a time, all loads of a group issued before its FMAs.
+template <typename T, int PTS, typename TV>
+__global__ void __launch_bounds__(RB) dcgs_update_kernel(const TV* __restrict__ V, int64_t vs, int count,
+                                                         T* u, const T* __restrict__ w, TV* __restrict__ v_out,
+                                                         int64_t N, const double* __restrict__ coef, double vscale) {
   __shared__ T s_r[64], s_i[64], t_r[64], t_i[64];
   __shared__ T cc[3];
-  using T2 = typename V2<T>::t;
+  const double vinv = 1.0 / vscale;
   for (int c = threadIdx.x; c < count; c += blockDim.x) {
-    s_r[c] = (T)coef[2 * c];
-    s_i[c] = (T)coef[2 * c + 1];
-    t_r[c] = (T)coef[2 * count + 2 * c];
-    t_i[c] = (T)coef[2 * count + 2 * c + 1];
+    s_r[c] = (T)(coef[2 * c] * vinv);
+    s_i[c] = (T)(coef[2 * c + 1] * vinv);
+    t_r[c] = (T)(coef[2 * count + 2 * c] * vinv);
+    t_i[c] = (T)(coef[2 * count + 2 * c + 1] * vinv);
   }
   if (threadIdx.x == 0) {
     cc[0] = (T)coef[4 * count];
@@ -301,72 +404,58 @@ __global__ void __launch_bounds__(RB) dcgs_update_kernel(const T* __restrict__ V
   }
   __syncthreads();
   const T cr = cc[0], ci = cc[1], inv = cc[2];
-  const int64_t npts = VEC ? N / 2 : N;
+  const T vsc = (T)vscale, vin = (T)vinv;  // powers of two: exact in T
+  const int64_t npts = N / PTS;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  auto one = [&](int64_t q) {
-    T ur = u[q], ui = u[N + q];
-    T wr = w[q], wi = w[N + q];
-    for (int c = 0; c < count; ++c) {
-      const T* v = V + (int64_t)c * vs;
-      const T vr = v[q], vi = v[N + q];
-      ur = fmx(-vr, s_r[c], fmx(vi, s_i[c], ur));
-      ui = fmx(-vr, s_i[c], fmx(-vi, s_r[c], ui));
-      wr = fmx(-vr, t_r[c], fmx(vi, t_i[c], wr));
-      wi = fmx(-vr, t_i[c], fmx(-vi, t_r[c], wi));
-    }
-    const T nr = ur * inv, ni = ui * inv;
-    v_out[q] = nr;
-    v_out[N + q] = ni;
-    wr = fmx(-nr, cr, fmx(ni, ci, wr));
-    wi = fmx(-nr, ci, fmx(-ni, cr, wi));
-    u[q] = wr * inv;
-    u[N + q] = wi * inv;
-  };
+  constexpr int UB = 8;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
-    if (VEC) {
-      T2 ur = ((const T2*)u)[q], ui = ((const T2*)(u + N))[q];
-      T2 wr = ((const T2*)w)[q], wi = ((const T2*)(w + N))[q];
-      // basis vectors in groups of UB: all loads of a group are issued before its FMAs
-      constexpr int UB = 8;
-      for (int c0 = 0; c0 < count; c0 += UB) {
-        T2 vr[UB], vi[UB];
+    T ur[PTS], ui[PTS], wr[PTS], wi[PTS];
+    ldpts<T, PTS, T>(u, q, ur);
+    ldpts<T, PTS, T>(u + N, q, ui);
+    ldpts<T, PTS, T>(w, q, wr);
+    ldpts<T, PTS, T>(w + N, q, wi);
+    for (int c0 = 0; c0 < count; c0 += UB) {
+      PtsReg<T, PTS, TV> vr[UB], vi[UB];
 #pragma unroll
-        for (int e = 0; e < UB; ++e) {
-          if (c0 + e < count) {
-            const T* v = V + (int64_t)(c0 + e) * vs;
-            vr[e] = ((const T2*)v)[q];
-            vi[e] = ((const T2*)(v + N))[q];
-          }
+      for (int e = 0; e < UB; ++e) {
+        if (c0 + e < count) {
+          const TV* v = V + (int64_t)(c0 + e) * vs;
+          vr[e].load(v, q);
+          vi[e].load(v + N, q);
         }
+      }
 #pragma unroll
-        for (int e = 0; e < UB; ++e) {
-          if (c0 + e < count) {
-            const int c = c0 + e;
-            ur.x = fmx(-vr[e].x, s_r[c], fmx(vi[e].x, s_i[c], ur.x));
-            ui.x = fmx(-vr[e].x, s_i[c], fmx(-vi[e].x, s_r[c], ui.x));
-            ur.y = fmx(-vr[e].y, s_r[c], fmx(vi[e].y, s_i[c], ur.y));
-            ui.y = fmx(-vr[e].y, s_i[c], fmx(-vi[e].y, s_r[c], ui.y));
-            wr.x = fmx(-vr[e].x, t_r[c], fmx(vi[e].x, t_i[c], wr.x));
-            wi.x = fmx(-vr[e].x, t_i[c], fmx(-vi[e].x, t_r[c], wi.x));
-            wr.y = fmx(-vr[e].y, t_r[c], fmx(vi[e].y, t_i[c], wr.y));
-            wi.y = fmx(-vr[e].y, t_i[c], fmx(-vi[e].y, t_r[c], wi.y));
+      for (int e = 0; e < UB; ++e) {
+        if (c0 + e < count) {
+          const int c = c0 + e;
+#pragma unroll
+          for (int k = 0; k < PTS; ++k) {
+            const T a = vr[e].get(k), b = vi[e].get(k);
+            ur[k] = fmx(-a, s_r[c], fmx(b, s_i[c], ur[k]));
+            ui[k] = fmx(-a, s_i[c], fmx(-b, s_r[c], ui[k]));
+            wr[k] = fmx(-a, t_r[c], fmx(b, t_i[c], wr[k]));
+            wi[k] = fmx(-a, t_i[c], fmx(-b, t_r[c], wi[k]));
           }
         }
       }
-      const T2 nr = {ur.x * inv, ur.y * inv}, ni = {ui.x * inv, ui.y * inv};
-      ((T2*)v_out)[q] = nr;
-      ((T2*)(v_out + N))[q] = ni;
-      wr.x = fmx(-nr.x, cr, fmx(ni.x, ci, wr.x));
-      wi.x = fmx(-nr.x, ci, fmx(-ni.x, cr, wi.x));
-      wr.y = fmx(-nr.y, cr, fmx(ni.y, ci, wr.y));
-      wi.y = fmx(-nr.y, ci, fmx(-ni.y, cr, wi.y));
-      ((T2*)u)[q] = T2{wr.x * inv, wr.y * inv};
-      ((T2*)(u + N))[q] = T2{wi.x * inv, wi.y * inv};
-    } else {
-      one(q);
     }
+    T nr[PTS], ni[PTS];
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+      nr[k] = ur[k] * inv * vsc;
+      ni[k] = ui[k] * inv * vsc;
+    }
+    stpts<T, PTS, TV>(v_out, q, nr);
+    stpts<T, PTS, TV>(v_out + N, q, ni);
+#pragma unroll
+    for (int k = 0; k < PTS; ++k) {
+      const T a = round_to<T, TV>(nr[k]) * vin, b = round_to<T, TV>(ni[k]) * vin;
+      wr[k] = fmx(-a, cr, fmx(b, ci, wr[k])) * inv;
+      wi[k] = fmx(-a, ci, fmx(-b, cr, wi[k])) * inv;
+    }
+    stpts<T, PTS, T>(u, q, wr);
+    stpts<T, PTS, T>(u + N, q, wi);
   }
-  if (VEC && (N & 1) && blockIdx.x == 0 && threadIdx.x == 0) one(N - 1);
 }
 
 // ---- GMRES least squares (FP64, one thread) ----
@@ -791,39 +880,63 @@ int cgs_blocks(int64_t N) {
   return (int)std::max<int64_t>(1, std::min(g, cap));
 }
 
-template <typename T>
-void launch_dcgs_dot(const T* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
-                     int nblocks, cudaStream_t s) {
+// Points per thread of the two Gram-Schmidt passes, as many as the planes' alignment allows
+// up to 2 for an FP32 or FP64 basis (one 8- or 16-byte load per plane and vector) and 4 for
+// an FP16 one (8-byte basis loads; fewer instructions per byte than 2 points).
+template <typename TV>
+int cgs_pts(int64_t N, int64_t vs) {
+  if (std::is_same<TV, __half>::value && N % 4 == 0 && vs % 4 == 0) return 4;
+  return (N % 2 == 0 && vs % 2 == 0) ? 2 : 1;
+}
+
+template <typename T, typename TV>
+void launch_dcgs_dot(const TV* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
+                     int nblocks, double vscale, cudaStream_t s) {
   note_launch();
-  if ((vs & 1) == 0 && (N & 1) == 0)
-    dcgs_dot_kernel<T, 2><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial);
+  const double vinv = 1.0 / vscale;
+  const int p = cgs_pts<TV>(N, vs);
+  if constexpr (std::is_same<TV, __half>::value) {
+    if (p == 4) {
+      dcgs_dot_kernel<T, 4, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
+      return;
+    }
+  }
+  if (p == 2)
+    dcgs_dot_kernel<T, 2, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
   else
-    dcgs_dot_kernel<T, 1><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial);
+    dcgs_dot_kernel<T, 1, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
 }
 
 // Blocks of the reduction pass: two per SM (its per-block epilogue favours few blocks).
 int dot_blocks() { return 2 * device_sm_count(); }
 
-template <typename T>
-void launch_dcgs_update(const T* V, int64_t vs, int count, T* u, const T* w, T* v_out, int64_t N,
-                        const double* coef, int nblocks, cudaStream_t s) {
+template <typename T, typename TV>
+void launch_dcgs_update(const TV* V, int64_t vs, int count, T* u, const T* w, TV* v_out, int64_t N,
+                        const double* coef, int nblocks, double vscale, cudaStream_t s) {
   note_launch();
-  if ((vs & 1) == 0 && (N & 1) == 0)
-    dcgs_update_kernel<T, true><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef);
+  const int p = cgs_pts<TV>(N, vs);
+  if constexpr (std::is_same<TV, __half>::value) {
+    if (p == 4) {
+      dcgs_update_kernel<T, 4, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef, vscale);
+      return;
+    }
+  }
+  if (p == 2)
+    dcgs_update_kernel<T, 2, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef, vscale);
   else
-    dcgs_update_kernel<T, false><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef);
+    dcgs_update_kernel<T, 1, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef, vscale);
 }
 
 template int cgs_blocks<float>(int64_t);
 template int cgs_blocks<double>(int64_t);
-template void launch_dcgs_dot<float>(const float*, int64_t, int, const float*, const float*, int64_t, double*, int,
-                                     cudaStream_t);
-template void launch_dcgs_dot<double>(const double*, int64_t, int, const double*, const double*, int64_t, double*,
-                                      int, cudaStream_t);
-template void launch_dcgs_update<float>(const float*, int64_t, int, float*, const float*, float*, int64_t,
-                                        const double*, int, cudaStream_t);
-template void launch_dcgs_update<double>(const double*, int64_t, int, double*, const double*, double*, int64_t,
-                                         const double*, int, cudaStream_t);
+#define INST_CGS(T, TV)                                                                              \
+  template void launch_dcgs_dot<T, TV>(const TV*, int64_t, int, const T*, const T*, int64_t, double*, int, double, \
+                                       cudaStream_t);                                                          \
+  template void launch_dcgs_update<T, TV>(const TV*, int64_t, int, T*, const T*, TV*, int64_t, const double*, int, \
+                                          double, cudaStream_t);
+INST_CGS(float, float)
+INST_CGS(float, __half)
+INST_CGS(double, double)
 
 #define INST_T(T)                                                                              \
   template void launch_sumsq<T>(const T*, int64_t, double*, int, cudaStream_t);                  \

@@ -18,6 +18,7 @@ GMRES, FGMRES, SKS, CHEB = 0, 1, 2, 3
 MAX_HIST = 1024
 CNN_NPARAMS = 15602
 CNN_OFF, CNN_ON, CNN_AUTO = 0, 1, 2
+BASIS_AUTO, BASIS_F32, BASIS_F16 = 0, 1, 2
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "DIVERGED", 3: "BREAKDOWN", 4: "NONFINITE",
           -1: "ERR_INVALID", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED"}
@@ -25,7 +26,7 @@ STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "DIVERGED", 3: "BREAKDOWN", 4: "NONFIN
 _FACE_CODE = {"D": DIRICHLET, "N": NEUMANN, "S": SOMMERFELD}
 
 # every symbol declared in include/helm6.h
-EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_apply_A", "helm6_apply_Pinv",
+EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_basis", "helm6_apply_A", "helm6_apply_Pinv",
            "helm6_solve", "helm6_rhs_gaussians", "helm6_destroy", "helm6_status_string",
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
@@ -44,7 +45,8 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("method", C.c_int), ("xform_terms", C.c_int),
                 ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int),
-                ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("own_stream", C.c_int)]
+                ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("own_stream", C.c_int),
+                ("basis", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -86,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_create.restype = I
     lib.helm6_dims.argtypes = [P, C.POINTER(C.c_int64)]
     lib.helm6_dims.restype = I
+    lib.helm6_basis.argtypes = [P]
+    lib.helm6_basis.restype = I
     lib.helm6_apply_A.argtypes = [P, P, P]
     lib.helm6_apply_A.restype = I
     lib.helm6_apply_Pinv.argtypes = [P, P, P]
@@ -180,7 +184,7 @@ class Solver:
 
     def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
                  max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None, use_graphs=False,
-                 dot_blocks=0, update_blocks=0, own_stream=False, cheb_bounds=(0.0, 0.0)):
+                 dot_blocks=0, update_blocks=0, own_stream=False, cheb_bounds=(0.0, 0.0), basis=BASIS_AUTO):
         lib = load()
         self._lib = lib
         o = Opts()
@@ -189,6 +193,7 @@ class Solver:
         o.inner_tol, o.xform_terms = inner_tol, xform_terms
         o.use_graphs, o.dot_blocks, o.update_blocks = int(bool(use_graphs)), int(dot_blocks), int(update_blocks)
         o.own_stream = int(bool(own_stream))
+        o.basis = int(basis)
         o.cheb_lo, o.cheb_hi = float(cheb_bounds[0]), float(cheb_bounds[1])
         if stream is not None:
             o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -205,6 +210,12 @@ class Solver:
         self.shape = (d[2], d[1], d[0])
         self.n, self.k, self.faces = n, kk, faces
         self.h = h if h > 0 else 1.0 / (n + 1)
+
+    @property
+    def basis(self):
+        """Storage of the Krylov basis as resolved at creation: BASIS_F32 or BASIS_F16 (MIXED
+        GMRES/FGMRES), BASIS_AUTO where it is FP64 or there is none."""
+        return _check(self._lib.helm6_basis(self._ctx), "helm6_basis")
 
     def close(self):
         if getattr(self, "_ctx", None):
