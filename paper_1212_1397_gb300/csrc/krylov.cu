@@ -292,30 +292,43 @@ __device__ __forceinline__ T round_to(T x) {
 //   a = sum |u|^2,  b = sum conj(u) w.
 // Partial layout per block (ncol = 4 count + 3 doubles): s (2 count), t (2 count), a, b (2).
 // The basis is stored in TV (T, or FP16 holding vscale V_i with vscale a power of two), so
-// the s and t sums are multiplied by vinv = 1 / vscale in the block epilogue.  Chunks of CHD
-// basis vectors: the loads of a point's chunk are issued together; at the end of a chunk
-// every accumulator is reduced by warp shuffles and one shared-memory exchange (a single
-// barrier), so the per-block epilogue stays short.
+// the s and t sums are multiplied by vinv = 1 / vscale in the block epilogue.
+// The block's warps form G = 1, 2 or 4 groups (the fewest with at most CHD basis vectors
+// each); all groups walk the same points, each reducing its own share of the basis, so u
+// and w come from DRAM once (the other groups' loads of them hit L1) however many vectors
+// there are.  More than G * CHD vectors (restarts beyond 32) take further rounds.  At the
+// end of a round every accumulator is reduced by warp shuffles and one shared-memory
+// exchange.
 template <typename T, int PTS, typename TV>
 __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(const TV* __restrict__ V, int64_t vs, int count,
                                                          const T* __restrict__ u, const T* __restrict__ w,
                                                          int64_t N, double* __restrict__ partial, double vinv) {
+  constexpr int NW = RB / 32;
   constexpr int NACC = 4 * CHD + 3;
-  __shared__ T sh[RB / 32][NACC];
+  __shared__ T sh[NW][NACC];
   const int ncol = 4 * count + 3;
   const bool hw = (w != nullptr);
   const int64_t npts = N / PTS;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double* out = partial + (int64_t)blockIdx.x * ncol;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nchunk = count > 0 ? (count + CHD - 1) / CHD : 1;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int base = ch * CHD;
-    const int nc = min(CHD, count - base);
+  const int G = count <= CHD ? 1 : count <= 2 * CHD ? 2 : 4;
+  const int wpg = NW / G;                     // warps per group
+  const int grp = warp / wpg;
+  const int tig = (warp % wpg) * 32 + lane;   // thread within the group
+  const int64_t tpg = (int64_t)wpg * 32;
+  const int64_t stride = (int64_t)gridDim.x * tpg;
+  const int nround = count > 0 ? (count + G * CHD - 1) / (G * CHD) : 1;
+  for (int rd = 0; rd < nround; ++rd) {
+    const int rbase = rd * G * CHD;
+    const int rcount = min(G * CHD, count - rbase);
+    const int cpg = (rcount + G - 1) / G;
+    const int base = rbase + grp * cpg;
+    const int nc = max(0, min(cpg, rcount - grp * cpg));
+    const bool own = (rd == 0 && grp == 0);   // this group also forms a and b
     T acc[NACC];
 #pragma unroll
     for (int c = 0; c < NACC; ++c) acc[c] = T(0);
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
+    for (int64_t q = (int64_t)blockIdx.x * tpg + tig; q < npts; q += stride) {
       T ur[PTS], ui[PTS], wr[PTS], wi[PTS];
       ldpts<T, PTS, T>(u, q, ur);
       ldpts<T, PTS, T>(u + N, q, ui);
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
           vi[c].load(v + N, q);
         }
       }
-      if (ch == 0) {
+      if (own) {
 #pragma unroll
         for (int k = 0; k < PTS; ++k) {
           acc[4 * CHD] = fmx(ur[k], ur[k], fmx(ui[k], ui[k], acc[4 * CHD]));
@@ -363,13 +376,17 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
       if (lane == 0) sh[warp][c] = v;
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < NACC; c += blockDim.x) {
+    // group gg's sums over its wpg warps; column c of its accumulators
+    for (int e = threadIdx.x; e < G * NACC; e += blockDim.x) {
+      const int gg = e / NACC, c = e - gg * NACC;
       double sum = 0.0;
-      for (int ww = 0; ww < RB / 32; ++ww) sum += (double)sh[ww][c];
+      for (int ww = 0; ww < wpg; ++ww) sum += (double)sh[gg * wpg + ww][c];
+      const int gbase = rbase + gg * cpg;
+      const int gnc = max(0, min(cpg, rcount - gg * cpg));
       if (c < 4 * CHD) {
         const int cc = c >> 2, kind = c & 3;
-        if (cc < nc) out[(kind < 2 ? 0 : 2 * count) + 2 * (base + cc) + (kind & 1)] = sum * vinv;
-      } else if (ch == 0) {
+        if (cc < gnc) out[(kind < 2 ? 0 : 2 * count) + 2 * (gbase + cc) + (kind & 1)] = sum * vinv;
+      } else if (rd == 0 && gg == 0) {
         out[4 * count + (c - 4 * CHD)] = sum;
       }
     }
