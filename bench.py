@@ -57,10 +57,10 @@ KERNEL_OF = {
 }
 
 # ncu DRAM bytes (read + write) per launch of a kernel over that launch's algorithmic bytes,
-# from the 128^3 capture summarised in profiles/dram_mixed_n128_k40.md (absent: not captured
-# since the kernel last changed).  The reduction pass reads its j + 2 fields once, so its
-# traffic grows with the fields it reads and the ratio carries to the 256^3 launches.
-NCU_TRAFFIC_RATIO = {}
+# from the capture at the bench size summarised in profiles/dram_dcgs_dot_f16_n256.md
+# (bytes-weighted over launches with 0-4 and 28-30 basis vectors; absent: not captured since
+# the kernel last changed).
+NCU_TRAFFIC_RATIO = {"dcgs_dot_kernel<float,4,__half>": 1.045}
 
 
 def peaks():
@@ -390,8 +390,9 @@ def main():
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
             "traffic": (NCU_TRAFFIC_RATIO[kernel_of[dom]] * alg_bytes if kernel_of[dom] in NCU_TRAFFIC_RATIO
                         else None),
-            "traffic_source": ("ncu dram bytes at 128^3 (profiles/dram_mixed_n128_k40.md), per launch scaled "
-                               "by the algorithmic bytes" if kernel_of[dom] in NCU_TRAFFIC_RATIO else None),
+            "traffic_source": ("ncu dram bytes at the bench size (profiles/dram_dcgs_dot_f16_n256.md): "
+                               "traffic / algorithmic bytes of the captured launches x this run's mean "
+                               "algorithmic bytes per launch" if kernel_of[dom] in NCU_TRAFFIC_RATIO else None),
             "per_launch_ms": per_launch_ms,
             "alg_bytes_per_launch": alg_bytes,
             "phase_frac": {p: (phases[p]["bytes"] / (phases[p]["ms"] * 1e-3) / 1e9) / hbm
