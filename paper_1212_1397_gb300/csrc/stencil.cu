@@ -220,7 +220,9 @@ __device__ __forceinline__ int ghost_index(int gi, int m, int lo_neumann, int hi
 
 // NORM: accumulate the block's |y|^2 (FP64) into sumsq; a compile-time flag so that the
 // FP32 path carries no FP64 arithmetic when no norm is wanted.
-template <int MODE, bool NORM>
+// RW: the interior weights are real (a real wavenumber), so each class term is two real
+// FMAs instead of a complex multiply-add.
+template <int MODE, bool NORM, bool RW>
 __global__ void __launch_bounds__(T4X* T4Y / T4R)
     stencil4_kernel(Geom g, StencilCoef coef, const float* __restrict__ x, float* __restrict__ y,
                     const float* __restrict__ f, double* __restrict__ sumsq) {
@@ -352,13 +354,19 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
         vi[rr][cc] = sbuf[buf][1][T4R * ty + rr][tx + 3 + cc];
       }
     }
+    // x-neighbour sums of the six halo rows, shared by the four points' face and diagonal sums
+    float hr[T4R + 2], hi[T4R + 2];
+#pragma unroll
+    for (int rr = 0; rr < T4R + 2; ++rr) {
+      hr[rr] = vr[rr][0] + vr[rr][2];
+      hi[rr] = vi[rr][0] + vi[rr][2];
+    }
 #pragma unroll
     for (int r = 0; r < T4R; ++r) {
       Sums<float> cur;
       cur.c = mk(vr[r + 1][1], vi[r + 1][1]);
-      cur.n = mk(vr[r + 1][0] + vr[r + 1][2] + vr[r][1] + vr[r + 2][1],
-                 vi[r + 1][0] + vi[r + 1][2] + vi[r][1] + vi[r + 2][1]);
-      cur.d = mk(vr[r][0] + vr[r][2] + vr[r + 2][0] + vr[r + 2][2], vi[r][0] + vi[r][2] + vi[r + 2][0] + vi[r + 2][2]);
+      cur.n = mk(hr[r + 1] + vr[r][1] + vr[r + 2][1], hi[r + 1] + vi[r][1] + vi[r + 2][1]);
+      cur.d = mk(hr[r] + hr[r + 2], hi[r] + hi[r + 2]);
       P0[r] = P1[r];
       P1[r] = P2[r];
       P2[r] = cur;
@@ -373,10 +381,17 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
         if (j >= g.my) continue;
         cpx<float> out;
         if (!slo && !shi) {
-          out = c0 * P1[r].c;
-          out = cfma(c1, P1[r].n + P0[r].c + P2[r].c, out);
-          out = cfma(c2, P1[r].d + P0[r].n + P2[r].n, out);
-          out = cfma(c3, P0[r].d + P2[r].d, out);
+          const cpx<float> s1 = P1[r].n + P0[r].c + P2[r].c, s2 = P1[r].d + P0[r].n + P2[r].n,
+                           s3 = P0[r].d + P2[r].d;
+          if constexpr (RW) {
+            out.re = fmaf(c3.re, s3.re, fmaf(c2.re, s2.re, fmaf(c1.re, s1.re, c0.re * P1[r].c.re)));
+            out.im = fmaf(c3.re, s3.im, fmaf(c2.re, s2.im, fmaf(c1.re, s1.im, c0.re * P1[r].c.im)));
+          } else {
+            out = c0 * P1[r].c;
+            out = cfma(c1, s1, out);
+            out = cfma(c2, s2, out);
+            out = cfma(c3, s3, out);
+          }
         } else {
           out = zero;
 #pragma unroll
@@ -440,16 +455,26 @@ void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const
     float* yf = (float*)y;
     const float* ff = (const float*)f;
     const bool nrm = sumsq != nullptr;
+    const bool rw = c.interior.w[1][0].im == 0.0 && c.interior.w[1][1].im == 0.0 &&
+                    c.interior.w[1][2].im == 0.0 && c.interior.w[0][2].im == 0.0;
+#define HELM6_S4(M, N)                                                                   \
+  do {                                                                                   \
+    if (rw)                                                                              \
+      stencil4_kernel<M, N, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, N ? sumsq : nullptr);  \
+    else                                                                                 \
+      stencil4_kernel<M, N, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, N ? sumsq : nullptr); \
+  } while (0)
     if (mode == 0 && !nrm)
-      stencil4_kernel<0, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+      HELM6_S4(0, false);
     else if (mode == 0)
-      stencil4_kernel<0, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+      HELM6_S4(0, true);
     else if (mode == 1 && !nrm)
-      stencil4_kernel<1, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+      HELM6_S4(1, false);
     else if (mode == 1)
-      stencil4_kernel<1, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, sumsq);
+      HELM6_S4(1, true);
     else
-      stencil4_kernel<2, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, nullptr);
+      HELM6_S4(2, false);
+#undef HELM6_S4
     return;
   }
   dim3 block(TX, TY);
