@@ -103,3 +103,21 @@ def test_auto_basis_resolution(H):
         assert s.basis == H.BASIS_AUTO
     with H.Solver(64, 20.0, "DDDDDD", precision=H.MIXED, method=H.SKS) as s:
         assert s.basis == H.BASIS_AUTO
+
+
+@pytest.mark.parametrize("precision,method,basis", [("MIXED", "FGMRES", "BASIS_F16"), ("MIXED", "FGMRES", "BASIS_F32"),
+                                                    ("FP64", "GMRES", "BASIS_AUTO")])
+def test_restart_beyond_32_vectors(H, precision, method, basis):
+    """Restart 40: the reduction pass covers more than 32 basis vectors in two rounds of its
+    warp groups (at most 8 vectors per group, 4 groups per round)."""
+    n, k, faces = 24, 26.0, "DDNNSS"  # about 110 GMRES(40) iterations
+    prob, F = _problem(n, k, faces, 77, nsrc=3)
+    Uref, info = O.solve(prob, F, tol=1e-12, restart=40, maxit=1000)
+    assert info["converged"]
+    tol = 1e-8 if precision == "MIXED" else 1e-10
+    with H.Solver(n, k, faces, precision=getattr(H, precision), method=getattr(H, method), max_restart=40,
+                  basis=getattr(H, basis)) as s:
+        u, st = s.solve(torch.from_numpy(F).cuda(), tol=tol, restart=40, maxit=1000)
+    assert st["rc"] == 0 and st["relres"] <= tol, st["status"]
+    assert st["iters"] > 32  # the last cycle reached more than 32 vectors
+    assert rel2(u.cpu().numpy(), Uref) < (1e-6 if precision == "MIXED" else 1e-8)
