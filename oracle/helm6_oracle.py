@@ -22,8 +22,12 @@ Readings of the paper taken here where it is garbled or silent:
   * Edges and corners: a homogeneous Neumann face is an even reflection of the unknowns
     for every ghost value needed anywhere (including the in-plane differences of another
     face's elimination); its data term is added to that face's own rows only.
-  * Sommerfeld-like faces are allowed on z only (the preconditioner of Section 3.3 assumes
-    it).
+  * Sommerfeld-like faces are allowed on one axis pair.  The paper writes the face rows for
+    the z faces only and the scheme is symmetric under exchanging axes, so Sommerfeld-like
+    faces on the x (or y) pair are the z-face problem with the x and z (or y and z) axes
+    exchanged; the operator and the preconditioner are applied that way (the right side's
+    face terms are written per axis and need no exchange).  Two axes with Sommerfeld-like
+    faces would need a complex eigenbasis in x or y and are not supported.
 """
 from __future__ import annotations
 
@@ -48,8 +52,19 @@ class Problem:
     def __post_init__(self):
         self.k = complex(self.k)
         assert len(self.faces) == 6 and all(c in FACES for c in self.faces)
-        assert "S" not in self.faces[:4], "Sommerfeld-like faces only on z"
+        s_axes = [a for a in range(3) if "S" in self.faces[2 * a:2 * a + 2]]
+        assert len(s_axes) <= 1, "Sommerfeld-like faces on one axis pair only"
+        self.s_axis = s_axes[0] if s_axes else None
         self.h = 1.0 / (self.n + 1)
+
+    def exchanged(self) -> "Problem":
+        """The same problem with the Sommerfeld-like axis exchanged with z."""
+        f = self.faces
+        if self.s_axis == 0:
+            return Problem(self.n, self.k, f[4:6] + f[2:4] + f[0:2])
+        if self.s_axis == 1:
+            return Problem(self.n, self.k, f[0:2] + f[4:6] + f[2:4])
+        return self
 
     def face(self, axis: int, side: int) -> str:
         return self.faces[2 * axis + side]
@@ -119,6 +134,12 @@ def sommerfeld_coefficients(k: complex, h: float) -> dict:
 # Finite-difference building blocks on ghost-padded arrays
 # ======================================================================================
 
+def exchange(U: np.ndarray, s_axis: int) -> np.ndarray:
+    """Array [z, y, x] of a problem with Sommerfeld-like faces on axis s_axis (0 = x, 1 = y)
+    as the array of its exchanged problem, and back (the exchange is its own inverse)."""
+    return np.ascontiguousarray(np.swapaxes(U, 0, 2 - s_axis))
+
+
 def _second_difference(P: np.ndarray, axis: int) -> np.ndarray:
     """[1, -2, 1] along `axis`; the result is two shorter along that axis."""
     n = P.shape[axis]
@@ -172,8 +193,12 @@ def apply_A(prob: Problem, U: np.ndarray, boundary=None) -> np.ndarray:
     ghost layer is the even reflection (Eq. 3DN with homogeneous data; the f terms of
     Eq. 3DN go to the right side).  At a Sommerfeld-like face the ghost plane's
     contribution B U_{-1} is replaced by G1 U_1 + G0 U_0 (Eq. 3DDISCS; its data term goes
-    to the right side).
+    to the right side).  Sommerfeld-like faces on x or y: the z-face rows on the exchanged
+    problem (see the header).
     """
+    if prob.s_axis in (0, 1):
+        assert boundary is None, "face data with Sommerfeld-like faces on x or y"
+        return exchange(apply_A(prob.exchanged(), exchange(U, prob.s_axis)), prob.s_axis)
     h, k = prob.h, prob.k
     c = scheme_coefficients(k, h)
     P = _pad_ghosts(prob, U, boundary)
@@ -362,7 +387,10 @@ def axis_matrix(prob: Problem, axis: int) -> np.ndarray:
 
 
 def apply_Ap(prob: Problem, U: np.ndarray) -> np.ndarray:
-    """A_p U = (T_x (+) T_y (+) T_z) U, the 7-point operator of Eq. 3DAP."""
+    """A_p U = (T_x (+) T_y (+) T_z) U, the 7-point operator of Eq. 3DAP (Sommerfeld-like
+    faces on x or y: on the exchanged problem)."""
+    if prob.s_axis in (0, 1):
+        return exchange(apply_Ap(prob.exchanged(), exchange(U, prob.s_axis)), prob.s_axis)
     Tx, Ty, Tz = (axis_matrix(prob, a) for a in range(3))
     return (np.einsum("xi,zyi->zyx", Tx, U) + np.einsum("yi,zix->zyx", Ty, U)
             + np.einsum("zi,iyx->zyx", Tz, U))
@@ -378,6 +406,10 @@ class Preconditioner:
 
     def __init__(self, prob: Problem):
         self.prob = prob
+        # Sommerfeld-like faces on x or y: the preconditioner of the exchanged problem
+        self.inner = Preconditioner(prob.exchanged()) if prob.s_axis in (0, 1) else None
+        if self.inner is not None:
+            return
         self.lam, self.V, self.W = [], [], []
         for axis in (0, 1):
             T = axis_matrix(prob, axis).real
@@ -393,6 +425,9 @@ class Preconditioner:
         self.d = np.diag(Tz).copy()
 
     def __call__(self, Y: np.ndarray) -> np.ndarray:
+        if self.inner is not None:
+            return exchange(self.inner(exchange(np.asarray(Y, dtype=np.complex128), self.prob.s_axis)),
+                            self.prob.s_axis)
         Wx, Wy = self.W
         Vx, Vy = self.V
         lx, ly = self.lam

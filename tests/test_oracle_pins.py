@@ -435,3 +435,72 @@ def test_dirichlet_ratio_bounds_against_closed_form():
     r = [lambda_3d(i, j, l, prob.h, 7.0) for i in range(1, 12) for j in range(1, 12) for l in range(1, 12)]
     ratio = np.array([la / lp for la, lp in r]).real
     assert abs(lo - ratio.min()) < 1e-12 and abs(hi - ratio.max()) < 1e-12
+
+
+# --------------------------------------------------------------------------------------
+# Sommerfeld-like faces on the x or y pair (the z-face rows by symmetry of the scheme)
+# --------------------------------------------------------------------------------------
+
+def _radiating(k, b=0.7):
+    """phi(t) with phi' + ik phi = 0 at t = 0 and phi' - ik phi = 0 at t = 1."""
+    a = (2j * k + b * (2j * k - 3)) / (2 - 2j * k)
+    return S.PolyExp([1, 0, a, b], -1j * k)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_sommerfeld_face_truncation_order_x_y(axis):
+    """The face rows on an x (or y) Sommerfeld-like pair are O(h^7), as on z: the radiating
+    factor is on that axis, an even Neumann factor on a Neumann pair, a Dirichlet factor on
+    the third axis."""
+    k = 7.0 + 0.2j
+    som = _radiating(k)
+    even_neu = S.Sum1D(S.cos1d(np.pi), S.Scaled1D(0.3, S.cos1d(2 * np.pi)))
+    dir_ = S.PolyExp([0, 1, -1], 0.4)
+    if axis == 0:
+        faces, fac = "SSNNDD", (som, even_neu, dir_)
+    else:
+        faces, fac = "NNSSDD", (even_neu, som, dir_)
+    u = S.Separable([(1.0,) + fac])
+    out = []
+    for n in (15, 31):
+        prob, r = row_residual(n, k, faces, u)
+        lo = np.take(r, 0, axis=2 - axis).max()
+        hi = np.take(r, -1, axis=2 - axis).max()
+        inner = np.take(r, np.arange(1, r.shape[2 - axis] - 1), axis=2 - axis).max()
+        out.append((lo, hi, inner))
+    assert order(out[0][0], out[1][0]) > 6.6, out
+    assert order(out[0][1], out[1][1]) > 6.6, out
+    assert order(out[0][2], out[1][2]) > 7.5, out
+
+
+def test_sommerfeld_x_sixth_order_convergence():
+    """Sommerfeld-like x faces, Dirichlet y/z: the solve's error falls by ~2^6 per halving
+    of h (the z-face experiment of Section 4.2.3 with x and z exchanged)."""
+    k = 20.0
+    c = 1j * k / (1 - 1j * k)
+    rad = S.PolyExp([1, 0, c], -1j * k)
+    u = S.Separable([(1.0, rad, S.poly_times([0, 1, -1], S.cos1d(k * np.pi)), X3)])
+    errs = []
+    for n in (47, 95):
+        prob = O.Problem(n, k, "SSDDDD")
+        F = O.rhs(prob, S.helmholtz_source(u, k))
+        errs.append(solve_error(prob, u, F)[2])
+    assert np.log(errs[0] / errs[1]) / np.log(96 / 48) > 5.5, errs
+
+
+@pytest.mark.parametrize("faces", ["SSNNDD", "DNSSND"])
+def test_exchanged_operator_and_preconditioner_consistency(faces):
+    """apply_A, A_p and A_p^{-1} of a problem with Sommerfeld-like faces on x or y are
+    those of the exchanged problem on the exchanged array (by construction), and A_p^{-1}
+    inverts A_p there (an independent check of the exchange in both directions)."""
+    prob = O.Problem(6, 4.0 + 0.1j, faces)
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal(prob.shape) + 1j * rng.standard_normal(prob.shape)
+    M = O.Preconditioner(prob)
+    np.testing.assert_allclose(M(O.apply_Ap(prob, U)), U, rtol=0, atol=1e-10 * np.abs(U).max())
+    # the operator's matrix equals the exchanged problem's matrix with rows and columns permuted
+    A = O.dense_matrix(lambda V: O.apply_A(prob, V), prob.shape)
+    pe = prob.exchanged()
+    Ae = O.dense_matrix(lambda V: O.apply_A(pe, V), pe.shape)
+    idx = O.exchange(np.arange(A.shape[0]).reshape(pe.shape), prob.s_axis).ravel()
+    np.testing.assert_allclose(A, Ae[np.ix_(idx, idx)], rtol=0, atol=1e-14)
