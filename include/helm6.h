@@ -14,8 +14,11 @@
  * Grid and unknowns.  Nodes are x_i = i h, i = 0..n+1.  A Dirichlet face's nodes are known
  * (zero) and carry no unknown; a Neumann or Sommerfeld-like face's nodes are unknowns, so
  * an axis has n + (number of its non-Dirichlet faces) unknowns (Section 3.3, N_z chosen so
- * that h is equal in all directions).  Sommerfeld-like faces are accepted on z only (the
- * preconditioner of Section 3.3 diagonalises x and y).
+ * that h is equal in all directions).  Sommerfeld-like faces are accepted on one axis pair
+ * (the preconditioner of Section 3.3 diagonalises the other two axes).  The paper writes
+ * them on z; a pair on x or y is solved as the z pair of the problem with that axis
+ * exchanged with z (the scheme is symmetric under exchanging axes), invisibly to the caller:
+ * arrays keep the caller's layout.  Two axes with such faces are not supported.
  *
  * Data at the boundary.  Every vector argument is a DEVICE pointer to complex128
  * (interleaved re, im doubles), x fastest: element (i, j, l) at index (l*my + j)*mx + i
@@ -133,8 +136,8 @@ void helm6_opts_default(helm6_opts* opts);
  * the unit cube, h = 1/(n+1)), wavenumber k and faces[6] = {x0, x1, y0, y1, z0, z1} of
  * helm6_bc.  Builds the 1D eigenbases (closed forms, FP64 host arithmetic), uploads them
  * and allocates the workspace.  opts may be NULL (defaults).  *out is set only on success.
- * Errors: INVALID (n out of range, Sommerfeld-like face on x or y, bad option values),
- * NOMEM, CUDA. */
+ * Errors: INVALID (n out of range, Sommerfeld-like faces on more than one axis pair, bad
+ * option values), NOMEM, CUDA. */
 int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[6],
                  const helm6_opts* opts);
 
@@ -243,8 +246,9 @@ int helm6_profile_read(helm6_ctx* ctx, helm6_profile* out);
  * overlap on the GPU (several streams, or several host threads on one device) race on it
  * and must be serialised by the caller.
  *
- * n, h, k, faces: as helm6_create.  F, u, r: DEVICE complex128 arrays (layout as above),
- * r must not overlap u.  sumsq: DEVICE pointer to one double.  stream: cudaStream_t or
+ * n, h, k, faces: as helm6_create, except that Sommerfeld-like faces are accepted on z only
+ * here (INVALID otherwise).  F, u, r: DEVICE complex128 arrays (layout as above), r must not
+ * overlap u.  sumsq: DEVICE pointer to one double.  stream: cudaStream_t or
  * NULL.  Work is enqueued on the stream; the call returns without synchronising.
  * Returns OK, INVALID (arguments, or grid too large), UNSUPPORTED (device ordinal >= 64)
  * or CUDA. */

@@ -23,7 +23,9 @@
 using namespace helm6;
 
 struct helm6_ctx {
-  Geom g;
+  Geom g;        // internal geometry: Sommerfeld-like faces, if any, on z
+  Geom gu;       // the caller's geometry (its array layout and faces)
+  int xaxis = -1;  // the caller's axis (0 = x, 1 = y) carrying Sommerfeld-like faces, exchanged with z
   int n = 0;
   double h = 0;
   cd k;
@@ -821,8 +823,23 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   if (!out || !faces || n < 1 || n > 4094) return HELM6_ERR_INVALID;
   for (int i = 0; i < 6; ++i)
     if (!valid_face(faces[i])) return HELM6_ERR_INVALID;
-  for (int i = 0; i < 4; ++i)
-    if (faces[i] == HELM6_SOMMERFELD) return HELM6_ERR_INVALID;
+  // Sommerfeld-like faces on one axis pair at most.  The face rows of Eq. 3DDISCS are
+  // written for z and the scheme is symmetric under exchanging axes, so an x or y pair is
+  // solved as the z pair of the problem with that axis exchanged with z: the internal
+  // geometry carries it on z, and only the conversions at the boundary see the exchange.
+  int s_axes = 0, xaxis = -1;
+  for (int a = 0; a < 3; ++a)
+    if (faces[2 * a] == HELM6_SOMMERFELD || faces[2 * a + 1] == HELM6_SOMMERFELD) {
+      ++s_axes;
+      if (a < 2) xaxis = a;
+    }
+  if (s_axes > 1) return HELM6_ERR_INVALID;
+  int fint[6];
+  for (int i = 0; i < 6; ++i) fint[i] = faces[i];
+  if (xaxis >= 0) {
+    std::swap(fint[2 * xaxis], fint[4]);
+    std::swap(fint[2 * xaxis + 1], fint[5]);
+  }
   helm6_opts o;
   helm6_opts_default(&o);
   if (opts) o = *opts;
@@ -856,12 +873,17 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   c->opts = o;
   c->stream = (cudaStream_t)o.stream;
   c->mrest = o.max_restart;
-  for (int i = 0; i < 6; ++i) c->g.face[i] = faces[i];
-  auto cnt = [&](int a) { return n + (faces[2 * a] != HELM6_DIRICHLET) + (faces[2 * a + 1] != HELM6_DIRICHLET); };
-  c->g.mx = cnt(0);
-  c->g.my = cnt(1);
-  c->g.mz = cnt(2);
-  c->g.N = (int64_t)c->g.mx * c->g.my * c->g.mz;
+  auto geom = [&](const int* f, Geom& g) {
+    for (int i = 0; i < 6; ++i) g.face[i] = f[i];
+    auto cnt = [&](int a) { return n + (f[2 * a] != HELM6_DIRICHLET) + (f[2 * a + 1] != HELM6_DIRICHLET); };
+    g.mx = cnt(0);
+    g.my = cnt(1);
+    g.mz = cnt(2);
+    g.N = (int64_t)g.mx * g.my * g.mz;
+  };
+  geom(fint, c->g);
+  geom(faces, c->gu);
+  c->xaxis = xaxis;
   stencil_coefficients(c->k, c->h, c->coef);
   const cd I(0.0, 1.0);
   c->diag0 = to_pod(-2.0 + c->k * c->k * c->h * c->h);
@@ -881,8 +903,8 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     return fail(HELM6_ERR_CUDA);
   // bases
   std::vector<double> Vx, Wx, lx, Vy, Wy, ly;
-  basis(n, faces[0], faces[1], Vx, Wx, lx);
-  basis(n, faces[2], faces[3], Vy, Wy, ly);
+  basis(n, c->g.face[0], c->g.face[1], Vx, Wx, lx);  // the internal x and y faces
+  basis(n, c->g.face[2], c->g.face[3], Vy, Wy, ly);
   const size_t mx2 = (size_t)c->g.mx * c->g.mx, my2 = (size_t)c->g.my * c->g.my;
   if ((rc = dalloc(c, &c->Vx64, mx2)) || (rc = dalloc(c, &c->Wx64, mx2)) || (rc = dalloc(c, &c->Vy64, my2)) ||
       (rc = dalloc(c, &c->Wy64, my2)) || (rc = dalloc(c, &c->Vx32, mx2)) || (rc = dalloc(c, &c->Wx32, mx2)) ||
@@ -1001,9 +1023,9 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
 
 int helm6_dims(const helm6_ctx* c, int64_t dims[3]) {
   if (!c || !dims) return HELM6_ERR_INVALID;
-  dims[0] = c->g.mx;
-  dims[1] = c->g.my;
-  dims[2] = c->g.mz;
+  dims[0] = c->gu.mx;
+  dims[1] = c->gu.my;
+  dims[2] = c->gu.mz;
   return HELM6_OK;
 }
 
@@ -1017,7 +1039,7 @@ int helm6_apply_A(helm6_ctx* c, const void* x, void* y) {
   if (!c || !x || !y) return HELM6_ERR_INVALID;
   cudaStream_t s = c->stream;
   const int64_t N = c->g.N;
-  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  launch_caller_to_planar(c->g, c->xaxis, (const double*)x, c->R64, s);
   if (c->opts.precision == HELM6_FP64) {
     launch_stencil<double>(c->g, c->coef, c->R64, c->E64, nullptr, nullptr, 0, nullptr, nullptr, s);
   } else {
@@ -1025,7 +1047,7 @@ int helm6_apply_A(helm6_ctx* c, const void* x, void* y) {
     launch_stencil<float>(c->g, c->coef, c->w32, c->zt32, nullptr, nullptr, 0, nullptr, nullptr, s);
     launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
   }
-  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  launch_planar_to_caller(c->g, c->xaxis, c->E64, (double*)y, s);
   CK(cudaGetLastError());
   return HELM6_OK;
 }
@@ -1036,7 +1058,7 @@ int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
   const int64_t N = c->g.N;
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
-  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  launch_caller_to_planar(c->g, c->xaxis, (const double*)x, c->R64, s);
   if (c->opts.precision == HELM6_FP64) {
     precond64(c, c->R64, c->E64);
   } else {
@@ -1044,7 +1066,7 @@ int helm6_apply_Pinv(helm6_ctx* c, const void* x, void* y) {
     precond32(c, c->w32, c->zt32);
     launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
   }
-  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  launch_planar_to_caller(c->g, c->xaxis, c->E64, (double*)y, s);
   CK(cudaGetLastError());
   const int st = check_status(c);
   return (st == HELM6_BREAKDOWN || st < 0) ? st : HELM6_OK;
@@ -1088,11 +1110,11 @@ int helm6_apply_stage2(helm6_ctx* c, const void* x, void* y) {
   const int64_t N = c->g.N;
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
-  launch_interleaved_to_planar((const double*)x, c->R64, N, s);
+  launch_caller_to_planar(c->g, c->xaxis, (const double*)x, c->R64, s);
   launch_convert<double, float>(c->R64, c->w32, N, 1.0, s);
   precond_cnn32(c, c->w32, c->zt32);
   launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
-  launch_planar_to_interleaved(c->E64, (double*)y, N, s);
+  launch_planar_to_caller(c->g, c->xaxis, c->E64, (double*)y, s);
   CK(cudaGetLastError());
   const int st = check_status(c);
   return (st == HELM6_BREAKDOWN || st < 0) ? st : HELM6_OK;
@@ -1110,7 +1132,7 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
   const int64_t N = c->g.N;
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
-  launch_interleaved_to_planar((const double*)F, c->F64, N, s);
+  launch_caller_to_planar(c->g, c->xaxis, (const double*)F, c->F64, s);
   double normF = 0;
   int rc = norm2<double>(c, c->F64, &normF);
   if (rc) return rc;
@@ -1122,7 +1144,7 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
     CK(cudaStreamSynchronize(s));
     status = HELM6_OK;
   } else {
-    launch_interleaved_to_planar((const double*)u, c->U64, N, s);
+    launch_caller_to_planar(c->g, c->xaxis, (const double*)u, c->U64, s);
     if (c->opts.method == HELM6_SKS)
       status = solve_sks(c, normF, tol, maxit, S);
     else if (c->opts.method == HELM6_CHEB)
@@ -1132,7 +1154,7 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
     else
       status = solve_mixed(c, normF, tol, restart, maxit, S);
     if (status < 0) return status;
-    launch_planar_to_interleaved(c->U64, (double*)u, N, s);
+    launch_planar_to_caller(c->g, c->xaxis, c->U64, (double*)u, s);
     S->relres = c->last_beta / normF;
   }
   CK(cudaStreamSynchronize(s));
@@ -1208,14 +1230,14 @@ int helm6_rhs_gaussians(helm6_ctx* c, int nsrc, const double* centers, const hel
                         const void* noise, void* F) {
   if (!c || !F || nsrc < 0 || nsrc > 4096 || !(sigma > 0)) return HELM6_ERR_INVALID;
   if (nsrc > 0 && (!centers || !amps)) return HELM6_ERR_INVALID;
-  return rhs_gaussians(c->g, c->h, c->k, nsrc, centers, (const double*)amps, sigma, (const double*)noise,
+  return rhs_gaussians(c->gu, c->h, c->k, nsrc, centers, (const double*)amps, sigma, (const double*)noise,
                        (double*)F, c->stream);
 }
 
 int helm6_rhs_separable(helm6_ctx* c, int nterms, const helm6_c64* coef, const helm6_c64* tables, void* F) {
   if (!c || !F || nterms < 0 || nterms > 4096) return HELM6_ERR_INVALID;
   if (nterms > 0 && (!coef || !tables)) return HELM6_ERR_INVALID;
-  return rhs_separable(c->g, c->h, c->k, nterms, (const double*)coef, (const double*)tables, (double*)F, c->stream);
+  return rhs_separable(c->gu, c->h, c->k, nterms, (const double*)coef, (const double*)tables, (double*)F, c->stream);
 }
 
 }  // extern "C"

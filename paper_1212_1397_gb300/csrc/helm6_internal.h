@@ -153,6 +153,11 @@ template <typename TI, typename TO>
 void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s);  // planar
 void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cudaStream_t s);
 void launch_planar_to_interleaved(const double* in, double* zout, int64_t N, cudaStream_t s);
+// The same between the caller's interleaved array and the internal planar layout of
+// geometry g when the caller's axis xaxis (0 = x, 1 = y) is the internal z axis (Sommerfeld-
+// like faces on that axis); xaxis < 0: no exchange.
+void launch_caller_to_planar(const Geom& g, int xaxis, const double* zin, double* out, cudaStream_t s);
+void launch_planar_to_caller(const Geom& g, int xaxis, const double* in, double* zout, cudaStream_t s);
 void launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t s);  // one double
 
 // Givens update of Hessenberg column j on the device (single thread, FP64):

@@ -169,6 +169,31 @@ __global__ void planar_to_inter_kernel(const double* __restrict__ in, double2* _
     z[idx] = make_double2(in[idx], in[N + idx]);
 }
 
+// Index in the caller's array of the internal point idx when the caller's axis xaxis
+// (0 = x, 1 = y) is the internal z axis (and the internal z axis is the caller's xaxis):
+// internal (i, j, l) is the caller's (l, j, i) for xaxis 0 and (i, l, j) for xaxis 1.
+__device__ __forceinline__ int64_t caller_index(int64_t idx, int mx, int my, int mz, int xaxis) {
+  const int64_t i = idx % mx, j = (idx / mx) % my, l = idx / ((int64_t)mx * my);
+  return xaxis == 0 ? (i * my + j) * mz + l : (j * mz + l) * mx + i;
+}
+
+__global__ void inter_to_planar_x_kernel(const double2* __restrict__ z, double* __restrict__ out, int mx, int my,
+                                         int mz, int xaxis) {
+  const int64_t N = (int64_t)mx * my * mz, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride) {
+    const double2 v = z[caller_index(idx, mx, my, mz, xaxis)];
+    out[idx] = v.x;
+    out[N + idx] = v.y;
+  }
+}
+
+__global__ void planar_to_inter_x_kernel(const double* __restrict__ in, double2* __restrict__ z, int mx, int my,
+                                         int mz, int xaxis) {
+  const int64_t N = (int64_t)mx * my * mz, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += stride)
+    z[caller_index(idx, mx, my, mz, xaxis)] = make_double2(in[idx], in[N + idx]);
+}
+
 __global__ void reduce_sum_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
   __shared__ double sh[RB / 32];
   double v = 0.0;
@@ -830,6 +855,24 @@ void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cud
 void launch_planar_to_interleaved(const double* in, double* zout, int64_t N, cudaStream_t s) {
   note_launch();
   planar_to_inter_kernel<<<grid_for(N, RB), RB, 0, s>>>(in, (double2*)zout, N);
+}
+
+void launch_caller_to_planar(const Geom& g, int xaxis, const double* zin, double* out, cudaStream_t s) {
+  if (xaxis < 0) {
+    launch_interleaved_to_planar(zin, out, g.N, s);
+    return;
+  }
+  note_launch();
+  inter_to_planar_x_kernel<<<grid_for(g.N, RB), RB, 0, s>>>((const double2*)zin, out, g.mx, g.my, g.mz, xaxis);
+}
+
+void launch_planar_to_caller(const Geom& g, int xaxis, const double* in, double* zout, cudaStream_t s) {
+  if (xaxis < 0) {
+    launch_planar_to_interleaved(in, zout, g.N, s);
+    return;
+  }
+  note_launch();
+  planar_to_inter_x_kernel<<<grid_for(g.N, RB), RB, 0, s>>>(in, (double2*)zout, g.mx, g.my, g.mz, xaxis);
 }
 
 void launch_reduce_sum(const double* partial, int n, double* out, cudaStream_t s) {

@@ -66,7 +66,9 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib_path):
     lib = H.load(lib_path)
     ctx = ctypes.c_void_p()
     k = H.C64(5.0, 0.0)
-    faces_bad = (ctypes.c_int * 6)(2, 0, 0, 0, 0, 0)        # Sommerfeld-like on x
+    faces_bad = (ctypes.c_int * 6)(2, 0, 0, 0, 0, 2)        # Sommerfeld-like on two axis pairs
+    assert lib.helm6_create(ctypes.byref(ctx), 8, 0.0, k, faces_bad, None) == -1
+    faces_bad = (ctypes.c_int * 6)(0, 0, 2, 2, 2, 0)
     assert lib.helm6_create(ctypes.byref(ctx), 8, 0.0, k, faces_bad, None) == -1
     faces = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
     assert lib.helm6_create(ctypes.byref(ctx), 0, 0.0, k, faces, None) == -1

@@ -181,7 +181,7 @@ def test_edge_cases(H):
         with pytest.raises(H.Helm6Error):
             s.solve(F, tol=1e-8, restart=100)       # restart above max_restart
     with pytest.raises(H.Helm6Error):
-        H.Solver(8, 3.0, "SDDDDD")
+        H.Solver(8, 3.0, "SDDDDS")  # Sommerfeld-like faces on two axis pairs
 
 
 def test_initial_guess_is_used(H):
