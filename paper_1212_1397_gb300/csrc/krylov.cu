@@ -205,7 +205,7 @@ __global__ void reduce_sum_kernel(const double* __restrict__ partial, int n, dou
 // ---- Arnoldi with delayed classical Gram-Schmidt (one reduction + one update per step) ----
 // Vector traits for 2-point loads of a planar field.
 
-constexpr int CHD = 8;  // basis vectors per chunk of the reduction pass (each chunk re-reads u and w)
+constexpr int CHD = 8;  // most basis vectors per warp group of the reduction pass (4 accumulators each)
 
 // P consecutive values of one plane, starting at point q * P, widened to the arithmetic
 // type T.  S is the storage type: T itself (P = 1, 2, or 4 for float) or __half (P = 1, 2
