@@ -59,3 +59,13 @@ def test_two_gloo_ranks(tmp_path):
     assert res[1]["printed"] == ""
     line = json.loads(res[0]["printed"])
     assert line["impl"] == "reference" and line["value"] == 123.0 and line["n_gpus"] == 2
+
+
+def test_metric_names_the_workload():
+    """The headline workload keeps its metric string; the others name their own size,
+    wavenumber, faces and tolerance."""
+    import bench
+    assert bench.metric_for(bench.WORKLOAD) == bench.METRIC
+    m = bench.metric_for("mixed_n256_k80c")
+    assert "256^3" in m and "k=80+0.8i" in m and "DDNNSS" in m and "1e-8" in m
+    assert "1e-10" in bench.metric_for("dirichlet_n32_k10")
