@@ -2,19 +2,22 @@
 """Time-to-solution of the sixth-order compact Helmholtz solve on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --ops R            # operator and preconditioner only (kernel profiling)
+    python bench.py --oracle-full      # the oracle's complete FP64 GMRES(30) solve, timed once
 
 A step is one complete solve of the large mixed-face problem: n = 256 interior points per
 side (256 x 258 x 258 = 17,040,384 complex unknowns), k = 80, Dirichlet x faces, Neumann y
 faces, Sommerfeld-like z faces, right side the compact assembly of 8 Gaussian sources with
 unit-modulus random phases, solved from u = 0 to ||F - A u|| / ||F|| <= 1e-8 (FP64 true
-residual) by FP64 refinement around FP32 FGMRES(30) with BF16-split tensor-core / FP32
+residual) by FP64 refinement around FP32 FGMRES(30) with BF16-split tensor-core
 transforms.  `value` is the device time per solve with F resident in HBM; `e2e` adds the
 host->device copy of F and the device->host copy of u (pinned buffers) to every step.
-The per-phase times, the roofline of the dominant kernel and the launch count come from a
-repeat of the timed solves with the library's phase events on (the events stay out of the
-timed region: recording them serialises the transform's side stream).
-The plain FP64 GMRES(30) solve of the same problem is timed beside it, and the CPU oracle
-on a bounded sample gives `cpu_baseline`.
+The per-phase times, the roofline of the kernel with the most device time and the launch
+count come from a repeat of the timed solves with the library's phase events on.
+Beside it: the same solve with an FP32 Krylov basis, with the learned second stage (AUTO),
+the plain FP64 GMRES(30) solve, GMRES(20) against the stationary SKS iteration on the
+128 x 130 x 130, k = 40 mixed workload, the 64-problem batched workload, and the CPU
+oracle's time-to-solution from a bounded sample of its own functions at the full size.
 
 With N > 1 (torchrun) every rank solves its own replica (independent right sides, no
 collective on the data path); the timed region is bracketed by barriers and the slowest
@@ -51,28 +54,30 @@ def metric_for(workload):
     tol = f"{cfg['tol']:.0e}".replace("e-0", "e-")
     return (f"time to rel-res {tol} at {cfg['n']}^3 k={kk} faces {cfg['faces']} "
             "(mixed FP32/BF16 + FP64 refinement)")
-# FP64 GMRES(30) iterations of this workload to 1e-8 (plain GPU path; the oracle runs the
-# same algorithm), used to scale the oracle's per-iteration sample to a time-to-solution.
-FP64_ITERS_NOMINAL = 175
+# The oracle's complete FP64 GMRES(30) solve of a workload from u = 0 to its tolerance,
+# measured once on the GPU machine's host cores by `bench.py --oracle-full` (seconds, iterations,
+# cycles, threads).  The iteration and cycle counts size the bounded sample's projection.
+ORACLE_FULL = {
+    "mixed_n256_k80": None,
+}
 
-# Library phases that are one kernel each (the roofline is reported for the slowest).
+# Library phases and the kernel each one launches (the four transform phases are one kernel).
 KERNEL_OF = {
-    "stencil": "stencil_kernel<float,0>",
-    "xform_x_fwd": "xform_tc_kernel (x forward)",
-    "xform_y_fwd": "xform_tc_kernel (y forward)",
+    "stencil": "stencil4_kernel",
+    "xform_x_fwd": "xform_tc_kernel",
+    "xform_y_fwd": "xform_tc_kernel",
     "ztri": "ztri_apply_kernel<float>",
-    "xform_y_inv": "xform_tc_kernel (y inverse)",
-    "xform_x_inv": "xform_tc_kernel (x inverse)",
+    "xform_y_inv": "xform_tc_kernel",
+    "xform_x_inv": "xform_tc_kernel",
     "gs_dot": "dcgs_dot_kernel<float,{p},{tv}>",
     "gs_update": "dcgs_update_kernel<float,{p},{tv}>",
     "resid64": "stencil_kernel<double,1>",
 }
 
-# ncu DRAM bytes (read + write) per launch of a kernel over that launch's algorithmic bytes,
-# from the capture at the bench size summarised in profiles/dram_dcgs_dot_f16_n256.md
-# (bytes-weighted over launches with 0-4 and 28-30 basis vectors; absent: not captured since
-# the kernel last changed).
-NCU_TRAFFIC_RATIO = {"dcgs_dot_kernel<float,4,__half>": 1.045}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch and unknown of a
+# kernel, from a capture of the kernel as it is now built (a kernel absent here was changed
+# since its last capture: traffic null).
+NCU_DRAM_BYTES_PER_UNKNOWN = {}
 
 
 def peaks():
@@ -137,22 +142,53 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def oracle_sample(cfg, iters_scale):
-    """CPU oracle on a bounded sample: preconditioner set-up plus one preconditioned matvec
-    (A_p^{-1} then A, the work of one GMRES iteration) at the full size, scaled to a
-    time-to-solution by the FP64 GMRES iteration count."""
+def oracle_problem(cfg, seed):
     import oracle as O
     prob = O.Problem(cfg["n"], cfg["k"], cfg["faces"])
-    x = inputs.complex_normal(12345, prob.shape)
+    return O, prob, inputs.complex_normal(seed, prob.shape)
+
+
+def oracle_unit_costs(O, prob, x):
+    """Seconds of the oracle's own work units at the full size on the host cores: the
+    preconditioner's set-up, one application of A_p^-1 and of A, and one modified
+    Gram-Schmidt projection as its GMRES does it (a dot product with one basis vector and
+    the update of w against it)."""
     t0 = time.perf_counter()
     M = O.Preconditioner(prob)
     t1 = time.perf_counter()
-    y = O.apply_A(prob, M(x))
+    z = M(x)
     t2 = time.perf_counter()
-    del y
-    per_iter = t2 - t1
-    est_ms = 1e3 * ((t1 - t0) + per_iter * iters_scale)
-    return est_ms, per_iter
+    w = O.apply_A(prob, z)
+    t3 = time.perf_counter()
+    hij = O._dot(x, w)
+    w = w - hij * x
+    t4 = time.perf_counter()
+    del z, w
+    return dict(setup=t1 - t0, precond=t2 - t1, apply_A=t3 - t2, proj=t4 - t3)
+
+
+def oracle_projection(u, iters, restart):
+    """Time-to-solution of the oracle's restarted GMRES(restart) taking `iters` iterations
+    (cycles of `restart` columns, the last one shorter), from its unit costs: set-up, the
+    initial residual, per iteration one A_p^-1 and one A plus j + 1 projections at column j,
+    per cycle the combination V y (one projection per column), A_p^-1 of it and the true
+    residual."""
+    cycles = max(1, -(-iters // restart))
+    lens = [restart] * (cycles - 1) + [iters - restart * (cycles - 1)]
+    proj = sum(L * (L + 1) // 2 + L for L in lens)
+    s = (u["setup"] + u["apply_A"] + iters * (u["precond"] + u["apply_A"])
+         + cycles * (u["precond"] + u["apply_A"]) + proj * u["proj"])
+    return 1e3 * s, cycles
+
+
+def oracle_counts(workload, fallback_iters=None):
+    """(iterations, source) of the oracle's complete solve of this workload."""
+    full = ORACLE_FULL.get(workload)
+    if full:
+        return full["iters"], "the oracle's complete solve of this workload (bench.py --oracle-full)"
+    if fallback_iters:
+        return fallback_iters, "the GPU's FP64 GMRES(30) iteration count of this run (oracle not run in full)"
+    return None, None
 
 
 def cpu_cores():
@@ -190,26 +226,91 @@ def reduce_max(x, dist):
 
 
 def run_reference(args, cfg, rank, world):
-    """--impl reference: the CPU oracle timed on the host cores (rank 0 only)."""
+    """--impl reference: the CPU oracle timed on the host cores (rank 0 only).  Each step
+    times a bounded sample of the oracle's own functions at the full size (set-up, one
+    A_p^-1, one A, one Gram-Schmidt projection); the value is the time-to-solution those
+    unit costs give for the iterations of the oracle's complete solve."""
     if rank != 0:
         return
+    O, prob, x = oracle_problem(cfg, 12345)
     for _ in range(args.warmup):
-        oracle_sample(cfg, FP64_ITERS_NOMINAL)
-    vals = []
+        oracle_unit_costs(O, prob, x)
+    iters, src = oracle_counts(args.workload)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no complete oracle solve recorded for "
+                          f"{args.workload} (bench.py --oracle-full)"}), flush=True)
+        return
+    step_s, vals = [], []
     for _ in range(args.steps):
-        ms, per_iter = oracle_sample(cfg, FP64_ITERS_NOMINAL)
-        vals.append(ms)
+        t0 = time.perf_counter()
+        u = oracle_unit_costs(O, prob, x)
+        step_s.append(time.perf_counter() - t0)
+        vals.append(oracle_projection(u, iters, cfg["restart"])[0])
     v = float(np.mean(vals))
-    sample = (f"oracle (numpy/LAPACK FP64) at the full 256^3 size: preconditioner set-up + one "
-              f"A(A_p^-1 x) per step ({per_iter:.2f} s), scaled by {FP64_ITERS_NOMINAL} GMRES iterations")
+    step_ms = 1e3 * float(np.mean(step_s))
+    sample = (f"oracle (numpy/LAPACK FP64) at the full {cfg['n']}^3 size, per step: preconditioner set-up, one "
+              f"A_p^-1, one A and one Gram-Schmidt projection ({step_ms / 1e3:.2f} s); value = those unit costs "
+              f"x the work of GMRES({cfg['restart']}) in {iters} iterations ({src})")
     line = {"impl": "reference", "metric": metric_for(args.workload), "value": v, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": cfg["n"], "k": str(cfg["k"]), "faces": cfg["faces"]},
             "cpu_baseline": {"kind": "oracle", "cores": cpu_cores(), "sample": sample, "value": v,
                              "unit": "ms"},
-            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "oracle_full": ORACLE_FULL.get(args.workload)}
     print(json.dumps(line), flush=True)
+
+
+def run_oracle_full(args, cfg):
+    """--oracle-full: the oracle's complete FP64 GMRES solve of the workload from u = 0 to
+    its tolerance, on the host cores, timed once (minutes at 256^3)."""
+    import oracle as O
+    n, k, faces = cfg["n"], cfg["k"], cfg["faces"]
+    prob = O.Problem(n, k, faces)
+    src = inputs.gaussian_sources(replica_seeds(0)[0], n, cfg.get("nsrc", 8))
+    noise = None
+    if cfg.get("noise", 0.0) > 0:
+        noise = cfg["noise"] * inputs.complex_normal(replica_seeds(0)[1], prob.shape)
+    F = O.rhs(prob, O.sources.gaussians(src), noise=noise)
+    t0 = time.perf_counter()
+    M = O.Preconditioner(prob)
+    U, info = O.gmres(lambda v: O.apply_A(prob, v), M, F, tol=cfg["tol"], restart=cfg["restart"],
+                      maxit=args.oracle_maxit)
+    t1 = time.perf_counter()
+    u = oracle_unit_costs(O, prob, inputs.complex_normal(12345, prob.shape))
+    proj, cycles = oracle_projection(u, info["iters"], cfg["restart"])
+    print(json.dumps({"oracle_full": {"workload": args.workload, "seconds": t1 - t0, "iters": info["iters"],
+                                      "cycles": cycles, "relres": info["relres"], "converged": info["converged"],
+                                      "cores": cpu_cores(), "unit_costs_s": u,
+                                      "projection_from_unit_costs_s": proj / 1e3}}), flush=True)
+
+
+def run_ops(args, cfg):
+    """--ops R: R applications each of the operator and of the preconditioner at the
+    workload's size (mixed precision), device-timed per application; for kernel profiling."""
+    import torch
+    from paper_1212_1397_gb300 import build
+    from paper_1212_1397_gb300 import helm6 as H
+    build.build()
+    H.load()
+    torch.cuda.set_device(0)
+    with H.Solver(cfg["n"], cfg["k"], cfg["faces"], precision=H.MIXED, method=H.SKS) as s:
+        x = torch.from_numpy(inputs.complex_normal(5, s.shape)).cuda()
+        y, z = s.apply_A(x), s.apply_Pinv(x)
+        torch.cuda.synchronize()
+        out = {}
+        for name, fn in (("apply_A", lambda: s.apply_A(x, y)), ("apply_Pinv", lambda: s.apply_Pinv(x, z))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.ops):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out[name + "_ms"] = e0.elapsed_time(e1) / args.ops
+        out.update(workload=args.workload, dims=list(s.dims), reps=args.ops,
+                   max_abs_Ax=float(y.abs().max()), max_abs_Pinv_x=float(z.abs().max()))
+    print(json.dumps({"ops": out}), flush=True)
 
 
 def main():
@@ -225,8 +326,19 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batched workload")
     ap.add_argument("--basis", default="auto", choices=["auto", "f32", "f16"],
                     help="storage of the inner solve's Krylov basis (auto: the library default)")
+    ap.add_argument("--no-f32", action="store_true", help="skip the FP32-basis solve")
+    ap.add_argument("--no-sks", action="store_true", help="skip the GMRES(20) vs SKS comparison")
+    ap.add_argument("--ops", type=int, default=0, help="only apply A and A_p^-1 this many times each")
+    ap.add_argument("--oracle-full", action="store_true", help="only the oracle's complete solve, timed once")
+    ap.add_argument("--oracle-maxit", type=int, default=2000)
     args = ap.parse_args()
     cfg = dict(inputs.WORKLOADS[args.workload])
+    if args.oracle_full:
+        run_oracle_full(args, cfg)
+        return
+    if args.ops > 0:
+        run_ops(args, cfg)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -343,6 +455,46 @@ def main():
                        "mode": "auto", "weights": os.path.basename(wfile)}
             solver.set_cnn(w["theta"], 1.0, H.CNN_OFF)
 
+    def timed_solve(slv, FF, uu, tol_, restart_, maxit_):
+        slv.solve(FF, uu.zero_(), tol=tol_, restart=restart_, maxit=maxit_)  # warm-up
+        uu.zero_()
+        sync_all(dist)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st_ = slv.solve(FF, uu, tol=tol_, restart=restart_, maxit=maxit_)
+        b.record(stream)
+        sync_all(dist)
+        return reduce_max(a.elapsed_time(b), dist), st_
+
+    # ---- the same mixed solve with the Krylov basis in FP32 ----
+    f32leg = None
+    if not args.no_f32 and solver.basis == H.BASIS_F16:
+        with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=restart, stream=stream,
+                      basis=H.BASIS_F32) as s32:
+            u32 = s32.empty()
+            ms32, st32 = timed_solve(s32, F, u32, tol, restart, 1000)
+            f32leg = {"ms": ms32, "iters": st32["iters"], "outer": st32["outer"], "relres": st32["relres"],
+                      "status": st32["status"], "basis": "f32"}
+            del u32
+
+    # ---- GMRES(20) against the stationary SKS iteration (Algorithm 1), mixed workload 128^3 ----
+    sks_leg = None
+    if not args.no_sks:
+        c2 = inputs.WORKLOADS["mixed_n128_k40"]
+        src2 = inputs.gaussian_sources(src_seed, c2["n"], c2["nsrc"])
+        sks_leg = {"workload": "mixed_n128_k40", "n": c2["n"], "k": str(c2["k"]), "faces": c2["faces"],
+                   "tol": c2["tol"]}
+        for name, meth, maxit in (("gmres20", H.FGMRES, 3000), ("sks", H.SKS, 3000)):
+            with H.Solver(c2["n"], c2["k"], c2["faces"], precision=H.MIXED, method=meth, max_restart=c2["restart"],
+                          stream=stream) as s2:
+                eta = torch.from_numpy(c2["noise"] * inputs.complex_normal(noise_seed, s2.shape)).cuda()
+                F2 = s2.rhs_gaussians(src2, noise=eta)
+                u2 = s2.empty()
+                ms2, st2 = timed_solve(s2, F2, u2, c2["tol"], c2["restart"], maxit)
+                sks_leg[name] = {"ms": ms2, "iters": st2["iters"], "outer": st2["outer"],
+                                 "relres": st2["relres"], "status": st2["status"]}
+                del F2, u2, eta
+
     # ---- plain FP64 GMRES(30) of the same problem ----
     plain = None
     if not args.no_plain:
@@ -386,39 +538,56 @@ def main():
         finally:
             B.close_batch(items)
 
-    # ---- roofline of the dominant kernel (live per-phase events) ----
+    # ---- roofline of the kernel with the most device time (live per-phase events) ----
     hbm, bf16, peak_src = peaks()
     phases = prof["phases"]
     f16 = solver.basis == H.BASIS_F16
     kernel_of = {ph: name.format(p=4 if f16 and N % 4 == 0 else 2, tv="__half" if f16 else "float")
                  for ph, name in KERNEL_OF.items()}
     single = [p for p in phases if p in kernel_of and phases[p]["count"] > 0]
-    dom = max(single, key=lambda p: phases[p]["ms"])
-    cnt = max(phases[dom]["count"], 1)
-    per_launch_ms = phases[dom]["ms"] / cnt
-    alg_bytes = phases[dom]["bytes"] / cnt        # algorithmic bytes per launch (mean)
-    achieved = phases[dom]["bytes"] / (phases[dom]["ms"] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": kernel_of[dom], "phase": dom, "achieved": achieved, "peak": hbm,
+    per_kernel = {}
+    for p in single:
+        kk_ = per_kernel.setdefault(kernel_of[p], {"ms": 0.0, "bytes": 0.0, "launches": 0, "phases": []})
+        kk_["ms"] += phases[p]["ms"]
+        kk_["bytes"] += phases[p]["bytes"]
+        kk_["launches"] += phases[p]["count"]
+        kk_["phases"].append(p)
+    dom = max(per_kernel, key=lambda kn: per_kernel[kn]["ms"])
+    dk = per_kernel[dom]
+    per_launch_ms = dk["ms"] / max(dk["launches"], 1)
+    alg_bytes = dk["bytes"] / max(dk["launches"], 1)   # algorithmic bytes per launch (mean)
+    achieved = dk["bytes"] / (dk["ms"] * 1e-3) / 1e9
+    tpu = NCU_DRAM_BYTES_PER_UNKNOWN.get(dom)
+    roof = {"bound": "hbm", "kernel": dom, "phases": dk["phases"], "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": (NCU_TRAFFIC_RATIO[kernel_of[dom]] * alg_bytes if kernel_of[dom] in NCU_TRAFFIC_RATIO
-                        else None),
-            "traffic_source": ("ncu dram bytes at the bench size (profiles/dram_dcgs_dot_f16_n256.md): "
-                               "traffic / algorithmic bytes of the captured launches x this run's mean "
-                               "algorithmic bytes per launch" if kernel_of[dom] in NCU_TRAFFIC_RATIO else None),
+            "traffic": tpu * N if tpu else None,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of this kernel "
+                               "as built now, per unknown, times this workload's unknowns") if tpu else None,
             "per_launch_ms": per_launch_ms,
             "alg_bytes_per_launch": alg_bytes,
+            "launches_per_step": dk["launches"] / args.steps,
+            "kernel_ms_per_step": {kn: v["ms"] / args.steps for kn, v in per_kernel.items()},
             "phase_frac": {p: (phases[p]["bytes"] / (phases[p]["ms"] * 1e-3) / 1e9) / hbm
                            for p in single}}
 
-    # ---- CPU oracle baseline (rank 0, N = 1) ----
+    # ---- CPU oracle baseline (rank 0, N = 1): bounded sample of its own functions ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters = plain["iters"] if plain else FP64_ITERS_NOMINAL
-        est, per_iter = oracle_sample(cfg, iters)
-        cpu = {"value": est, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"oracle (numpy/LAPACK FP64) preconditioner set-up + one A(A_p^-1 x) at "
-                         f"the full size ({per_iter:.2f} s), scaled by the {iters} FP64 GMRES "
-                         f"iterations this workload takes"}
+        iters, isrc = oracle_counts(args.workload, plain["iters"] if plain else None)
+        if iters is not None:
+            O, oprob, ox = oracle_problem(cfg, 12345)
+            reps = 3
+            t0 = time.perf_counter()
+            us = [oracle_unit_costs(O, oprob, ox) for _ in range(reps)]
+            samp_s = time.perf_counter() - t0
+            u_med = {key: float(np.median([u_[key] for u_ in us])) for key in us[0]}
+            est, cyc = oracle_projection(u_med, iters, restart)
+            cpu = {"value": est, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": (f"oracle (numpy/LAPACK FP64) at the full size, {reps} x (set-up, one A_p^-1, one A, "
+                              f"one Gram-Schmidt projection), {samp_s:.1f} s; value = median unit costs x the work "
+                              f"of GMRES({restart}) in {iters} iterations, {cyc} cycles ({isrc})"),
+                   "unit_costs_s": u_med, "oracle_full": ORACLE_FULL.get(args.workload)}
+            del O, oprob, ox
 
     if rank == 0:
         last = stats[-1]
@@ -436,6 +605,8 @@ def main():
             "status": last["status"],
             "plain_fp64": plain,
             "mixed_learned": learned,
+            "mixed_f32_basis": f32leg,
+            "gmres_vs_sks": sks_leg,
             "batch64": batch,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 16 * N,
                     "d2h_bytes_per_step": 16 * N},

@@ -127,6 +127,9 @@ typedef struct {
                                    GMRES, true residuals for SKS and refinement steps) */
   int cnn_cycles;     /* MIXED FGMRES with a learned stage attached: inner cycles that used
                          it (the others used the direct preconditioner alone) */
+  int cnn_fallbacks;  /* learned-stage cycles whose correction was non-finite: discarded
+                         (U kept its last iterate) and the rest of the solve used the
+                         direct preconditioner alone */
 } helm6_stats;
 
 /* Fill opts with the defaults listed above. */
@@ -228,23 +231,28 @@ int helm6_profile_read(helm6_ctx* ctx, helm6_profile* out);
 
 /* ---- Residual without device allocation (the paper has no counterpart) ----
  * r = F - A u for the sixth-order operator of helm6_apply_A, and *sumsq = ||r||_2^2, for
- * callers that cannot call cudaMalloc: code that runs where allocation is not allowed or
- * not possible -- a custom device allocator or memory pool that must not re-enter
- * cudaMalloc, an embedding runtime that owns every byte of device memory, a real-time loop
- * that must never block on the allocator, or a CUDA host callback (which may not make
- * CUDA calls that allocate).  It takes the problem description instead of a context (a
- * context allocates workspace), allocates nothing and calls no allocating routine.
+ * callers that cannot call cudaMalloc: a custom device allocator or memory pool that must
+ * not re-enter cudaMalloc, an embedding runtime that owns every byte of device memory, or a
+ * real-time loop that must never block on the allocator.  It takes the problem description
+ * instead of a context (a context allocates workspace), allocates nothing and calls no
+ * allocating routine.  It enqueues two kernels on `stream`, so it must be called from
+ * ordinary host code: not from a CUDA host function or stream callback, where no CUDA call
+ * is allowed at all.
  *
  * Its only scratch is a file-scope device array of HELM6_NOALLOC_MAX_BLOCKS doubles
  * (512 KiB) that every GPU which loads the library holds until the process exits.  Sizes
  * whose stencil grid needs more than HELM6_NOALLOC_MAX_BLOCKS thread blocks --
- * ceil(mx/32) * ceil(my/8) * ceil(mz/16), about n > 510 for a cube -- are rejected with
- * HELM6_ERR_INVALID before any device work.  The first call on each device looks up the
- * array's device address with that device current (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Every call shares the array and leaves its partial sums
- * there; each call writes every slot it reads, so nothing needs clearing, but calls that
- * overlap on the GPU (several streams, or several host threads on one device) race on it
- * and must be serialised by the caller.
+ * ceil(mx/32) * ceil(my/8) * ceil(mz/16): a cube up to n = 640 with Dirichlet faces, up to
+ * n = 638 with non-Dirichlet faces on every axis -- are rejected with HELM6_ERR_INVALID
+ * before any device work.  The first call on each device looks up the array's device
+ * address with that device current (cudaGetSymbolAddress); with CUDA's lazy module
+ * loading that first call may also load the library's device code and back the array with
+ * device memory.  So make one warm-up call per device from ordinary code, before any
+ * stream capture and before entering a context where allocation is forbidden; only the
+ * later calls are guaranteed to allocate nothing.  Every call shares the array and leaves
+ * its partial sums there; each call writes every slot it reads, so nothing needs clearing,
+ * but calls that overlap on the GPU (several streams, or several host threads on one
+ * device) race on it and must be serialised by the caller.
  *
  * n, h, k, faces: as helm6_create, except that Sommerfeld-like faces are accepted on z only
  * here (INVALID otherwise).  F, u, r: DEVICE complex128 arrays (layout as above), r must not
@@ -270,10 +278,15 @@ int helm6_residual_noalloc(int n, double h, helm6_c64 k, const int faces[6], con
 #define HELM6_CNN_NPARAMS 15602
 enum { HELM6_CNN_OFF = 0,   /* detach: the direct preconditioner alone */
        HELM6_CNN_ON = 1,    /* every inner cycle uses the learned stage */
-       HELM6_CNN_AUTO = 2   /* of inner cycles 0-2 only cycle 1 uses it; the later cycles use
-                               it only if cycle 1 reduced the true residual per iteration at
-                               least 10 % more (in logarithm) than cycle 2 did without it;
-                               otherwise the direct preconditioner alone (the fallback) */ };
+       HELM6_CNN_AUTO = 2   /* a probe: of inner cycles 0-2 only cycle 1 uses it, and only for
+                               its first 3 columns (flexible GMRES allows a different map per
+                               column); the later cycles use it on every column only if those
+                               3 columns reduced the residual estimate per column at least
+                               10 % more (in logarithm) than the first 3 columns of cycle 2
+                               did without it; otherwise the direct preconditioner alone (the
+                               fallback).  In every mode a learned-stage cycle whose
+                               correction is non-finite is discarded and the rest of the solve
+                               falls back (helm6_stats.cnn_fallbacks) */ };
 
 /* Attach (or with HELM6_CNN_OFF detach) a network to a MIXED FGMRES context.  theta: HOST
  * array of HELM6_CNN_NPARAMS floats (copied); out_scale: c above.  Allocates two BF16

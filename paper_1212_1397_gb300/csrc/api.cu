@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -76,7 +77,14 @@ struct helm6_ctx {
   float* cnn_t = nullptr;                          // u - A A_p^{-1} u, planar FP32
   uint16_t *cnn_a0 = nullptr, *cnn_a1 = nullptr;   // BF16 activations, 16 per point
   double* cnn_ss = nullptr;                        // ||u - A A_p^{-1} u||^2
-  double cyc_rate[3] = {1.0, 1.0, 1.0};            // per-iteration reduction of mixed cycles 0-2
+  // AUTO probe: the learned stage preconditions the first cnn_cols columns of a cycle (the
+  // rest use the direct preconditioner); probe_est is the cycle's residual estimate after
+  // probe_cols columns (relative to its start), probe_rate[1] / [2] the per-column
+  // reduction over those columns in cycle 1 (with the stage) and cycle 2 (without)
+  int cnn_cols = 1 << 30;
+  int probe_cols = 0;
+  double probe_est = 0.0;
+  double probe_rate[3] = {1.0, 1.0, 1.0};
   // CUDA graphs of the Arnoldi steps (opts.use_graphs): key (j, full, learned stage)
   struct StepGraph {
     cudaGraphExec_t exec;
@@ -363,6 +371,17 @@ template <>
 void (*precond_cnn_ptr<float>())(helm6_ctx*, const float*, float*) {
   return precond_cnn32;
 }
+// The direct preconditioner of precision T (what the learned stage falls back to).
+template <typename T>
+void (*precond_plain_ptr())(helm6_ctx*, const T*, T*);
+template <>
+void (*precond_plain_ptr<float>())(helm6_ctx*, const float*, float*) {
+  return precond32;
+}
+template <>
+void (*precond_plain_ptr<double>())(helm6_ctx*, const double*, double*) {
+  return precond64;
+}
 
 // ---- norms ----
 template <typename T>
@@ -429,6 +448,7 @@ int arnoldi(helm6_ctx* c, TV* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol,
     } else {
       k = sidx;
       if (st) st->iters++;
+      if (sidx == c->probe_cols) c->probe_est = est;
       push_hist(st, est);  // rescaled by the caller
       if (!(est > abs_tol) || !std::isfinite(est) || brk) *stop = true;
     }
@@ -436,10 +456,12 @@ int arnoldi(helm6_ctx* c, TV* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol,
   };
   // Enqueue step j: preconditioner and operator on u_j (full steps), the reduction pass,
   // the FP64 step algebra, the estimate's readback and event, and the update pass.
+  // column j's preconditioner: the learned stage only for the first cnn_cols columns
+  auto prec_of = [&](int j) { return (prec == precond_cnn_ptr<T>() && j >= c->cnn_cols) ? precond_plain_ptr<T>() : prec; };
   auto enqueue = [&](int j, bool full) -> int {
     if (full) {
       T* zj = flexible ? Z + (int64_t)j * vs : zt;
-      prec(c, u, zj);
+      prec_of(j)(c, u, zj);
       cudaEvent_t e = prof_start(c);
       launch_stencil<T>(c->g, coef, zj, w, nullptr, nullptr, 0, nullptr, nullptr, s);
       prof_stop(c, HELM6_PH_STENCIL, e);
@@ -474,7 +496,7 @@ int arnoldi(helm6_ctx* c, TV* V, T* Z, T* u, T* w, T* zt, int m, double abs_tol,
   for (int j = 0;; ++j) {
     const bool full = (j < m) && (applied < maxsteps);
     if (graphs) {
-      const int key = (j * 2 + (full ? 1 : 0)) * 2 + (prec == precond_cnn_ptr<T>() ? 1 : 0);
+      const int key = (j * 2 + (full ? 1 : 0)) * 2 + (prec_of(j) == precond_cnn_ptr<T>() ? 1 : 0);
       auto it = c->step_graphs.find(key);
       if (it == c->step_graphs.end()) {
         // first use of this step: capture and instantiate it, one thread at a time (the
@@ -594,15 +616,19 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
 }
 
 // MIXED: FP64 refinement around FP32 FGMRES with the FP32 preconditioner.
+// Columns of the AUTO probe (cycle 1 preconditions this many columns with the learned stage).
+constexpr int kCnnProbe = 3;
+
 // Whether inner cycle `cyc` of a mixed solve uses the learned stage: ON always; AUTO uses
-// it in cycle 1 only of cycles 0-2 (cycle 0, from the initial guess, reduces faster than
-// any later one and is not compared), and afterwards only if cycle 1 (with) reduced the
-// true residual per iteration by at least 10 % more, in logarithm, than cycle 2 (without).
+// it for the first kCnnProbe columns of cycle 1 only, of cycles 0-2 (cycle 0, from the
+// initial guess, reduces faster than any later one and is not compared), and afterwards
+// on every column only if those probe columns reduced the residual estimate per column by
+// at least 10 % more, in logarithm, than the same columns of cycle 2 (without the stage).
 bool cnn_cycle(const helm6_ctx* c, int cyc) {
   if (c->cnn_mode == HELM6_CNN_ON) return true;
   if (c->cnn_mode != HELM6_CNN_AUTO) return false;
   if (cyc < 3) return cyc == 1;
-  const double l1 = std::log(std::max(c->cyc_rate[1], 1e-300)), l2 = std::log(std::max(c->cyc_rate[2], 1e-300));
+  const double l1 = std::log(std::max(c->probe_rate[1], 1e-300)), l2 = std::log(std::max(c->probe_rate[2], 1e-300));
   return l2 < 0 && l1 < 1.1 * l2;
 }
 
@@ -614,6 +640,10 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
   int iters = 0;
   const double inner = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-5;
   int cyc = 0;
+  // set when a learned-stage cycle produced a non-finite correction: the rest of this
+  // solve uses the direct preconditioner alone (the fallback)
+  bool cnn_failed = false;
+  std::vector<double> qhost;
   while (true) {
     if (!std::isfinite(beta)) return HELM6_NONFINITE;
     if (beta <= tol * normF) return HELM6_OK;
@@ -623,8 +653,12 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     int k = 0;
     double b0 = 0;
     const int h0 = st ? st->nhist : 0;
-    const bool use_cnn = cnn_cycle(c, cyc);
+    const bool use_cnn = !cnn_failed && cnn_cycle(c, cyc);
     auto* prec = use_cnn ? precond_cnn32 : precond32;
+    const bool probing = c->cnn_mode == HELM6_CNN_AUTO && (cyc == 1 || cyc == 2);
+    c->cnn_cols = (probing && use_cnn) ? kCnnProbe : (1 << 30);
+    c->probe_cols = probing ? kCnnProbe : 0;
+    c->probe_est = std::numeric_limits<double>::quiet_NaN();
     rc = c->V16 ? arnoldi<float, __half>(c, c->V16, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
                                          prec, c->coef, &k, &b0, st)
                 : arnoldi<float, float>(c, c->V32, c->Z32, c->u32, c->w32, c->zt32, m, itol, maxit - iters, true,
@@ -633,11 +667,30 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     if (st && use_cnn) st->cnn_cycles++;
     fix_hist(st, h0, beta / normF);
     iters += k;
-    const double beta_in = beta;
-    if (k > 0) {
-      launch_tri_mul(c->Tm, c->mrest, k, c->yv, c->qv, c->stream);
-      launch_lincomb<float, double>(c->Z32, 2 * c->g.N, k, c->qv, beta, c->U64, c->g.N, 1, c->stream);
+    bool apply = k > 0;
+    if (k > 0) launch_tri_mul(c->Tm, c->mrest, k, c->yv, c->qv, c->stream);
+    if (use_cnn) {
+      // A network that returns NaN/Inf (corrupt weights, an input far outside its training
+      // range) makes the cycle's estimate or coefficients non-finite.  Then U64 keeps the
+      // last good iterate and the remaining cycles fall back to the direct preconditioner.
+      bool bad = false;
+      if (st && st->nhist > h0)
+        for (int i = h0; i < st->nhist; ++i) bad = bad || !std::isfinite(st->hist[i]);
+      if (k > 0) {
+        qhost.resize(2 * (size_t)k);
+        CK(cudaMemcpyAsync(qhost.data(), c->qv, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (double q : qhost) bad = bad || !std::isfinite(q);
+      } else {
+        bad = true;  // the cycle stopped before its first column: the stage's first output failed
+      }
+      if (bad) {
+        apply = false;
+        cnn_failed = true;
+        if (st) st->cnn_fallbacks++;
+      }
     }
+    if (apply) launch_lincomb<float, double>(c->Z32, 2 * c->g.N, k, c->qv, beta, c->U64, c->g.N, 1, c->stream);
     if (st) st->outer++;
     rc = residual64(c, &beta);
     if (rc) return rc;
@@ -646,8 +699,14 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
       const int cs = check_status(c);
       if (cs == HELM6_BREAKDOWN || cs < 0) return cs;
     }
-    // per-iteration reduction of this cycle (for the AUTO choice of the learned stage)
-    if (cyc < 3) c->cyc_rate[cyc] = (k > 0 && beta_in > 0) ? std::pow(beta / beta_in, 1.0 / k) : 1.0;
+    // per-column reduction over the probe columns (for the AUTO choice of the learned
+    // stage); a cycle that ended before them, or failed, gives no reduction
+    if (probing)
+      c->probe_rate[cyc] = (std::isfinite(c->probe_est) && c->probe_est > 0 && !cnn_failed)
+                               ? std::pow(c->probe_est, 1.0 / kCnnProbe)
+                               : 1.0;
+    c->cnn_cols = 1 << 30;
+    c->probe_cols = 0;
     ++cyc;
   }
 }

@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
   load_stage(p, m0, 0, warp, lane, xr);
   const uint32_t id = idesc(npad);
 
+  int last_commit = -1;  // thread 0: the last stage whose MMAs were committed
   // No block-wide barrier in the loop: each thread waits only for the MMAs that last read
   // the stage buffer it is about to overwrite, stores its part of the data stage and
   // arrives on afull; thread 0 alone waits for afull and the basis before issuing.
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
                    : "memory");
+      last_commit = kt;
       // stage (kt + 1) & 1 was last read by the MMAs of step kt - 1
       if (kt >= 1 && kt + 1 < p.nk) {
         if (!poll(done(st ^ 1), ((kt - 1) >> 1) & 1)) {
@@ -244,12 +246,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
     }
   }
 
-  // wait for the last committed stage (commits complete in order)
+  // wait for the last committed stage (commits complete in order), also after a timeout
+  // elsewhere: no MMA may still write tensor memory when it is freed below
   __syncthreads();
-  if (!*fail) {
-    const int last = p.nk - 1;
-    if (!poll(done(last & 1), (last >> 1) & 1)) *fail = 1;
-  }
+  if (tid == 0 && last_commit >= 0 && !poll(done(last_commit & 1), (last_commit >> 1) & 1)) *fail = 1;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (!*fail) {

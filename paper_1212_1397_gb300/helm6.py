@@ -52,12 +52,14 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("status", C.c_int),
                 ("relres", C.c_double), ("t_total_ms", C.c_double), ("nhist", C.c_int),
-                ("hist", C.c_double * MAX_HIST), ("cnn_cycles", C.c_int)]
+                ("hist", C.c_double * MAX_HIST), ("cnn_cycles", C.c_int),
+                ("cnn_fallbacks", C.c_int)]
 
     def to_dict(self):
         return dict(iters=self.iters, outer=self.outer, status=STATUS.get(self.status, self.status),
                     relres=self.relres, t_total_ms=self.t_total_ms,
-                    history=list(self.hist[: self.nhist]), cnn_cycles=self.cnn_cycles)
+                    history=list(self.hist[: self.nhist]), cnn_cycles=self.cnn_cycles,
+                    cnn_fallbacks=self.cnn_fallbacks)
 
 
 class Profile(C.Structure):
@@ -162,8 +164,18 @@ def residual_noalloc(n, k, faces, F, u, r, sumsq, h=0.0, stream=None):
     F, u, r: complex128 CUDA tensors of the grid's shape; sumsq: float64 CUDA tensor of one
     element.  Returns the library's return code (raises on errors)."""
     import torch
-    if not (isinstance(sumsq, torch.Tensor) and sumsq.is_cuda and sumsq.dtype == torch.float64):
-        raise TypeError("sumsq must be a float64 CUDA tensor")
+    if len(faces) != 6 or any(ch not in _FACE_CODE for ch in faces):
+        raise ValueError(f"faces must be 6 letters over D, N, S, got {faces!r}")
+    # unknowns per axis: n plus one per non-Dirichlet face of that axis
+    mx, my, mz = (int(n) + (faces[2 * a] != "D") + (faces[2 * a + 1] != "D") for a in range(3))
+    npts = mx * my * mz
+    for name, t in (("F", F), ("u", u), ("r", r)):
+        if not isinstance(t, torch.Tensor) or t.numel() != npts:
+            got = t.numel() if isinstance(t, torch.Tensor) else type(t).__name__
+            raise ValueError(f"{name} must hold mx*my*mz = {mx}*{my}*{mz} = {npts} elements, got {got}")
+    if not (isinstance(sumsq, torch.Tensor) and sumsq.is_cuda and sumsq.dtype == torch.float64
+            and sumsq.numel() >= 1):
+        raise TypeError("sumsq must be a float64 CUDA tensor of at least one element")
     lib = load()
     f = (C.c_int * 6)(*[_FACE_CODE[ch] for ch in faces])
     kk = complex(k)

@@ -76,3 +76,21 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib_path):
     lib.helm6_opts_default(ctypes.byref(o))
     o.max_restart = 1000
     assert lib.helm6_create(ctypes.byref(ctx), 8, 0.0, k, faces, ctypes.byref(o)) == -1
+
+
+def test_noalloc_binding_rejects_wrong_sizes_before_any_launch():
+    """residual_noalloc checks F, u and r against the grid that n and faces imply before it
+    touches the library or the device (a short r would be written out of bounds)."""
+    torch = pytest.importorskip("torch")
+    from paper_1212_1397_gb300 import helm6 as H
+    n, faces = 6, "DDNNSS"            # 6 x 8 x 8 unknowns
+    good = torch.zeros((8, 8, 6), dtype=torch.complex128)
+    short = torch.zeros(8 * 8 * 6 - 1, dtype=torch.complex128)
+    ss = torch.zeros(1, dtype=torch.float64)
+    for F, u, r in ((short, good, good), (good, short, good), (good, good, short)):
+        with pytest.raises(ValueError):
+            H.residual_noalloc(n, 3.0, faces, F, u, r, ss)
+    with pytest.raises(ValueError):
+        H.residual_noalloc(n, 3.0, "DDNNS", good, good, good, ss)
+    with pytest.raises(ValueError):
+        H.residual_noalloc(n, 3.0, "DDNNSX", good, good, good, ss)

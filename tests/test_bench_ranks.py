@@ -32,8 +32,11 @@ def _rank_main(rank, world, port, out_dir):
     bench.sync_all(dist, cuda=False)
     worst = bench.reduce_max(local_ms, dist)
     seeds = bench.replica_seeds(rank)
-    # reference arm: only rank 0 runs and prints (the oracle sample is replaced by a stub)
-    bench.oracle_sample = lambda cfg, iters: (123.0, 0.5)
+    # reference arm: only rank 0 runs and prints (the oracle's unit costs and its recorded
+    # complete solve are replaced by stubs: 0.1 s per unit, 40 iterations)
+    bench.oracle_problem = lambda cfg, seed: (None, None, None)
+    bench.oracle_unit_costs = lambda O, prob, x: dict(setup=0.1, precond=0.1, apply_A=0.1, proj=0.1)
+    bench.ORACLE_FULL[bench.WORKLOAD] = dict(iters=40, cycles=2, seconds=1.0)
     args = type("A", (), dict(warmup=0, steps=1, gpus=world, workload=bench.WORKLOAD))()
     buf = io.StringIO()
     with redirect_stdout(buf):
@@ -58,7 +61,22 @@ def test_two_gloo_ranks(tmp_path):
     assert res[0]["seeds"] != res[1]["seeds"]
     assert res[1]["printed"] == ""
     line = json.loads(res[0]["printed"])
-    assert line["impl"] == "reference" and line["value"] == 123.0 and line["n_gpus"] == 2
+    # 0.1 s x (set-up + initial A + 40 (A_p^-1 + A) + 2 cycles (A_p^-1 + A)
+    # + (465 + 30) + (55 + 10) projections) = 0.1 s x 646
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
+    assert abs(line["value"] - 64600.0) < 1e-6, line["value"]
+
+
+def test_oracle_projection_counts_the_gmres_work():
+    """The projection of the oracle's GMRES(m) from its unit costs: per column j of a cycle
+    j + 1 projections, per cycle one more per column (V y), A_p^-1 and A per iteration and
+    per cycle, plus the set-up and the initial residual."""
+    import bench
+    u = dict(setup=1.0, precond=10.0, apply_A=100.0, proj=1000.0)
+    ms, cyc = bench.oracle_projection(u, 35, 30)
+    assert cyc == 2
+    proj = (30 * 31 // 2 + 30) + (5 * 6 // 2 + 5)
+    assert ms == 1e3 * (1.0 + 100.0 + 35 * 110.0 + 2 * 110.0 + proj * 1000.0)
 
 
 def test_metric_names_the_workload():

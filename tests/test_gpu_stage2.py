@@ -138,6 +138,56 @@ def test_solve_with_learned_stage_matches_oracle(H, mode):
         assert st["cnn_cycles"] >= min(1, st["outer"] - 1)
 
 
+@pytest.mark.parametrize("fault,mode", [("nan_weight", "CNN_ON"), ("overflow", "CNN_ON"),
+                                        ("nan_weight", "CNN_AUTO")])
+def test_failing_network_falls_back_to_the_direct_preconditioner(H, fault, mode):
+    """Faults injected on the host into the network's parameters: one NaN weight (corrupt
+    weights), or weights scaled by 1e30 so that the BF16/FP32 forward overflows (a failing
+    network).  The learned-stage cycle's non-finite correction is discarded, the rest of the
+    solve runs on A_p^-1 alone and still reaches the oracle's solution."""
+    n, k, faces = 29, 10.0 + 0.1j, "DDNNSS"
+    prob = O.Problem(n, k, faces)
+    src = inputs.gaussian_sources(3, n, 2, margin_h=4)
+    F = O.rhs(prob, O.sources.gaussians(src))
+    Uref, _ = O.solve(prob, F, tol=1e-13)
+    th = _theta(11)
+    if fault == "nan_weight":
+        th[5] = np.nan
+    else:
+        th = (th * np.float32(1e30)).astype(np.float32)
+    with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=10) as s:
+        _, st0 = s.solve(torch.from_numpy(F).cuda(), tol=1e-8, restart=10, maxit=400)
+        s.set_cnn(th, 0.05, getattr(H, mode))
+        u, st = s.solve(torch.from_numpy(F).cuda(), tol=1e-8, restart=10, maxit=400)
+    assert st["rc"] == 0 and st["relres"] <= 1e-8, st["status"]
+    assert st["cnn_fallbacks"] == 1 and st["cnn_cycles"] == 1, st
+    assert np.isfinite(u.cpu().numpy()).all()
+    assert rel2(u.cpu().numpy(), Uref) < 1e-6
+    # the failed cycle's iterations are spent, the rest is the plain solve's work
+    assert st["iters"] <= st0["iters"] + 10
+
+
+def test_wavenumber_on_the_preconditioner_spectrum(H):
+    """k^2 h^2 placed exactly on the spectrum of the 7-point operator (mode (1,1,1) of the
+    Dirichlet cube): A_p is singular up to rounding, its z-line for that mode has a pivot at
+    rounding level.  The solver must answer with a documented status, and a converged
+    answer must satisfy the oracle's operator to the tolerance (A itself stays regular: its
+    symbol differs from A_p's at O(h^2))."""
+    n = 15
+    h = 1.0 / (n + 1)
+    k = float(np.sqrt(3 * 4 * np.sin(np.pi * h / 2) ** 2) / h)
+    prob = O.Problem(n, k, "DDDDDD")
+    F = O.rhs(prob, O.sources.gaussians(inputs.gaussian_sources(5, n, 1, margin_h=4)))
+    for prec, meth in ((H.FP64, H.GMRES), (H.MIXED, H.FGMRES)):
+        with H.Solver(n, k, "DDDDDD", precision=prec, method=meth, max_restart=20) as s:
+            u, st = s.solve(torch.from_numpy(F).cuda(), tol=1e-8, restart=20, maxit=300)
+        assert st["status"] in ("OK", "NOT_CONVERGED", "BREAKDOWN", "NONFINITE"), st["status"]
+        if st["rc"] == 0:
+            U = u.cpu().numpy()
+            res = np.linalg.norm(F - O.apply_A(prob, U)) / np.linalg.norm(F)
+            assert res <= 1.05e-8, (prec, res)
+
+
 def test_learned_stage_argument_errors(H):
     th = _theta(12)
     with H.Solver(10, 5.0, "DDNNSS", precision=H.FP64, method=H.GMRES) as s:
@@ -189,7 +239,7 @@ def test_trained_network_gain(H, capsys):
     (reported); (2) iterations of mixed
     FGMRES(30) to 1e-8 without the stage, with it on every cycle, and in AUTO mode.  All
     three solutions must match the oracle's; the learned stage must cut the one-step
-    residual; AUTO may cost at most its one probe cycle over the plain solve."""
+    residual; AUTO may cost at most its three probe columns over the plain solve."""
     w = _weights()
     theta, c = w["theta"], float(w["out_scale"])
     assert w["val"][-1] < 0.35  # held-out patches: residual energy left, relative to N = 0
@@ -219,4 +269,6 @@ def test_trained_network_gain(H, capsys):
     with capsys.disabled():
         print("\nlearned stage gain:", out)
     assert out["iterate_residual"]["ratio"] < 0.8
-    assert out["CNN_AUTO"]["iters"] <= out["CNN_OFF"]["iters"] + 30
+    # AUTO's probe is 3 learned-stage columns: it may not cost more than a few iterations
+    # over the direct preconditioner alone (time-to-solution is printed above)
+    assert out["CNN_AUTO"]["iters"] <= out["CNN_OFF"]["iters"] + 4
