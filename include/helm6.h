@@ -194,6 +194,19 @@ int helm6_rhs_gaussians(helm6_ctx* ctx, int nsrc, const double* centers,
 int helm6_rhs_separable(helm6_ctx* ctx, int nterms, const helm6_c64* coef, const helm6_c64* tables,
                         void* F);
 
+/* Inhomogeneous Dirichlet data on a z face (Section 4.2: u = u_b at z = 1 with the Neumann
+ * face at z = 0, Tables 5 and 6): the face's nodes are known, so their contribution to the
+ * rows of the neighbouring plane moves to the right side,
+ *     F(l, j, i) -= sum_{|di|,|dj| <= 1} w(di, dj) u_b(j + dj, i + di),
+ * w the weights of the interior rows' z +- 1 plane in Eq. scheme (centre, 4 neighbours, 4
+ * diagonals).  face: 4 (z = 0) or 5 (z = top), a Dirichlet face of the context; data: DEVICE
+ * complex128 array of (my + 2) x (mx + 2) values on the face's node layer, x fastest, with
+ * its ring (entry (j + 1, i + 1) is the node above/below unknown (i, j); the ring holds the
+ * nodes on the neighbouring faces' ghost columns and rows); F: DEVICE complex128, updated in
+ * place.  Stream-ordered.  Returns OK, INVALID (NULL argument, face not Dirichlet),
+ * UNSUPPORTED (an x or y face, or a context with Sommerfeld-like faces on x or y) or CUDA. */
+int helm6_lift_dirichlet(helm6_ctx* ctx, int face, const void* data, void* F);
+
 /* ---- Measurement (not part of the method) ----
  * Per-phase device time of helm6_solve / helm6_apply_* measured with CUDA events on the
  * context's stream, and the number of kernels the library launched.  Off by default;

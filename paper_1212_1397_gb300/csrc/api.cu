@@ -52,7 +52,7 @@ struct helm6_ctx {
   // MIXED: BF16 hi/lo basis tiles for the tensor-core transforms (null: SIMT FP32 path)
   uint8_t *Wx_tc = nullptr, *Wy_tc = nullptr, *Vx_tc = nullptr, *Vy_tc = nullptr;
   int* tcerr = nullptr;
-  float *zrinv32 = nullptr, *zcp32 = nullptr;  // z-line pivot tables (tensor-core path)
+  ZLines zl;  // z-line pivot tables (tensor-core path)
   // FP64 vectors (2N doubles each)
   double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
   double* D64 = nullptr;           // Chebyshev direction
@@ -92,8 +92,6 @@ struct helm6_ctx {
   };
   std::map<int, StepGraph> step_graphs;
   cudaStream_t cap_stream = nullptr;  // private stream the step graphs are captured on
-  cudaStream_t aux_stream = nullptr;  // side stream of the transforms' FP32 tail columns
-  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   bool own_stream = false;            // `stream` was created by the context
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
@@ -324,19 +322,19 @@ void precond_tc(helm6_ctx* c, const float* in, float* out) {
   const int terms = c->opts.xform_terms;
   const int rows_x = 2 * g.mz * g.my, rows_y = 2 * g.mz * g.mx;
   cudaEvent_t e = prof_start(c);
-  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
+  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s);
   prof_stop(c, HELM6_PH_XFWD, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
+  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s);
   prof_stop(c, HELM6_PH_YFWD, e);
   e = prof_start(c);
-  launch_ztri_apply<float>(g, c->zrinv32, c->zcp32, c->tB32, c->tA32, s);
+  launch_ztri_apply(g, c->zl, c->tB32, c->tA32, c->tcerr, s);
   prof_stop(c, HELM6_PH_ZTRI, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
+  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s);
   prof_stop(c, HELM6_PH_YINV, e);
   e = prof_start(c);
-  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s, c->aux_stream, c->aux_fork, c->aux_join);
+  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s);
   prof_stop(c, HELM6_PH_XINV, e);
 }
 
@@ -865,9 +863,6 @@ void helm6_destroy(helm6_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (auto& kv : c->step_graphs) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
-  if (c->aux_fork) cudaEventDestroy(c->aux_fork);
-  if (c->aux_join) cudaEventDestroy(c->aux_join);
   for (void* p : c->allocs) cudaFree(p);
   cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
@@ -1059,13 +1054,13 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     if ((rc = upt(&c->Wx_tc, Wx, c->g.mx)) || (rc = upt(&c->Vx_tc, Vx, c->g.mx)) ||
         (rc = upt(&c->Wy_tc, Wy, c->g.my)) || (rc = upt(&c->Vy_tc, Vy, c->g.my)))
       return fail(rc);
-    if ((rc = dalloc(c, &c->zrinv32, v)) || (rc = dalloc(c, &c->zcp32, v))) return fail(rc);
-    if (cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming) != cudaSuccess)
-      return fail(HELM6_ERR_CUDA);
+    const size_t lines = (size_t)c->g.mx * c->g.my;
+    if ((rc = dalloc(c, &c->zl.rinv, v)) || (rc = dalloc(c, &c->zl.rc, lines)) ||
+        (rc = dalloc(c, &c->zl.rconv, lines)) || (rc = dalloc(c, &c->zl.rlast, lines)))
+      return fail(rc);
+    if (ztri_configure(c->g) != HELM6_OK) return fail(HELM6_ERR_CUDA);
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
-    launch_ztri_table<float>(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zrinv32, c->zcp32, c->status, 0, 1);
+    launch_ztri_table(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zl, c->status, 0, 1);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
     int zst = 0;
     if (cudaMemcpy(&zst, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(HELM6_ERR_CUDA);
@@ -1297,6 +1292,14 @@ int helm6_rhs_separable(helm6_ctx* c, int nterms, const helm6_c64* coef, const h
   if (!c || !F || nterms < 0 || nterms > 4096) return HELM6_ERR_INVALID;
   if (nterms > 0 && (!coef || !tables)) return HELM6_ERR_INVALID;
   return rhs_separable(c->gu, c->h, c->k, nterms, (const double*)coef, (const double*)tables, (double*)F, c->stream);
+}
+
+int helm6_lift_dirichlet(helm6_ctx* c, int face, const void* data, void* F) {
+  if (!c || !data || !F) return HELM6_ERR_INVALID;
+  if (face != 4 && face != 5) return HELM6_ERR_UNSUPPORTED;
+  if (c->xaxis >= 0) return HELM6_ERR_UNSUPPORTED;
+  if (c->gu.face[face] != HELM6_DIRICHLET) return HELM6_ERR_INVALID;
+  return lift_dirichlet_z(c->gu, c->coef, face - 4, (const double*)data, (double*)F, c->stream);
 }
 
 }  // extern "C"

@@ -112,16 +112,14 @@ void launch_axis_gemm(const T* A, const T* B, T* C, int m, int ncols, int ld, in
 // out(row, p) = sum_k in(row, k) B(p, k), rows of length K, M_total rows, P <= tc_max_axis().
 // W: tc_prepare_basis(B).  transposed = 0: out[row*P + p]; 1: out[(row/R)*R*P + p*R + row%R].
 // terms: 1 (hi*hi), 2 (+ lo*hi), 3 (+ hi*lo).  *err is set if a bounded wait timed out.
+// Persistent: one CTA per SM (all of its shared memory and tensor memory).
 int tc_npad(int P);
 int tc_nk(int K);
 int tc_max_axis();
 int tc_configure();
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out);
-// aux, fork, join (all non-null, or null): a stream and two events that let the FP32 tail
-// columns (257 to 288 output columns) run beside the tensor-core kernel; s waits for them.
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s, cudaStream_t aux = nullptr,
-                     cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+                     int transposed, int R, int* err, cudaStream_t s);
 
 // Tridiagonal solve along z for every (x, y) mode pair, Thomas algorithm started at the
 // Sommerfeld-like end (if any).  x: input, y: output (may alias x), cw: scratch of 2N T.
@@ -131,12 +129,21 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
                  const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor = 0);
 
 // The same z-line solve with the elimination's pivots precomputed in FP64 (once per
-// context) and stored as tables rinv (pivot reciprocals) and cpr (c') of 2N T each.
-template <typename T>
-void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, T* rinv,
-                       T* cpr, int* status, cudaStream_t s, int xmajor);
-template <typename T>
-void launch_ztri_apply(const Geom& g, const T* rinv, const T* cpr, const T* x, T* y, cudaStream_t s);
+// context) and stored in FP32: rinv (2N floats, planar, indexed like the field) holds the
+// pivot reciprocal of every step; per line, rc is the first step from which the stored
+// pivots of steps < m - 1 no longer change, rconv that pivot and rlast the last step's.
+struct ZLines {
+  float* rinv = nullptr;
+  int* rc = nullptr;
+  float2* rconv = nullptr;
+  float2* rlast = nullptr;
+};
+void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, ZLines z,
+                       int* status, cudaStream_t s, int xmajor);
+int ztri_configure(const Geom& g);  // kernel attributes (before any capture)
+// y = the z-line solve of x (planar FP32, x-mode-major planes); *err set if a bounded wait
+// of the blocked kernel timed out.
+void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, int* err, cudaStream_t s);
 
 // BLAS-1 style kernels on planar complex vectors of N points.
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
@@ -178,6 +185,11 @@ int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers
 // [nterm][3][5][max(mx, my, mz)] of the factors' derivatives 0..4 at the unknown nodes.
 int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, const double* tables, double* F,
                   cudaStream_t s);
+
+// F -= the contribution of known Dirichlet values ub ((my + 2) x (mx + 2) complex128, the
+// face's node layer with its ring) on the z face `side` (0: z = 0, 1: z = top) to the
+// neighbouring plane's rows; F complex128 interleaved in geometry g.
+int lift_dirichlet_z(const Geom& g, const StencilCoef& coef, int side, const double* ub, double* F, cudaStream_t s);
 
 // y += alpha x (planar, 2N reals), mixed input/output precision.
 template <typename TI, typename TO>

@@ -208,4 +208,39 @@ int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, 
   return launch_rhs(g, h, k, nterm, mmax, tab, coef, nullptr, F, s);
 }
 
+namespace {
+
+// Lifting of inhomogeneous Dirichlet data on a z face: the face's nodes are known, so their
+// contribution to the neighbouring plane's rows moves to the right side,
+//   F(l, j, i) -= sum over the 3 x 3 face nodes around (i, j) of w(di, dj) u_b,
+// w = the interior rows' weights of the z +- 1 plane (centre c1, 4 neighbours c2, 4
+// diagonals c3 of Eq. scheme).  ub: (my + 2) x (mx + 2) complex128 values on the face's
+// node layer, ring included (the nodes of the neighbouring faces' ghost columns and rows).
+__global__ void lift_z_kernel(Geom g, c64d w0, c64d w1, c64d w2, int l, const double* __restrict__ ub,
+                              double* __restrict__ F) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)g.mx * g.my) return;
+  const int i = (int)(t % g.mx), j = (int)(t / g.mx);
+  const int ld = g.mx + 2;
+  auto at = [&](int jj, int ii) { const int64_t o = (int64_t)jj * ld + ii; return Z{ub[2 * o], ub[2 * o + 1]}; };
+  const Z c = at(j + 1, i + 1);
+  const Z n = at(j, i + 1) + at(j + 2, i + 1) + at(j + 1, i) + at(j + 1, i + 2);
+  const Z d = at(j, i) + at(j, i + 2) + at(j + 2, i) + at(j + 2, i + 2);
+  const Z s = zc(w0) * c + zc(w1) * n + zc(w2) * d;
+  const int64_t o = (int64_t)l * g.mx * g.my + t;
+  F[2 * o] -= s.re;
+  F[2 * o + 1] -= s.im;
+}
+
+}  // namespace
+
+int lift_dirichlet_z(const Geom& g, const StencilCoef& coef, int side, const double* ub, double* F, cudaStream_t s) {
+  const RowWeights& w = coef.interior;
+  const int l = side ? g.mz - 1 : 0;
+  const int64_t n = (int64_t)g.mx * g.my;
+  note_launch();
+  lift_z_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, w.w[2][0], w.w[2][1], w.w[2][2], l, ub, F);
+  return cudaGetLastError() == cudaSuccess ? (int)HELM6_OK : (int)HELM6_ERR_CUDA;
+}
+
 }  // namespace helm6

@@ -336,9 +336,11 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
       whi[a][b] = cast<float>(coef.s_hi.w[a][b]);
     }
   const cpx<float> zero = {0.f, 0.f};
-  Sums<float> P0[T4R], P1[T4R], P2[T4R];
+  // plane sums of three consecutive planes, rotated by renaming: the loop below is
+  // unrolled by three so that no register moves are needed
+  Sums<float> SA[T4R], SB[T4R], SC[T4R];
 #pragma unroll
-  for (int r = 0; r < T4R; ++r) P0[r] = P1[r] = P2[r] = Sums<float>{zero, zero, zero};
+  for (int r = 0; r < T4R; ++r) SA[r] = SB[r] = SC[r] = Sums<float>{zero, zero, zero};
   double acc = 0.0;
 
   const int pfirst = l0 - 1;
@@ -346,7 +348,9 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
     if (pfirst + d <= l1) stage(pfirst + d, d);
     cp_commit();
   }
-  for (int p = pfirst; p <= l1; ++p) {
+  // step p: the sums of plane p go to PN; rows of plane p - 1 use P0 (plane p - 2), P1
+  // (plane p - 1) and PN (plane p)
+  auto step = [&](int p, Sums<float>(&PN)[T4R], Sums<float>(&P0)[T4R], Sums<float>(&P1)[T4R]) {
     const int k = p - pfirst;
     if (p + DIST <= l1) stage(p + DIST, (k + DIST) % NBUF);
     cp_commit();
@@ -376,9 +380,7 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
       cur.c = mk(vr[r + 1][1], vi[r + 1][1]);
       cur.n = mk(hr[r + 1] + vr[r][1] + vr[r + 2][1], hi[r + 1] + vi[r][1] + vi[r + 2][1]);
       cur.d = mk(hr[r] + hr[r + 2], hi[r] + hi[r + 2]);
-      P0[r] = P1[r];
-      P1[r] = P2[r];
-      P2[r] = cur;
+      PN[r] = cur;
     }
     const int l = p - 1;
     if (l >= l0 && i < g.mx) {
@@ -390,8 +392,8 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
         if (j >= g.my) continue;
         cpx<float> out;
         if (!slo && !shi) {
-          const cpx<float> s1 = P1[r].n + P0[r].c + P2[r].c, s2 = P1[r].d + P0[r].n + P2[r].n,
-                           s3 = P0[r].d + P2[r].d;
+          const cpx<float> s1 = P1[r].n + P0[r].c + PN[r].c, s2 = P1[r].d + P0[r].n + PN[r].n,
+                           s3 = P0[r].d + PN[r].d;
           if constexpr (RW) {
             out.re = fmaf(c3.re, s3.re, fmaf(c2.re, s2.re, fmaf(c1.re, s1.re, c0.re * P1[r].c.re)));
             out.im = fmaf(c3.re, s3.im, fmaf(c2.re, s2.im, fmaf(c1.re, s1.im, c0.re * P1[r].c.im)));
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
             const cpx<float> wp = slo ? wlo[2][a] : whi[2][a];
             const cpx<float> s0 = (a == 0) ? P0[r].c : (a == 1) ? P0[r].n : P0[r].d;
             const cpx<float> s1 = (a == 0) ? P1[r].c : (a == 1) ? P1[r].n : P1[r].d;
-            const cpx<float> s2 = (a == 0) ? P2[r].c : (a == 1) ? P2[r].n : P2[r].d;
+            const cpx<float> s2 = (a == 0) ? PN[r].c : (a == 1) ? PN[r].n : PN[r].d;
             out = cfma(wc, s0, out);
             out = cfma(wm, s1, out);
             out = cfma(wp, s2, out);
@@ -427,6 +429,11 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
         if (NORM) acc += (double)out.re * out.re + (double)out.im * out.im;
       }
     }
+  };
+  for (int p = pfirst; p <= l1; p += 3) {
+    step(p, SA, SB, SC);
+    if (p + 1 <= l1) step(p + 1, SB, SC, SA);
+    if (p + 2 <= l1) step(p + 2, SC, SA, SB);
   }
   cp_wait<0>();
   if (NORM) {

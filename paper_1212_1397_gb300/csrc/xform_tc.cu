@@ -7,25 +7,33 @@
 // hi = bf16(x) and lo = bf16(x - hi); the basis is split the same way on the host, and
 // D accumulates hi*hi + lo*hi (+ hi*lo) in FP32 in tensor memory (1, 2 or 3 products).
 //
-// CTA = 128 data rows (one MMA M) x one group of at most 256 output columns (P > 256 is
-// cut into two groups, interleaved in the grid so that the two CTAs of a row tile run
-// together and share its data in L2).  K is streamed in 32-element stages, double
-// buffered, in the no-swizzle K-major layout: a core matrix is 8 rows x 16 bytes stored
-// contiguously, core matrices 8 rows apart are 128 B apart and the K direction steps by
-// one whole column of core matrices.  The basis stage arrives by a bulk copy completing on
-// an mbarrier; the data stage is loaded, split and stored by all threads (each warp writes
-// whole core matrices, conflict-free); one thread issues the MMAs and commits them to a
-// second mbarrier that releases the stage.  At most 256 tensor-memory columns and about
-// 100 KB of shared memory per CTA let two CTAs share an SM.  Every mbarrier wait is
-// bounded; a timeout sets *err, skips the remaining work, and the CTA still frees its
-// tensor memory.
-//
-// Epilogue: each warp reads its 32 tensor-memory lanes (rows) and half of the columns and
-// stores either transposed within planes of R rows (out[(row/R)*R*P + p*R + row%R], which
-// keeps consecutive lanes on consecutive addresses) or row-major (out[row*P + p]) through
-// shared memory, 64 rows at a time, so that rows are written coalesced.
+// Persistent and warp-specialised: one CTA per SM walks the work items (128-row tile x
+// column group) blockIdx.x, + gridDim.x, ...; K is streamed in 32-element stages through
+// three rings in shared memory:
+//   * converter warps (4 x 32 threads, thread t <-> row t of the tile) copy their row's 32
+//     FP32 values of a stage into a private slot of an FP32 ring with cp.async, three
+//     stages ahead, then split them into the BF16 hi/lo operand ring (no-swizzle K-major
+//     core matrices: 8 rows x 16 bytes, 8-row groups 128 B apart, K step one column of
+//     core matrices) and arrive on the stage's `afull` mbarrier.  Output columns beyond
+//     256 (at most 8, the 258-point Neumann axes) are accumulated in FP32 by the same
+//     threads from the values they already hold, and written by them;
+//   * one producer thread streams the basis stage (hi and lo tiles, prepared on the host)
+//     into the basis ring with cp.async.bulk completing on `bfull`;
+//   * one MMA thread waits for both, issues the tcgen05.mma's of the stage into one of two
+//     256-column tensor-memory accumulators and commits them to `sfree` (which releases the
+//     stage's operand slots) and, after a tile's last stage, to `tfull`;
+//   * four epilogue warps drain the other accumulator (tcgen05.ld, 32 lanes = 32 rows per
+//     warp) while the next tile's MMAs run, store it either transposed within planes of R
+//     rows (out[(row/R)*R*P + p*R + row%R]: consecutive lanes on consecutive addresses) or
+//     row-major through a per-warp shared-memory transpose (out[row*P + p]: each row
+//     segment written by consecutive lanes), and release it on `tempty`.
+// Every mbarrier wait is bounded and warp-uniform; a timeout sets a shared flag that ends
+// every role's loop, and *err for the host.  Whatever the path, the MMA thread waits
+// (bounded) for all of its committed MMAs, the producer for its last bulk copy and the
+// converters for their cp.async groups before the tensor memory is freed.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "helm6_internal.h"
@@ -35,20 +43,43 @@ namespace helm6 {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_KT = 32;                   // K per stage
-constexpr int TC_KC = TC_KT / 8;            // core-matrix columns per stage
-constexpr int TC_THREADS = 256;
-constexpr int TC_GMAX = 256;                // output columns of one CTA (MMA N limit)
-constexpr int A_TILE = TC_M * TC_KT * 2;    // bytes of one BF16 term of the data stage
-constexpr int A_LBO = (TC_M / 8) * 128;     // K step of the data stage (one core-matrix column)
+constexpr int TC_KT = 32;                // K per stage
+constexpr int TC_KC = TC_KT / 8;         // core-matrix columns per stage
+constexpr int TC_GMAX = 256;             // output columns of one work item (MMA N limit)
+constexpr int TC_TAILMAX = 8;            // FP32 columns beyond 256 done by the converters
+constexpr int NS = 3;                    // operand ring stages (data hi/lo and basis)
+constexpr int ND = 3;                    // FP32 data ring stages (cp.async in flight)
+constexpr int EPI_WARPS = 4;             // warps 0-3: epilogue (tensor-memory lane quarters)
+constexpr int CONV_WARPS = 4;            // warps 4-7: converters
+constexpr int W_PROD = 8, W_MMA = 9;     // basis producer, MMA issuer + TMEM owner
+constexpr int TC_THREADS = 320;
+constexpr int A_TILE = TC_M * TC_KT * 2;            // bytes of one BF16 term of a data stage
+constexpr int A_STAGE = 2 * A_TILE;                 // hi + lo
+constexpr int A_LBO = (TC_M / 8) * 128;             // K step of the data stage
+constexpr int B_STAGE = 2 * TC_KC * TC_GMAX * 16;   // hi + lo basis, 256 rows
+constexpr int D_STAGE = TC_M * TC_KT * 4;           // FP32 data, 128 B per row
+constexpr int STG_LD = 33;                          // epilogue transpose stride (floats)
+constexpr int OFF_A = 0;
+constexpr int OFF_B = OFF_A + NS * A_STAGE;
+constexpr int OFF_D = OFF_B + NS * B_STAGE;
+constexpr int OFF_T = OFF_D + ND * D_STAGE;
+constexpr int TAIL_FLOATS = TC_TAILMAX * (TC_GMAX + TC_TAILMAX);
+constexpr int OFF_S = OFF_T + TAIL_FLOATS * 4;
+constexpr int OFF_BAR = OFF_S + EPI_WARPS * 32 * STG_LD * 4;
+constexpr int NBAR = 3 * NS + 5;  // afull, bfull, sfree per stage; tfull, tempty per buffer; drain
+constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;  // + alignment of the base to 1024
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+static_assert(OFF_B % 1024 == 0 && OFF_D % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 constexpr int kMaxPolls = 1 << 22;
 
 struct TcArgs {
   const float* in;
   float* out;
-  const uint8_t* W;  // per column group: [kt][term][kc][Npad_g / 8][8 rows][16 B]
+  const uint8_t* W;   // per column group: [kt][term][kc][Npad_g / 8][8 rows][16 B]
+  const float* Bt;    // tail basis rows (FP32, tail x K) or null
   int M_total, K, P, nk, terms, transposed, R;
-  int ngroups, gcols;  // column groups and columns per group (the last may have fewer)
+  int ngroups, gcols, tail, nwork;
   int* err;
 };
 
@@ -68,18 +99,32 @@ __device__ __forceinline__ uint32_t idesc(int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool poll(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, P1;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait by one thread; gives up when the flag is raised by another role.
+__device__ __forceinline__ bool poll1(uint32_t bar, uint32_t parity, volatile int* fail) {
   for (int it = 0; it < kMaxPolls; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
+    if (try_wait(bar, parity)) return true;
+    if ((it & 255) == 255 && *fail) return false;
   }
+  *fail = 1;
   return false;
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the warp takes its answer.
+__device__ __forceinline__ bool pollw(uint32_t bar, uint32_t parity, volatile int* fail, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = poll1(bar, parity, fail) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
@@ -89,233 +134,305 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
-constexpr int A_PER_THREAD = TC_M * TC_KT / 2 / TC_THREADS;  // float pairs per thread per stage (8)
-
-// Stage kt of the data: core matrix cm = 8 warp + i holds rows 8 (cm % 16) .. + 7 and
-// k = 32 kt + 8 (cm / 16) .. + 7; lane l holds row l / 4 and the k pair 2 (l % 4).  Zero
-// outside the field.  Pairs are 8-byte aligned when K is even.
-__device__ __forceinline__ void load_stage(const TcArgs& p, int m0, int kt, int warp, int lane, float2* xr) {
-  const int r8 = lane >> 2, pr = lane & 3;
-#pragma unroll
-  for (int i = 0; i < A_PER_THREAD; ++i) {
-    const int cm = warp * A_PER_THREAD + i;
-    const int row = m0 + 8 * (cm & 15) + r8;
-    const int k = kt * TC_KT + 8 * (cm >> 4) + 2 * pr;
-    float2 v = make_float2(0.f, 0.f);
-    if (row < p.M_total) {
-      const float* src = p.in + (int64_t)row * p.K + k;
-      if (k + 1 < p.K && !(p.K & 1)) {
-        v = __ldg((const float2*)src);
-      } else {
-        if (k < p.K) v.x = __ldg(src);
-        if (k + 1 < p.K) v.y = __ldg(src + 1);
-      }
-    }
-    xr[i] = v;
-  }
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// Split the stage into BF16 hi / lo: core matrix cm at (cm / 16) * A_LBO + (cm % 16) * 128.
-__device__ __forceinline__ void store_stage(uint8_t* sA, int warp, int lane, const float2* xr) {
-#pragma unroll
-  for (int i = 0; i < A_PER_THREAD; ++i) {
-    const int cm = warp * A_PER_THREAD + i;
-    const int off = (cm >> 4) * A_LBO + (cm & 15) * 128 + lane * 4;
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(xr[i].x), h1 = __float2bfloat16_rn(xr[i].y);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(xr[i].x - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(xr[i].y - __bfloat162float(h1));
-    __nv_bfloat162 hh, ll;
-    hh.x = h0;
-    hh.y = h1;
-    ll.x = l0;
-    ll.y = l1;
-    *(__nv_bfloat162*)(sA + off) = hh;
-    *(__nv_bfloat162*)(sA + A_TILE + off) = ll;
-  }
+template <int VEC>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes) {
+  if constexpr (VEC == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(VEC), "r"(bytes)
+                 : "memory");
 }
 
 __host__ __device__ __forceinline__ int round16(int n) { return ((n + 15) / 16) * 16; }
-int tc_nk_(int K) { return (K + TC_KT - 1) / TC_KT; }
 
-__global__ void __launch_bounds__(TC_THREADS, 2) xform_tc_kernel(TcArgs p) {
+// Work item w of the launch: row tile w / ngroups, column group w % ngroups.
+struct Item {
+  int m0, grp, c0, pc, npad;
+};
+__device__ __forceinline__ Item item(const TcArgs& p, int w) {
+  Item it;
+  it.grp = w % p.ngroups;
+  it.m0 = (w / p.ngroups) * TC_M;
+  it.c0 = it.grp * p.gcols;
+  it.pc = min(p.gcols, p.P - it.c0);
+  it.npad = round16(it.pc);
+  return it;
+}
+
+// Split 8 FP32 values into 8 BF16 hi (16 bytes) and 8 BF16 lo.
+__device__ __forceinline__ void split8(const float4& a, const float4& b, uint4& hi, uint4& lo) {
+  const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat162 hh = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+    const float2 hf = __bfloat1622float2(hh);
+    __nv_bfloat162 ll = __floats2bfloat162_rn(x[2 * q] - hf.x, x[2 * q + 1] - hf.y);
+    h[q] = *reinterpret_cast<uint32_t*>(&hh);
+    l[q] = *reinterpret_cast<uint32_t*>(&ll);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int grp = (int)(blockIdx.x % p.ngroups);
-  const int m0 = (int)(blockIdx.x / p.ngroups) * TC_M;
-  const int c0 = grp * p.gcols;                   // first output column of this CTA
-  const int pc = min(p.gcols, p.P - c0);          // its columns
-  const int npad = round16(pc);                   // MMA N
-  const int gpad = round16(p.gcols);              // N of the groups before the last
-  const int bterm = TC_KC * npad * 16;            // basis bytes of one term of one stage
-  const int bstage = 2 * bterm;
-  const int stage_bytes = 2 * A_TILE + 2 * TC_KC * TC_GMAX * 16;  // fixed stride (largest group)
-  uint64_t* bars = (uint64_t*)(smem + 2 * stage_bytes);  // full[0..1], done[0..1], afull[0..1]
-  uint32_t* tslot = (uint32_t*)(bars + 6);
-  int* fail = (int*)(tslot + 1);
-  const uint32_t ncols = npad > 128 ? 256u : (npad > 64 ? 128u : (npad > 32 ? 64u : 32u));
+  uint64_t* bars = (uint64_t*)(smem + OFF_BAR);
+  uint32_t* tslot = (uint32_t*)(smem + OFF_MISC);
+  volatile int* fail = (volatile int*)(tslot + 1);
   const uint32_t bar0 = s_addr(bars);
-  auto full = [&](int s) { return bar0 + 8u * s; };          // basis stage arrived (bulk copy)
-  auto done = [&](int s) { return bar0 + 16u + 8u * s; };    // MMAs of the stage completed
-  auto afull = [&](int s) { return bar0 + 32u + 8u * s; };   // every thread stored its data part
-  // this group's basis: the groups before it hold nk stages of 2 terms of gpad rows each
-  const uint8_t* W = p.W + (size_t)grp * p.nk * 2 * TC_KC * gpad * 16;
+  auto afull = [&](int s) { return bar0 + 8u * s; };             // converters stored the data stage
+  auto bfull = [&](int s) { return bar0 + 8u * (NS + s); };      // basis stage arrived
+  auto sfree = [&](int s) { return bar0 + 8u * (2 * NS + s); };  // the stage's MMAs completed
+  auto tfull = [&](int b) { return bar0 + 8u * (3 * NS + b); };  // accumulator b complete
+  auto tempty = [&](int b) { return bar0 + 8u * (3 * NS + 2 + b); };  // accumulator b drained
+  const uint32_t drain = bar0 + 8u * (3 * NS + 4);                 // every MMA issued completed
 
   if (tid == 0) {
-    for (int s = 0; s < 4; ++s) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s), "r"(1));
-    for (int s = 4; s < 6; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s), "r"(TC_THREADS));
+    for (int s = 0; s < NS; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(afull(s)), "r"(CONV_WARPS));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bfull(s)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sfree(s)), "r"(1));
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tfull(b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tempty(b)), "r"(EPI_WARPS));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(drain), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
     *fail = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tslot)), "r"(ncols));
+  float* sBt = (float*)(smem + OFF_T);
+  for (int i = tid; i < p.tail * p.K; i += TC_THREADS) sBt[i] = p.Bt[i];
+  if (warp == W_MMA) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tslot)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
+  const int nitems = (int)blockIdx.x < p.nwork ? (p.nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nstages = nitems * p.nk;
 
-  const int btx = (p.terms == 3 ? 2 : 1) * bterm;  // bytes the bulk copy brings
-
-  // basis stages 0 and 1 are requested up front; stage kt + 1 is requested as soon as the
-  // MMAs of step kt - 1 have released its buffer (right after step kt is committed)
-  auto issue_b = [&](int kt) {
-    const int st = kt & 1;
-    uint8_t* sB = smem + st * stage_bytes + 2 * A_TILE;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(st)), "r"(btx) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s_addr(sB)),
-        "l"(W + (size_t)kt * bstage), "r"(btx), "r"(full(st))
-        : "memory");
-  };
-  if (tid == 0) {
-    issue_b(0);
-    if (p.nk > 1) issue_b(1);
-  }
-  float2 xr[A_PER_THREAD];
-  load_stage(p, m0, 0, warp, lane, xr);
-  const uint32_t id = idesc(npad);
-
-  int last_commit = -1;  // thread 0: the last stage whose MMAs were committed
-  // No block-wide barrier in the loop: each thread waits only for the MMAs that last read
-  // the stage buffer it is about to overwrite, stores its part of the data stage and
-  // arrives on afull; thread 0 alone waits for afull and the basis before issuing.
-  for (int kt = 0; kt < p.nk; ++kt) {
-    const int st = kt & 1;
-    uint8_t* sA = smem + st * stage_bytes;
-    uint8_t* sB = sA + 2 * A_TILE;
-    if (kt >= 2 && !poll(done(st), ((kt - 2) >> 1) & 1)) {
-      *fail = 1;
-      break;
-    }
-    store_stage(sA, warp, lane, xr);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(afull(st)) : "memory");
-    if (kt + 1 < p.nk) load_stage(p, m0, kt + 1, warp, lane, xr);  // in flight during the MMAs
-    if (tid == 0) {
-      if (!poll(afull(st), (kt >> 1) & 1) || !poll(full(st), (kt >> 1) & 1)) {
-        *fail = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t aHi = s_addr(sA), aLo = aHi + A_TILE, bHi = s_addr(sB), bLo = bHi + bterm;
-      const uint32_t b_lbo = (uint32_t)npad * 16;
-#pragma unroll
-      for (int kk = 0; kk < TC_KT / 16; ++kk) {
-        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t ah = sdesc(aHi + kk * 2 * A_LBO, A_LBO, 128);
-        const uint64_t bh = sdesc(bHi + kk * 2 * b_lbo, b_lbo, 128);
-        mma(tmem, ah, bh, id, acc);
-        if (p.terms >= 2) mma(tmem, sdesc(aLo + kk * 2 * A_LBO, A_LBO, 128), bh, id, 1u);
-        if (p.terms >= 3) mma(tmem, ah, sdesc(bLo + kk * 2 * b_lbo, b_lbo, 128), id, 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(done(st))
-                   : "memory");
-      last_commit = kt;
-      // stage (kt + 1) & 1 was last read by the MMAs of step kt - 1
-      if (kt >= 1 && kt + 1 < p.nk) {
-        if (!poll(done(st ^ 1), ((kt - 1) >> 1) & 1)) {
-          *fail = 1;
-          break;
+  if (warp == W_PROD) {
+    // ---- basis producer ----
+    int last = -1;
+    if (lane == 0) {
+      int g = 0;
+      for (int i = 0; i < nitems && !*fail; ++i) {
+        const Item it = item(p, (int)blockIdx.x + i * (int)gridDim.x);
+        const int gpad = round16(p.gcols);
+        const int bterm = TC_KC * it.npad * 16;
+        const int btx = (p.terms == 3 ? 2 : 1) * bterm;
+        const uint8_t* Wg = p.W + (size_t)it.grp * p.nk * 2 * TC_KC * gpad * 16;
+        for (int kt = 0; kt < p.nk; ++kt, ++g) {
+          const int s = g % NS, u = g / NS;
+          if (u >= 1 && !poll1(sfree(s), (u - 1) & 1, fail)) break;
+          const uint32_t dst = s_addr(smem + OFF_B + s * B_STAGE);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bfull(s)), "r"(btx) : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+              "l"(Wg + (size_t)kt * 2 * bterm), "r"(btx), "r"(bfull(s))
+              : "memory");
+          last = g;
         }
-        issue_b(kt + 1);
+        if (*fail) break;
       }
+      // the last copy must have landed before the CTA ends
+      if (last >= 0) poll1(bfull(last % NS), (last / NS) & 1, fail);
     }
-  }
-
-  // wait for the last committed stage (commits complete in order), also after a timeout
-  // elsewhere: no MMA may still write tensor memory when it is freed below
-  __syncthreads();
-  if (tid == 0 && last_commit >= 0 && !poll(done(last_commit & 1), (last_commit >> 1) & 1)) *fail = 1;
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!*fail) {
-    const int g = warp & 3, h = warp >> 2;
-    const int half = ((npad / 8 + 1) / 2) * 8;  // columns of warp half 0 (multiple of 8)
-    const int cbeg = h ? half : 0, cend = h ? npad : half;
-    const int r = 32 * g + lane;  // row within the tile = tensor-memory lane
-    const int row = m0 + r;
-    const bool live = row < p.M_total;
-    if (p.transposed) {
-      const int plane = row / p.R, rr = row - plane * p.R;
-      const int64_t obase = (int64_t)plane * p.R * p.P + rr;
-      for (int cc = cbeg; cc < cend; cc += 8) {
-        uint32_t v[8];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-            : "r"(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)cc));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (cc + j < pc && live) p.out[obase + (int64_t)(c0 + cc + j) * p.R] = __uint_as_float(v[j]);
+    __syncwarp();
+  } else if (warp == W_MMA) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      int g = 0;
+      for (int i = 0; i < nitems && !*fail; ++i) {
+        const Item it = item(p, (int)blockIdx.x + i * (int)gridDim.x);
+        const int b = i & 1, v = i >> 1;
+        if (v >= 1 && !poll1(tempty(b), (v - 1) & 1, fail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t id = idesc(it.npad);
+        const uint32_t bterm = TC_KC * it.npad * 16, b_lbo = (uint32_t)it.npad * 16;
+        const uint32_t d = tmem + (uint32_t)(b * TC_GMAX);
+        bool ok = true;
+        for (int kt = 0; kt < p.nk; ++kt, ++g) {
+          const int s = g % NS, u = g / NS;
+          if (!poll1(afull(s), u & 1, fail) || !poll1(bfull(s), u & 1, fail)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t aHi = s_addr(smem + OFF_A + s * A_STAGE), aLo = aHi + A_TILE;
+          const uint32_t bHi = s_addr(smem + OFF_B + s * B_STAGE), bLo = bHi + bterm;
+          const int nkk = min(TC_KT / 16, (p.K - kt * TC_KT + 15) / 16);
+          for (int kk = 0; kk < nkk; ++kk) {
+            const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            const uint64_t ah = sdesc(aHi + kk * 2 * A_LBO, A_LBO, 128);
+            const uint64_t bh = sdesc(bHi + kk * 2 * b_lbo, b_lbo, 128);
+            mma(d, ah, bh, id, acc);
+            if (p.terms >= 2) mma(d, sdesc(aLo + kk * 2 * A_LBO, A_LBO, 128), bh, id, 1u);
+            if (p.terms >= 3) mma(d, ah, sdesc(bLo + kk * 2 * b_lbo, b_lbo, 128), id, 1u);
+          }
+          commit(sfree(s));
+        }
+        if (!ok) break;
+        commit(tfull(b));
       }
-    } else {
-      // row-major: 64 rows at a time through shared memory (stride pc + 1), then each warp
-      // copies whole rows of pc floats to out[row * P + c0 ..]
-      float* stile = (float*)smem;
-      const int sld = pc + 1;
-      for (int pass = 0; pass < 2; ++pass) {
-        if ((g >> 1) == pass) {
-          const int rl = r - 64 * pass;
-          // four 8-column loads per wait (faster here; the transposed path above is not)
-          for (int cc = cbeg; cc < cend; cc += 32) {
-            uint32_t v[32];
+      // every MMA issued above has completed before the tensor memory is freed
+      commit(drain);
+      poll1(drain, 0, fail);
+    }
+    __syncwarp();
+  } else if (warp >= EPI_WARPS) {
+    // ---- converters: thread t holds row t of the tile ----
+    const int t = tid - EPI_WARPS * 32;
+    const uint32_t ring = s_addr(smem + OFF_D) + (uint32_t)t * 128;
+    const int sw = t & 7;  // 16-byte chunk swizzle of the private slot (conflict-free reads)
+    float tacc[TC_TAILMAX];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (cc + 8 * q < cend)
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                    : "=r"(v[8 * q]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]), "=r"(v[8 * q + 4]),
-                      "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
-                    : "r"(tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(cc + 8 * q)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    for (int c = 0; c < TC_TAILMAX; ++c) tacc[c] = 0.f;
+    // issue the copies of stage q (work item q / nk, K stage q % nk) into ring slot q % ND
+    auto issue = [&](int q) {
+      if (q < nstages) {
+        const Item it = item(p, (int)blockIdx.x + (q / p.nk) * (int)gridDim.x);
+        const int row = it.m0 + t, k0 = (q % p.nk) * TC_KT;
+        const uint32_t slot = ring + (uint32_t)((q % ND) * D_STAGE);
+        const bool rvalid = row < p.M_total;
+        const float* rsrc = p.in + (rvalid ? (int64_t)row * p.K : 0);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (cc + j < cend && cc + j < pc) stile[rl * sld + cc + j] = __uint_as_float(v[j]);
+        for (int c = 0; c < 128 / VEC; ++c) {
+          const int k = k0 + c * (VEC / 4);
+          const bool valid = rvalid && k < p.K;
+          const int c16 = (c * VEC) / 16, within = (c * VEC) % 16;
+          cp_async<VEC>(slot + (uint32_t)(((c16 ^ sw) << 4) + within), valid ? (const void*)(rsrc + k) : (const void*)p.in,
+                        valid ? VEC : 0);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int q = 0; q < ND; ++q) issue(q);
+    const int rg = t >> 3, r8 = t & 7;
+    for (int g = 0; g < nstages; ++g) {
+      const int s = g % NS, u = g / NS, kt = g % p.nk;
+      asm volatile("cp.async.wait_group %0;" ::"n"(ND - 1) : "memory");
+      if (u >= 1 && !pollw(sfree(s), (u - 1) & 1, fail, lane)) break;
+      const uint8_t* dslot = smem + OFF_D + (size_t)(g % ND) * D_STAGE + (size_t)t * 128;
+      uint8_t* sA = smem + OFF_A + s * A_STAGE;
+      const int k0 = kt * TC_KT;
+#pragma unroll
+      for (int kg = 0; kg < TC_KC; ++kg) {
+        const float4 a = *(const float4*)(dslot + (((2 * kg) ^ sw) << 4));
+        const float4 b = *(const float4*)(dslot + (((2 * kg + 1) ^ sw) << 4));
+        uint4 hi, lo;
+        split8(a, b, hi, lo);
+        const int off = kg * A_LBO + rg * 128 + r8 * 16;
+        *(uint4*)(sA + off) = hi;
+        *(uint4*)(sA + A_TILE + off) = lo;
+        if (p.tail) {
+          const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int c = 0; c < TC_TAILMAX; ++c) {
+            if (c < p.tail) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const int k = k0 + 8 * kg + e;
+                if (k < p.K) tacc[c] = fmaf(x[e], sBt[c * p.K + k], tacc[c]);
+              }
+            }
           }
         }
-        __syncthreads();
-        const int rows = min(64, p.M_total - (m0 + 64 * pass));
-        float* dst = p.out + (int64_t)(m0 + 64 * pass) * p.P + c0;
-        // consecutive lanes on consecutive words: conflict-free reads, 128-byte stores
-        for (int rr = warp; rr < rows; rr += TC_THREADS / 32) {
-          const float* srow = stile + rr * sld;
-          float* drow = dst + (int64_t)rr * p.P;
-          for (int cc = lane; cc < pc; cc += 32) drow[cc] = srow[cc];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(afull(s)) : "memory");
+      issue(g + ND);
+      if (p.tail && kt == p.nk - 1) {
+        const Item it = item(p, (int)blockIdx.x + (g / p.nk) * (int)gridDim.x);
+        const int row = it.m0 + t;
+        if (row < p.M_total) {
+          const int plane = row / p.R, rr = row - plane * p.R;
+          float* o = p.transposed ? p.out + (int64_t)plane * p.R * p.P + rr + (int64_t)TC_GMAX * p.R
+                                  : p.out + (int64_t)row * p.P + TC_GMAX;
+          const int64_t cs = p.transposed ? p.R : 1;
+#pragma unroll
+          for (int c = 0; c < TC_TAILMAX; ++c)
+            if (c < p.tail) o[c * cs] = tacc[c];
         }
-        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < TC_TAILMAX; ++c) tacc[c] = 0.f;
       }
     }
-  } else if (tid == 0) {
-    atomicExch(p.err, 1);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    // ---- epilogue: warp q reads tensor-memory lanes 32 q .. 32 q + 31 (tile rows) ----
+    const int q = warp;
+    float* stg = (float*)(smem + OFF_S) + q * 32 * STG_LD;
+    for (int i = 0; i < nitems; ++i) {
+      const Item it = item(p, (int)blockIdx.x + i * (int)gridDim.x);
+      const int b = i & 1, v = i >> 1;
+      if (!pollw(tfull(b), v & 1, fail, lane)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int row0 = it.m0 + 32 * q;
+      const int row = row0 + lane;
+      const bool live = row < p.M_total;
+      const int nrows = min(32, p.M_total - row0);
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * TC_GMAX);
+      int64_t obase = 0;
+      if (p.transposed) {
+        const int plane = row / p.R, rr = row - plane * p.R;
+        obase = (int64_t)plane * p.R * p.P + rr;
+      }
+      for (int cc = 0; cc < it.npad; cc += 32) {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + (uint32_t)cc));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int ncol = min(32, it.pc - cc);
+        if (p.transposed) {
+          if (live) {
+            float* o = p.out + obase + (int64_t)(it.c0 + cc) * p.R;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < ncol) o[(int64_t)j * p.R] = __uint_as_float(r[j]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * STG_LD + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          if (lane < ncol) {
+            float* o = p.out + (int64_t)row0 * p.P + it.c0 + cc + lane;
+            for (int rr = 0; rr < nrows; ++rr) o[(int64_t)rr * p.P] = stg[rr * STG_LD + lane];
+          }
+          __syncwarp();
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty(b)) : "memory");
+    }
   }
+
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (tid == 0 && *fail) atomicExch(p.err, 1);
+  if (warp == W_MMA) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 uint16_t to_bf16(float f) {
@@ -333,11 +450,10 @@ float from_bf16(uint16_t b) {
   return f;
 }
 
-// Columns beyond the first 256 computed by the FP32 tail kernel (a few only; more take a
-// second tensor-core column group).
-constexpr int TC_TAILMAX = 32;
-constexpr int TC_TAILK = TC_GMAX + TC_TAILMAX;  // longest row on the tail path (square bases: K = P)
-int tc_tail(int P, int K) { return (P > TC_GMAX && P - TC_GMAX <= TC_TAILMAX && K <= TC_TAILK) ? P - TC_GMAX : 0; }
+int tc_nk_(int K) { return (K + TC_KT - 1) / TC_KT; }
+// Output columns beyond the first 256 accumulated in FP32 by the converter threads (a few
+// only, square bases K = P; more take a second tensor-core column group).
+int tc_tail(int P, int K) { return (P > TC_GMAX && P - TC_GMAX <= TC_TAILMAX && K <= TC_GMAX + TC_TAILMAX) ? P - TC_GMAX : 0; }
 int tc_groups(int P, int K) { return tc_tail(P, K) ? 1 : (P + TC_GMAX - 1) / TC_GMAX; }
 int tc_gcols(int P, int K) {
   return tc_tail(P, K) ? TC_GMAX : round16((P + tc_groups(P, K) - 1) / tc_groups(P, K));
@@ -347,76 +463,16 @@ size_t tc_tile_bytes(int P, int K) {
   return (size_t)tc_groups(P, K) * tc_nk_(K) * 2 * TC_KC * tc_gcols(P, K) * 16;
 }
 
-// The last P - 256 output columns: out(row, 256 + c) = sum_k in(row, k) Bt(c, k) in FP32, one
-// warp per row (lanes stride over k, shuffle reduction), Bt staged in shared memory.  TT > 0:
-// that many columns, known at compile time; TT = 0: any T <= TC_TAILMAX.
-template <int TT>
-__global__ void __launch_bounds__(256) xform_tail_kernel(const float* __restrict__ in, float* __restrict__ out,
-                                                         const float* __restrict__ Bt, int M_total, int K, int P,
-                                                         int T_rt, int transposed, int R) {
-  constexpr int TM = TT > 0 ? TT : TC_TAILMAX;
-  const int T = TT > 0 ? TT : T_rt;
-  extern __shared__ float sbt[];
-  for (int i = threadIdx.x; i < T * K; i += blockDim.x) sbt[i] = Bt[i];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t row = (int64_t)blockIdx.x * 8 + warp; row < M_total; row += (int64_t)gridDim.x * 8) {
-    const float* r = in + row * K;
-    float acc[TM];
-#pragma unroll
-    for (int c = 0; c < TM; ++c) acc[c] = 0.f;
-    // the whole row first (K <= 288 on this path: at most 9 values per lane), so that all
-    // of a warp's loads are in flight together
-    float v[TC_TAILK / 32];
-#pragma unroll
-    for (int q = 0; q < TC_TAILK / 32; ++q) {
-      const int k = lane + 32 * q;
-      v[q] = k < K ? __ldg(r + k) : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < TC_TAILK / 32; ++q) {
-      const int k = lane + 32 * q;
-      if (k >= K) break;
-      if constexpr (TT > 0) {
-#pragma unroll
-        for (int c = 0; c < TT; ++c) acc[c] = fmaf(v[q], sbt[c * K + k], acc[c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < TM; ++c)
-          if (c < T) acc[c] = fmaf(v[q], sbt[c * K + k], acc[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < TM; ++c) {
-      if (c >= T) break;
-      float x = acc[c];
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == c) {
-        const int col = TC_GMAX + c;
-        if (transposed) {
-          const int64_t plane = row / R, rr = row - plane * R;
-          out[plane * R * P + (int64_t)col * R + rr] = x;
-        } else {
-          out[row * P + col] = x;
-        }
-      }
-    }
-  }
-}
-
 }  // namespace
 
 int tc_npad(int P) { return round16(P < 16 ? 16 : P); }
 
 int tc_nk(int K) { return (K + TC_KT - 1) / TC_KT; }
 
-// two stages of data (2 x 8 KB) and basis (2 terms x 4 core-matrix columns x 256 rows x 16 B)
-size_t tc_smem_bytes(int) { return 2 * (size_t)(2 * A_TILE + 2 * TC_KC * TC_GMAX * 16) + 64 + 1024; }
-
 // Basis B (P x K, row-major, FP64) as BF16 hi/lo tiles in the kernel's shared-memory
 // layout, per column group g (columns [g G, g G + G), G = tc_gcols(P), rows padded to a
 // multiple of 16): stage kt, term, core-matrix column kc, row n: 16 bytes at
-// ((kt * 2 + term) * 4 + kc) * npad_g * 16 + n * 16.
+// ((kt * 2 + term) * 4 + kc) * npad_g * 16 + n * 16; then the tail rows in FP32.
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out) {
   const int nk = tc_nk(K), ng = tc_groups(P, K), G = tc_gcols(P, K), T = tc_tail(P, K);
   const size_t tiles = tc_tile_bytes(P, K);
@@ -451,16 +507,19 @@ int tc_max_axis() { return 2 * TC_GMAX; }
 int tc_configure() {
   static int done = 0;
   if (done) return HELM6_OK;
-  if (cudaFuncSetAttribute(xform_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(0)) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(xform_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(xform_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(xform_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+          cudaSuccess)
     return HELM6_ERR_CUDA;
   done = 1;
   return HELM6_OK;
 }
 
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s, cudaStream_t aux, cudaEvent_t fork,
-                     cudaEvent_t join) {
+                     int transposed, int R, int* err, cudaStream_t s) {
   TcArgs a;
   a.in = in;
   a.out = out;
@@ -474,39 +533,22 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   a.R = R;
   a.ngroups = tc_groups(P, K);
   a.gcols = tc_gcols(P, K);
+  a.tail = tc_tail(P, K);
+  a.Bt = a.tail ? (const float*)(W + tc_tile_bytes(P, K)) : nullptr;
+  a.nwork = ((M_total + TC_M - 1) / TC_M) * a.ngroups;
   a.err = err;
-  a.P = P;
-  const unsigned grid = (unsigned)(((M_total + TC_M - 1) / TC_M) * a.ngroups);
-  const bool side = tc_tail(P, K) > 0 && aux && fork && join;
-  if (side) {  // fork before the tensor-core kernel so that the tail can start with it
-    cudaEventRecord(fork, s);
-    cudaStreamWaitEvent(aux, fork, 0);
-  }
+  if (a.nwork == 0) return;
+  static int sms = 0;
+  if (!sms) sms = device_sm_count();
+  const unsigned grid = (unsigned)std::min(a.nwork, sms);
   note_launch();
-  xform_tc_kernel<<<grid, TC_THREADS, tc_smem_bytes(0), s>>>(a);
-  const int T = tc_tail(P, K);
-  if (T > 0) {
-    static int sms = 0;
-    if (!sms) sms = device_sm_count();
-    const float* Bt = (const float*)(W + tc_tile_bytes(P, K));
-    note_launch();
-    const size_t sm = (size_t)T * K * sizeof(float);
-    const int g = 8 * sms;
-    // with an auxiliary stream the tail runs beside the tensor-core kernel (both only read
-    // `in`, and write disjoint columns of `out`); s waits for it before any later work
-    cudaStream_t ts = side ? aux : s;
-    switch (T) {
-      case 1: xform_tail_kernel<1><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 2: xform_tail_kernel<2><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 3: xform_tail_kernel<3><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      case 4: xform_tail_kernel<4><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-      default: xform_tail_kernel<0><<<g, 256, sm, ts>>>(in, out, Bt, M_total, K, P, T, transposed, R); break;
-    }
-    if (ts != s) {
-      cudaEventRecord(join, ts);
-      cudaStreamWaitEvent(s, join, 0);
-    }
-  }
+  const uintptr_t ia = (uintptr_t)in;
+  if (K % 4 == 0 && ia % 16 == 0)
+    xform_tc_kernel<16><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+  else if (K % 2 == 0 && ia % 8 == 0)
+    xform_tc_kernel<8><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+  else
+    xform_tc_kernel<4><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
 }
 
 }  // namespace helm6

@@ -31,7 +31,8 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_basis", "h
            "helm6_profile_enable", "helm6_profile_read", "helm6_residual_noalloc", "helm6_set_cnn",
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
            "helm6_cnn_train_step", "helm6_cnn_set_residual_loss", "helm6_cnn_get_params",
-           "helm6_cnn_trainer_destroy", "helm6_solve_batch", "helm6_rhs_separable")
+           "helm6_cnn_trainer_destroy", "helm6_solve_batch", "helm6_rhs_separable",
+           "helm6_lift_dirichlet")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
           "gs_update", "gs_small", "resid64", "other", "cnn")
@@ -129,6 +130,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_cnn_trainer_destroy.restype = None
     lib.helm6_rhs_separable.argtypes = [P, I, C.POINTER(C64), C.POINTER(C64), P]
     lib.helm6_rhs_separable.restype = I
+    lib.helm6_lift_dirichlet.argtypes = [P, I, P, P]
+    lib.helm6_lift_dirichlet.restype = I
     lib.helm6_solve_batch.argtypes = [C.POINTER(P), I, C.POINTER(P), C.POINTER(P), D, I, I, I,
                                       C.POINTER(Stats)]
     lib.helm6_solve_batch.restype = I
@@ -309,6 +312,17 @@ class Solver:
             raise ValueError(f"tables must have shape {(nt, 3, 5, max(self.dims))}, got {tb.shape}")
         _check(self._lib.helm6_rhs_separable(self._ctx, nt, cf.ctypes.data_as(C.POINTER(C64)),
                                              tb.ctypes.data_as(C.POINTER(C64)), _ptr(F)), "helm6_rhs_separable")
+        return F
+
+    def lift_dirichlet(self, face, data, F):
+        """F -= the contribution of Dirichlet values `data` ((my+2) x (mx+2) complex128 CUDA
+        tensor, the face's node layer with its ring) on z face `face` ("z0" or "z1")."""
+        import torch
+        fi = {"z0": 4, "z1": 5}[face]
+        mx, my, _ = self.dims
+        if not isinstance(data, torch.Tensor) or tuple(data.shape) != (my + 2, mx + 2):
+            raise ValueError(f"data must have shape {(my + 2, mx + 2)}")
+        _check(self._lib.helm6_lift_dirichlet(self._ctx, fi, _ptr(data), _ptr(F)), "helm6_lift_dirichlet")
         return F
 
     def rhs_gaussians(self, sources, noise=None, F=None):
