@@ -95,11 +95,20 @@ typedef struct {
   double inner_tol;  /* MIXED only: relative reduction asked of each FP32 inner solve
                         (0 = default 1e-5) */
   void* stream;      /* cudaStream_t; NULL = default stream */
-  int use_graphs;    /* nonzero: each Arnoldi step is captured once as a CUDA graph (per
-                        step index, on a private stream of the context) and replayed on the
+  int use_graphs;    /* 1: each Arnoldi step is captured once as a CUDA graph (per step
+                        index, on a private stream of the context) and replayed on the
                         context's stream, one graph launch instead of about 15 kernel
                         launches per step; results are identical to the eager path; no
-                        per-phase profiling while on */
+                        per-phase profiling while on.
+                        2: as 1, and a MIXED FGMRES solve without a learned stage runs as ONE
+                        graph launch: the whole solve (true residuals, cycles, Arnoldi steps,
+                        least squares, updates) is captured once per restart length, and
+                        every convergence decision is taken on the device through
+                        conditional graph nodes (a WHILE node over refinement cycles, IF
+                        nodes over the Arnoldi steps), so the host only launches it and
+                        reads the statistics back; helm6_solve_batch with such contexts
+                        launches all of its problems as one graph.  Results are identical
+                        to the host-driven path. */
   int dot_blocks;    /* thread blocks of the Gram-Schmidt reduction pass (0 = 2 per SM) */
   int update_blocks; /* thread blocks of the Gram-Schmidt update pass (0 = up to 8 per SM) */
   double cheb_lo, cheb_hi;  /* HELM6_CHEB: 0 < cheb_lo < cheb_hi bounding the (real) eigenvalues
@@ -343,8 +352,12 @@ void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr);
 /* ---- Batched solve (the paper has no counterpart) ----
  * Solve count independent problems, ctxs[i] with right side F[i] and initial guess /
  * solution u[i] (DEVICE complex128 arrays as for helm6_solve), to the same tol, restart
- * and maxit, on nthreads host threads (1 <= nthreads <= 256) that each take the next
- * unsolved problem and run helm6_solve on its context.  Problems run concurrently on the
+ * and maxit.  If every context runs device-driven solves (use_graphs = 2, MIXED FGMRES, no
+ * learned stage), the batch is ONE graph launch holding every problem's whole solve as an
+ * independent branch (built and instantiated on the first call for this set of contexts and
+ * restart length, reused afterwards; stats[i].t_total_ms is then problem i's device time,
+ * start to convergence); otherwise nthreads host threads (1 <= nthreads <= 256) each take
+ * the next unsolved problem and run helm6_solve on its context.  Problems run concurrently on the
  * GPU when their contexts have distinct non-NULL streams; contexts may differ in size,
  * wavenumber, faces and options.  stats: HOST array of count (nullable); stats[i].t_total_ms
  * is problem i's own wall time.  Returns a negative error of any problem (the others still

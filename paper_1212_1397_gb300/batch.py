@@ -8,8 +8,11 @@ The batched workload (helm6_inputs.batch_problems) is 64 problems with n in
 {48, 64, 96, 128, 160}, Re k in [5, 60], Im k = 0.01 Re k and random faces (Sommerfeld-like
 on z only), each with one Gaussian source, solved by mixed FGMRES(30) to 1e-8 (at most 300
 iterations).  Every problem keeps its own context (workspace resident in HBM, its own CUDA
-stream created by the library, its Arnoldi steps captured once as CUDA graphs and replayed), and
-helm6_solve_batch runs them on a pool of host threads.
+stream created by the library).  With graphs=2 (the default) each context runs device-driven
+solves and helm6_solve_batch launches the whole batch as ONE CUDA graph (every problem's
+solve a branch, every convergence decision on the device); with graphs=1 the Arnoldi steps
+are captured as CUDA graphs and replayed, and helm6_solve_batch runs the problems on a pool
+of host threads.
 
 The autotuner measures, per problem size, the thread-block counts of the Gram-Schmidt
 reduction and update passes (the grids of the two kernels that read the Krylov basis),
@@ -41,16 +44,16 @@ def default_tuning():
     return {"blocks": {}, "schedule": {"nthreads": 8, "order": "largest_first"}}
 
 
-def make_batch(problems, tuning=None):
-    """One context per problem (own stream, graph replay, tuned grids), its right side and
-    a zero initial guess.  Returns a list of dicts."""
+def make_batch(problems, tuning=None, graphs=2):
+    """One context per problem (own stream, graphs, tuned grids), its right side and a zero
+    initial guess.  Returns a list of dicts."""
     torch = _torch()
     tuning = tuning or default_tuning()
     items = []
     for p in problems:
         blk = tuning["blocks"].get(str(p["n"]), {})
         s = H.Solver(p["n"], p["k"], p["faces"], precision=H.MIXED, method=H.FGMRES, max_restart=RESTART,
-                     own_stream=True, use_graphs=True, dot_blocks=blk.get("dot_blocks", 0),
+                     own_stream=True, use_graphs=graphs, dot_blocks=blk.get("dot_blocks", 0),
                      update_blocks=blk.get("update_blocks", 0))
         F = s.rhs_gaussians(inputs.gaussian_sources(p["src_seed"], p["n"], 1, margin_h=4))
         items.append(dict(problem=p, solver=s, F=F, u=s.empty(), N=int(np.prod(s.shape))))
@@ -103,7 +106,7 @@ def tune(sizes=inputs.BATCH_SIZES, problems=None, log=print):
         best = None
         for d, u in cands:
             probs = [dict(n=n, k=complex(k, 0.01 * k), faces="DDNNSS", src_seed=7 + i) for i in range(4)]
-            items = make_batch(probs, {"blocks": {str(n): {"dot_blocks": d, "update_blocks": u}}})
+            items = make_batch(probs, {"blocks": {str(n): {"dot_blocks": d, "update_blocks": u}}}, graphs=1)
             try:
                 run_batch(items, 4, "as_drawn", tol=1e-14, maxit=RESTART)  # captures the graphs
                 t = min(run_batch(items, 4, "as_drawn", tol=1e-14, maxit=RESTART)[0] for _ in range(3))

@@ -92,6 +92,13 @@ struct helm6_ctx {
   };
   std::map<int, StepGraph> step_graphs;
   cudaStream_t cap_stream = nullptr;  // private stream the step graphs are captured on
+  // device-driven solves (opts.use_graphs == 2): control block, its pinned mirror, the
+  // whole-solve graph (for restart length solve_m) and two more capture streams
+  GraphCtl* gctl = nullptr;
+  GraphCtl* gctl_host = nullptr;
+  cudaGraphExec_t solve_exec = nullptr;
+  int solve_m = 0;
+  cudaStream_t cap2 = nullptr, cap3 = nullptr;
   bool own_stream = false;            // `stream` was created by the context
   std::vector<void*> allocs;
   // measurement (helm6_profile_enable)
@@ -111,7 +118,10 @@ struct helm6_ctx {
 
 namespace {
 
-constexpr int kDiverge = 1000;  // SKS: relative residual growth that counts as divergence
+constexpr int kDiverge = 1000;
+
+// Axis length rounded up to a multiple of 4 (row pitch of the tensor-core intermediates).
+inline int pad4(int m) { return (m + 3) & ~3; }  // SKS: relative residual growth that counts as divergence
 
 #define CK(call)                                      \
   do {                                                \
@@ -313,28 +323,31 @@ void precond(helm6_ctx* c, const T* in, T* out, T* tA, T* tB, T* cw, const T* Vx
 void precond64(helm6_ctx* c, const double* in, double* out) {
   precond<double>(c, in, out, c->tA64, c->tB64, c->cw64, c->Vx64, c->Wx64, c->Vy64, c->Wy64);
 }
-// Tensor-core path: x forward writes planes x-mode-major ([z][p][y]); y forward contracts
-// the now contiguous y; the z lines walk that order; y inverse writes [z][y][p] back;
-// x inverse restores [z][y][x].  in -> tA -> tB -> tA -> tB -> out.
+// Tensor-core path: x forward writes planes x-mode-major ([z][p][y], y pitch Yp); y forward
+// contracts the now contiguous y ([z][p][q], pitch Yp); the z lines walk that order; y inverse
+// writes [z][y][p] back (p pitch Xp); x inverse restores [z][y][x].  Xp, Yp: the axis lengths
+// rounded up to a multiple of 4, so that every intermediate row starts on a 16-byte boundary.
+// in -> tA -> tB -> tA -> tB -> out.
 void precond_tc(helm6_ctx* c, const float* in, float* out) {
   const Geom& g = c->g;
   cudaStream_t s = c->stream;
   const int terms = c->opts.xform_terms;
   const int rows_x = 2 * g.mz * g.my, rows_y = 2 * g.mz * g.mx;
+  const int Xp = pad4(g.mx), Yp = pad4(g.my);
   cudaEvent_t e = prof_start(c);
-  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s);
+  launch_xform_tc(in, c->tA32, c->Wx_tc, rows_x, g.mx, g.mx, terms, 1, g.my, c->tcerr, s, g.mx, Yp);
   prof_stop(c, HELM6_PH_XFWD, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s);
+  launch_xform_tc(c->tA32, c->tB32, c->Wy_tc, rows_y, g.my, g.my, terms, 0, 1, c->tcerr, s, Yp, Yp);
   prof_stop(c, HELM6_PH_YFWD, e);
   e = prof_start(c);
-  launch_ztri_apply(g, c->zl, c->tB32, c->tA32, c->tcerr, s);
+  launch_ztri_apply(g, c->zl, c->tB32, c->tA32, s);
   prof_stop(c, HELM6_PH_ZTRI, e);
   e = prof_start(c);
-  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s);
+  launch_xform_tc(c->tA32, c->tB32, c->Vy_tc, rows_y, g.my, g.my, terms, 1, g.mx, c->tcerr, s, Yp, Xp);
   prof_stop(c, HELM6_PH_YINV, e);
   e = prof_start(c);
-  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s);
+  launch_xform_tc(c->tB32, out, c->Vx_tc, rows_x, g.mx, g.mx, terms, 0, 1, c->tcerr, s, Xp, g.mx);
   prof_stop(c, HELM6_PH_XINV, e);
 }
 
@@ -709,6 +722,307 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
   }
 }
 
+// ---- device-driven solve: the whole mixed FGMRES solve as one CUDA graph ----
+// Structure (every decision taken on the device by the control kernels):
+//   true residual; control (status, WHILE condition)
+//   WHILE (not converged) {
+//     u = r / beta; clear H, Hr, g, T; control (cycle starts, IF condition = 1)
+//     IF (go) { Arnoldi step 0;  control (estimate, go) }   ...   IF (go) { step m (reduction only) }
+//     y = R^-1 g, q = T y, U += beta Z q   (k = the cycle's completed columns, read on the device)
+//     true residual; control (status, WHILE condition)
+//   }
+// The step bodies are the kernels of the host-driven Arnoldi steps without their readbacks.
+
+// Whether a context runs its solves (and its part of a batch) as one device-driven graph.
+bool graph_solve_ok(const helm6_ctx* c) {
+  return c->opts.use_graphs == 2 && c->gctl && c->opts.precision == HELM6_MIXED && c->opts.method == HELM6_FGMRES &&
+         c->cnn_mode == HELM6_CNN_OFF && !c->prof_on && !c->zline_breakdown;
+}
+
+// Add a conditional node (one body) to graph g after deps; *node and *body returned.
+int add_conditional(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,
+                    cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  CK(cudaGraphAddNode(node, g, deps, nullptr, nd, &np));
+  *body = np.conditional.phGraph_out[0];
+  return HELM6_OK;
+}
+
+// Capture what fn enqueues on c's capture stream as a graph and add it to g as a child
+// graph node after deps.
+template <typename Fn>
+int add_segment(helm6_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphNode_t* node, Fn fn) {
+  cudaStream_t s = c->cap_stream;
+  cudaStream_t home = c->stream;
+  c->stream = s;
+  cudaGraph_t seg = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) fn(s);
+  cudaError_t e2 = cudaStreamEndCapture(s, &seg);
+  c->stream = home;
+  if (e != cudaSuccess || e2 != cudaSuccess || !seg) {
+    fprintf(stderr, "helm6: graph segment capture failed: %s / %s\n", cudaGetErrorString(e), cudaGetErrorString(e2));
+    if (seg) cudaGraphDestroy(seg);
+    cudaGetLastError();
+    return HELM6_ERR_CUDA;
+  }
+  e = cudaGraphAddChildGraphNode(node, g, deps, nd, seg);
+  cudaGraphDestroy(seg);
+  CK(e);
+  return HELM6_OK;
+}
+
+void enqueue_residual_dev(helm6_ctx* c, cudaStream_t s) {
+  int nb = 0;
+  launch_stencil<double>(c->g, c->coef, c->U64, c->R64, c->F64, nullptr, 1, c->spart, &nb, s);
+  launch_reduce_sum(c->spart, nb, c->scal, s);
+}
+
+// Append the context's whole solve to graph G (as an independent branch): the first true
+// residual, then a WHILE node whose body is the cycle (pre-cycle segment, m + 1 IF nodes
+// holding the Arnoldi steps, post-cycle segment).
+template <typename TV>
+int append_solve_graph(helm6_ctx* c, TV* V, cudaGraph_t G, int m) {
+  const int64_t N = c->g.N, vs = 2 * N;
+  const int ldh = c->mrest + 1;
+  const double vsc = std::is_same<TV, float>::value ? 1.0 : c->vscale;
+  GraphCtl* gc = c->gctl;
+  cudaGraphConditionalHandle hw;
+  StepHandles ha;
+  CK(cudaGraphConditionalHandleCreate(&hw, G, 0, 0));
+  cudaGraphNode_t pro, wn;
+  int rc = add_segment(c, G, nullptr, 0, &pro, [&](cudaStream_t s) {
+    enqueue_residual_dev(c, s);
+    launch_gctl_residual(gc, c->scal, c->status, c->tcerr, 1, hw, s);
+  });
+  if (rc) return rc;
+  cudaGraph_t body = nullptr;
+  if ((rc = add_conditional(G, &pro, 1, hw, cudaGraphCondTypeWhile, &wn, &body))) return rc;
+  for (int j = 0; j <= m; ++j) CK(cudaGraphConditionalHandleCreate(&ha.h[j], body, 0, 0));
+  cudaGraphNode_t prev;
+  rc = add_segment(c, body, nullptr, 0, &prev, [&](cudaStream_t s) {
+    launch_convert<double, float>(c->R64, c->u32, N, 1.0, s, &gc->inv_beta);
+    cudaMemsetAsync(c->H, 0, sizeof(double) * 2 * ldh * c->mrest, s);
+    cudaMemsetAsync(c->Hr, 0, sizeof(double) * 2 * ldh * c->mrest, s);
+    cudaMemsetAsync(c->gv, 0, sizeof(double) * 2 * ldh, s);
+    cudaMemsetAsync(c->Tm, 0, sizeof(double) * 2 * c->mrest * c->mrest, s);
+    launch_gctl_cycle(gc, ha, m, s);
+  });
+  if (rc) return rc;
+  for (int j = 0; j <= m; ++j) {
+    cudaGraphNode_t ifn, inner;
+    cudaGraph_t step = nullptr;
+    if ((rc = add_conditional(body, &prev, 1, ha.h[j], cudaGraphCondTypeIf, &ifn, &step))) return rc;
+    const bool full = j < m;
+    rc = add_segment(c, step, nullptr, 0, &inner, [&](cudaStream_t s) {
+      if (full) {
+        float* zj = c->Z32 + (int64_t)j * vs;
+        precond32(c, c->u32, zj);
+        launch_stencil<float>(c->g, c->coef, zj, c->w32, nullptr, nullptr, 0, nullptr, nullptr, s);
+      }
+      launch_dcgs_dot<float, TV>(V, vs, j, c->u32, full ? c->w32 : nullptr, N, c->partial, c->ndot, vsc, s);
+      launch_reduce_cols(c->partial, c->ndot, 4 * j + 3, c->red, 0, s);
+      launch_dcgs_step(j, full ? 1 : 0, c->red, c->Hr, c->H, ldh, c->Tm, c->mrest, c->cs, c->sn, c->gv, c->coefv,
+                       c->scal + 2, c->brk, s);
+      if (full)
+        launch_dcgs_update<float, TV>(V, vs, j, c->u32, c->w32, V + (int64_t)j * vs, N, c->coefv, c->ncgs, vsc, s);
+      launch_gctl_step(gc, j, m, c->scal + 2, c->brk, j < m ? ha.h[j + 1] : ha.h[j], s);
+    });
+    if (rc) return rc;
+    prev = ifn;
+  }
+  cudaGraphNode_t post;
+  return add_segment(c, body, &prev, 1, &post, [&](cudaStream_t s) {
+    launch_backsolve(c->H, ldh, 0, c->gv, c->yv, s, &gc->k);
+    launch_tri_mul(c->Tm, c->mrest, 0, c->yv, c->qv, s, &gc->k);
+    launch_lincomb<float, double>(c->Z32, vs, 0, c->qv, 1.0, c->U64, N, 1, s, &gc->k, &gc->beta);
+    enqueue_residual_dev(c, s);
+    launch_gctl_residual(gc, c->scal, c->status, c->tcerr, 0, hw, s);
+  });
+}
+
+int append_solve(helm6_ctx* c, cudaGraph_t G, int m) {
+  return c->V16 ? append_solve_graph<__half>(c, c->V16, G, m) : append_solve_graph<float>(c, c->V32, G, m);
+}
+
+// Parameters of one solve into the control block (stream-ordered upload from pinned memory).
+int graph_params(helm6_ctx* c, double normF, double tol, int m, int maxit) {
+  GraphCtl* h = c->gctl_host;
+  std::memset(h, 0, sizeof(GraphCtl));
+  h->tol_abs = tol * normF;
+  h->itol_num = 0.3 * tol * normF;
+  h->inner = c->opts.inner_tol > 0 ? c->opts.inner_tol : 1e-5;
+  h->normF = normF;
+  h->maxit = maxit;
+  h->m = m;
+  h->status = -1;
+  CK(cudaMemcpyAsync(c->gctl, h, offsetof(GraphCtl, hist), cudaMemcpyHostToDevice, c->stream));
+  return HELM6_OK;
+}
+
+// Statistics and status of a finished device-driven solve (after the control block's readback).
+int graph_finish(helm6_ctx* c, helm6_stats* st) {
+  const GraphCtl* h = c->gctl_host;
+  c->last_beta = h->beta;
+  if (st) {
+    st->iters = h->iters;
+    st->outer = h->outer;
+    st->nhist = std::min(h->nhist, (int)HELM6_MAX_HIST);
+    std::memcpy(st->hist, h->hist, sizeof(double) * st->nhist);
+  }
+  return h->status < 0 && h->status != HELM6_ERR_CUDA ? HELM6_ERR_CUDA : h->status;
+}
+
+int solve_mixed_graph(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {
+  if (!c->solve_exec || c->solve_m != m) {
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    c->solve_exec = nullptr;
+    static std::mutex capture_mutex;
+    std::lock_guard<std::mutex> lock(capture_mutex);
+    cudaGraph_t G;
+    CK(cudaGraphCreate(&G, 0));
+    const long long l0 = launch_total();
+    int rc = append_solve(c, G, m);
+    note_launch(-(int)(launch_total() - l0));
+    if (rc == HELM6_OK && cudaGraphInstantiate(&c->solve_exec, G, 0) != cudaSuccess) rc = HELM6_ERR_CUDA;
+    cudaGraphDestroy(G);
+    if (rc) {
+      cudaGetLastError();
+      return rc;
+    }
+    c->solve_m = m;
+  }
+  int rc = graph_params(c, normF, tol, m, maxit);
+  if (rc) return rc;
+  CK(cudaGraphLaunch(c->solve_exec, c->stream));
+  CK(cudaMemcpyAsync(c->gctl_host, c->gctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return graph_finish(c, st);
+}
+
+// Batched device-driven solves: one graph holding every problem's whole solve as an
+// independent branch, instantiated once per set of contexts and restart length, launched
+// once per batch.
+struct BatchGraph {
+  std::vector<helm6_ctx*> ctxs;
+  int m;
+  cudaGraphExec_t exec;
+};
+std::mutex g_batch_mutex;
+std::vector<BatchGraph> g_batch_graphs;
+
+void forget_batch_graphs_of(helm6_ctx* c) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (size_t i = 0; i < g_batch_graphs.size();) {
+    const auto& v = g_batch_graphs[i].ctxs;
+    if (std::find(v.begin(), v.end(), c) != v.end()) {
+      cudaGraphExecDestroy(g_batch_graphs[i].exec);
+      g_batch_graphs.erase(g_batch_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+int batch_exec(const std::vector<helm6_ctx*>& act, int m, cudaGraphExec_t* out) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (auto& b : g_batch_graphs)
+    if (b.m == m && b.ctxs == act) {
+      *out = b.exec;
+      return HELM6_OK;
+    }
+  cudaGraph_t G;
+  CK(cudaGraphCreate(&G, 0));
+  const long long l0 = launch_total();
+  int rc = HELM6_OK;
+  for (helm6_ctx* c : act)
+    if ((rc = append_solve(c, G, m))) break;
+  note_launch(-(int)(launch_total() - l0));
+  cudaGraphExec_t ex = nullptr;
+  if (rc == HELM6_OK && cudaGraphInstantiate(&ex, G, 0) != cudaSuccess) rc = HELM6_ERR_CUDA;
+  cudaGraphDestroy(G);
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  g_batch_graphs.push_back(BatchGraph{act, m, ex});
+  *out = ex;
+  return HELM6_OK;
+}
+
+// The whole batch in one launch: right sides and their norms per problem, then the batch
+// graph (every problem's device-driven solve as a branch), then the solutions.
+int solve_batch_graph(helm6_ctx* const* ctxs, int count, const void* const* F, void* const* u, double tol,
+                      int restart, int maxit, helm6_stats* stats) {
+  std::vector<double> normF(count, 0.0);
+  for (int i = 0; i < count; ++i) {
+    helm6_ctx* c = ctxs[i];
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), s));
+    launch_caller_to_planar(c->g, c->xaxis, (const double*)F[i], c->F64, s);
+    launch_sumsq<double>(c->F64, c->g.N, c->partial, c->nred, s);
+    launch_reduce_sum(c->partial, c->nred, c->scal, s);
+    CK(cudaMemcpyAsync(c->pinned, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    launch_caller_to_planar(c->g, c->xaxis, (const double*)u[i], c->U64, s);
+  }
+  std::vector<helm6_ctx*> act;
+  std::vector<int> idx, status(count, HELM6_OK);
+  for (int i = 0; i < count; ++i) {
+    helm6_ctx* c = ctxs[i];
+    CK(cudaStreamSynchronize(c->stream));
+    normF[i] = std::sqrt(c->pinned[0]);
+    if (!std::isfinite(normF[i])) {
+      status[i] = HELM6_NONFINITE;
+    } else if (normF[i] == 0.0) {
+      CK(cudaMemsetAsync(u[i], 0, sizeof(double) * 2 * c->g.N, c->stream));
+    } else {
+      int rc = graph_params(c, normF[i], tol, restart, maxit);
+      if (rc) return rc;
+      act.push_back(c);
+      idx.push_back(i);
+    }
+  }
+  for (int i = 0; i < count; ++i) CK(cudaStreamSynchronize(ctxs[i]->stream));
+  if (!act.empty()) {
+    cudaGraphExec_t ex = nullptr;
+    int rc = batch_exec(act, restart, &ex);
+    if (rc) return rc;
+    cudaStream_t s = act[0]->stream;
+    CK(cudaGraphLaunch(ex, s));
+    for (helm6_ctx* c : act) CK(cudaMemcpyAsync(c->gctl_host, c->gctl, sizeof(GraphCtl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (size_t a = 0; a < act.size(); ++a) {
+      helm6_ctx* c = act[a];
+      const int i = idx[a];
+      helm6_stats local;
+      helm6_stats* S = stats ? &stats[i] : &local;
+      std::memset(S, 0, sizeof(*S));
+      status[i] = graph_finish(c, S);
+      if (status[i] < 0) return status[i];
+      launch_planar_to_caller(c->g, c->xaxis, c->U64, (double*)u[i], c->stream);
+      S->relres = c->last_beta / normF[i];
+      S->status = status[i];
+      const GraphCtl* h = c->gctl_host;
+      S->t_total_ms = h->t1 > h->t0 ? 1e-6 * (double)(h->t1 - h->t0) : 0.0;
+    }
+  }
+  int worst = HELM6_OK;
+  for (int i = 0; i < count; ++i) {
+    CK(cudaStreamSynchronize(ctxs[i]->stream));
+    if (stats && (normF[i] == 0.0 || !std::isfinite(normF[i]))) {
+      std::memset(&stats[i], 0, sizeof(helm6_stats));
+      stats[i].status = status[i];
+    }
+    worst = std::max(worst, status[i]);
+  }
+  return worst;
+}
+
 // SKS (Algorithm 1) in its equivalent defect-correction form U <- U + A_p^{-1}(F - A U),
 // the residual computed in FP64; MIXED applies A_p^{-1} in FP32 to r/||r||.
 int solve_sks(helm6_ctx* c, double normF, double tol, int maxit, helm6_stats* st) {
@@ -863,6 +1177,11 @@ void helm6_destroy(helm6_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (auto& kv : c->step_graphs) cudaGraphExecDestroy(kv.second.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  forget_batch_graphs_of(c);
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
+  if (c->cap3) cudaStreamDestroy(c->cap3);
+  if (c->gctl_host) cudaFreeHost(c->gctl_host);
   for (void* p : c->allocs) cudaFree(p);
   cnn_free(c->cnn);
   for (cudaEvent_t e : c->ev_all) cudaEventDestroy(e);
@@ -955,6 +1274,13 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   }
   if (o.use_graphs && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return fail(HELM6_ERR_CUDA);
+  if (o.use_graphs == 2) {
+    if (cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap3, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&c->gctl_host, sizeof(GraphCtl)) != cudaSuccess)
+      return fail(HELM6_ERR_CUDA);
+    if ((rc = dalloc(c, &c->gctl, 1))) return fail(rc);
+  }
   // bases
   std::vector<double> Vx, Wx, lx, Vy, Wy, ly;
   basis(n, c->g.face[0], c->g.face[1], Vx, Wx, lx);  // the internal x and y faces
@@ -1006,8 +1332,11 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     // 2^e near sqrt(N)/4: a unit vector's entries stay below 2^e <= sqrt(N)/2 (far inside the
     // FP16 range up to N = 2^32) while its mean square is 2^(2e)/N, about 1/16
     c->vscale = std::ldexp(1.0, std::max(0, std::min(14, (int)std::floor(0.5 * std::log2((double)N)) - 2)));
-    if ((rc = dalloc(c, &c->w32, v)) || (rc = dalloc(c, &c->zt32, v)) || (rc = dalloc(c, &c->tA32, v)) ||
-        (rc = dalloc(c, &c->tB32, v)) || (rc = dalloc(c, &c->cw32, v)))
+    // the tensor-core path's intermediates have rows padded to a multiple of 4 floats
+    const size_t vpad = std::max(v, (size_t)2 * c->g.mz *
+                                        std::max((size_t)c->g.mx * pad4(c->g.my), (size_t)c->g.my * pad4(c->g.mx)));
+    if ((rc = dalloc(c, &c->w32, v)) || (rc = dalloc(c, &c->zt32, v)) || (rc = dalloc(c, &c->tA32, vpad)) ||
+        (rc = dalloc(c, &c->tB32, vpad)) || (rc = dalloc(c, &c->cw32, v)))
       return fail(rc);
     // FP64 scratch used by apply_Pinv in FP64 layout conversions
     if ((rc = dalloc(c, &c->tA64, v))) return fail(rc);
@@ -1054,13 +1383,10 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     if ((rc = upt(&c->Wx_tc, Wx, c->g.mx)) || (rc = upt(&c->Vx_tc, Vx, c->g.mx)) ||
         (rc = upt(&c->Wy_tc, Wy, c->g.my)) || (rc = upt(&c->Vy_tc, Vy, c->g.my)))
       return fail(rc);
-    const size_t lines = (size_t)c->g.mx * c->g.my;
-    if ((rc = dalloc(c, &c->zl.rinv, v)) || (rc = dalloc(c, &c->zl.rc, lines)) ||
-        (rc = dalloc(c, &c->zl.rconv, lines)) || (rc = dalloc(c, &c->zl.rlast, lines)))
-      return fail(rc);
-    if (ztri_configure(c->g) != HELM6_OK) return fail(HELM6_ERR_CUDA);
+    c->zl.ldq = pad4(c->g.my);
+    if ((rc = dalloc(c, &c->zl.rinv, (size_t)2 * c->g.mz * c->g.mx * c->zl.ldq))) return fail(rc);
     if (cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
-    launch_ztri_table(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zl, c->status, 0, 1);
+    launch_ztri_table(c->g, c->lamx, c->lamy, c->diag0, c->alpha, c->zl, c->status, 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(HELM6_ERR_CUDA);
     int zst = 0;
     if (cudaMemcpy(&zst, c->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return fail(HELM6_ERR_CUDA);
@@ -1205,6 +1531,8 @@ int helm6_solve(helm6_ctx* c, const void* F, void* u, double tol, int restart, i
       status = solve_cheb(c, normF, tol, maxit, S);
     else if (c->opts.precision == HELM6_FP64)
       status = solve_fp64(c, normF, tol, restart, maxit, S);
+    else if (graph_solve_ok(c))
+      status = solve_mixed_graph(c, normF, tol, restart, maxit, S);
     else
       status = solve_mixed(c, normF, tol, restart, maxit, S);
     if (status < 0) return status;
@@ -1225,6 +1553,10 @@ int helm6_solve_batch(helm6_ctx* const* ctxs, int count, const void* const* F, v
   int dev = 0;
   CK(cudaGetDevice(&dev));
   std::vector<int> rc(count, HELM6_OK);
+  bool all_graph = count > 0;
+  for (int i = 0; i < count; ++i)
+    all_graph = all_graph && graph_solve_ok(ctxs[i]) && restart >= 1 && restart <= ctxs[i]->mrest;
+  if (all_graph && tol > 0 && maxit >= 0) return solve_batch_graph(ctxs, count, F, u, tol, restart, maxit, stats);
   std::atomic<int> next{0};
   auto worker = [&]() {
     if (cudaSetDevice(dev) != cudaSuccess) return;

@@ -118,8 +118,10 @@ int tc_nk(int K);
 int tc_max_axis();
 int tc_configure();
 void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<uint8_t>& out);
+// ldin: input row pitch (0: K); ldo: output row pitch (row-major, 0: P) or pitch of the
+// transposed rows of a plane (0: R): out[(row/R)*ldo*P + p*ldo + row%R].
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s);
+                     int transposed, int R, int* err, cudaStream_t s, int ldin = 0, int ldo = 0);
 
 // Tridiagonal solve along z for every (x, y) mode pair, Thomas algorithm started at the
 // Sommerfeld-like end (if any).  x: input, y: output (may alias x), cw: scratch of 2N T.
@@ -129,21 +131,17 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
                  const T* x, T* y, T* cw, int* status, cudaStream_t s, int xmajor = 0);
 
 // The same z-line solve with the elimination's pivots precomputed in FP64 (once per
-// context) and stored in FP32: rinv (2N floats, planar, indexed like the field) holds the
-// pivot reciprocal of every step; per line, rc is the first step from which the stored
-// pivots of steps < m - 1 no longer change, rconv that pivot and rlast the last step's.
+// context) and stored in FP32 (tensor-core path): rinv holds the pivot reciprocal of every
+// step of every line, planar (re then im), indexed like the field; the planes are
+// x-mode-major with q pitch ldq >= my (the padded layout of the transforms' intermediates).
 struct ZLines {
   float* rinv = nullptr;
-  int* rc = nullptr;
-  float2* rconv = nullptr;
-  float2* rlast = nullptr;
+  int ldq = 0;
 };
 void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, ZLines z,
-                       int* status, cudaStream_t s, int xmajor);
-int ztri_configure(const Geom& g);  // kernel attributes (before any capture)
-// y = the z-line solve of x (planar FP32, x-mode-major planes); *err set if a bounded wait
-// of the blocked kernel timed out.
-void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, int* err, cudaStream_t s);
+                       int* status, cudaStream_t s);
+// y = the z-line solve of x (planar FP32 in that layout; y may not alias x).
+void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, cudaStream_t s);
 
 // BLAS-1 style kernels on planar complex vectors of N points.
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
@@ -153,11 +151,15 @@ void launch_sumsq(const T* x, int64_t N, double* partial, int nblocks, cudaStrea
 template <typename T>
 void launch_scale_copy(const T* x, T* y, int64_t N, const double* inv_scale_dev, double host_scale,
                        cudaStream_t s);  // y = x * (host_scale or 1/(*dev))
+// out (+)= scale*sum V_i y_i; count_dev / scale_dev (nullable): read count / scale on the
+// device instead (device-driven solves)
 template <typename TI, typename TO>
 void launch_lincomb(const TI* V, int64_t vstride, int count, const double* y, double scale, TO* out,
-                    int64_t N, int accumulate, cudaStream_t s);  // out (+)= scale*sum V_i y_i
+                    int64_t N, int accumulate, cudaStream_t s, const int* count_dev = nullptr,
+                    const double* scale_dev = nullptr);
 template <typename TI, typename TO>
-void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s);  // planar
+void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s,
+                    const double* scale_dev = nullptr);  // planar, y = scale x
 void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cudaStream_t s);
 void launch_planar_to_interleaved(const double* in, double* zout, int64_t N, cudaStream_t s);
 // The same between the caller's interleaved array and the internal planar layout of
@@ -175,7 +177,8 @@ void launch_givens(double* H, int ldh, int j, double* cs, double* sn, double* g,
 // H[j+1, j] = sqrt(*sumsq); inv = 1/that (0 if zero).
 void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* inv, cudaStream_t s);
 // Solve the j x j upper triangular system R y = g (complex double) on the device.
-void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s);
+void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s,
+                      const int* j_dev = nullptr);
 
 // Compact right side for Gaussian sources (FP64, complex128 interleaved output F).
 // centers: host nsrc*3, amps: host nsrc*2 (re, im); noise: device complex128 or nullptr.
@@ -218,7 +221,8 @@ void launch_dcgs_update(const TV* V, int64_t vs, int count, T* u, const T* w, TV
                         const double* coef, int nblocks, double vscale, cudaStream_t s);
 void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R, int ldh, double* T, int ldt,
                       double* cs, double* sn, double* g, double* coef, double* est, int* brk, cudaStream_t s);
-void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s);
+void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s,
+                    const int* k_dev = nullptr);
 
 // Learned second preconditioner stage (cnn.cu).  theta: HELM6_CNN_NPARAMS master
 // parameters; wf / wb: BF16-rounded taps of every layer in the forward layout
@@ -240,6 +244,32 @@ int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, c
                     uint16_t* act0, uint16_t* act1, float out_scale, float* z, int* err, cudaStream_t s);
 
 int device_sm_count();
+
+// Device-driven solve (one CUDA graph per solve, convergence decided on the device through
+// conditional nodes): parameters written by the host before the launch, state kept by the
+// control kernels and read back after it.
+struct GraphCtl {
+  double tol_abs;   // tol ||F||
+  double itol_num;  // 0.3 tol ||F||: a cycle's inner tolerance is max(inner, itol_num / beta)
+  double inner;
+  double normF;
+  int maxit, m;
+  double beta, inv_beta, itol;  // current true residual norm, its inverse, inner tolerance
+  int iters, outer, k, status;  // status: -1 running, else a HELM6 return code
+  int nhist, pad;
+  unsigned long long t0, t1;    // %globaltimer at the start and the end of the solve
+  double hist[HELM6_MAX_HIST];
+};
+void launch_gctl_residual(GraphCtl* g, const double* sumsq, const int* zst, const int* tcerr, int first,
+                          cudaGraphConditionalHandle hw, cudaStream_t s);
+// One conditional handle per IF node (a handle belongs to exactly one conditional node):
+// step j's control kernel enables step j + 1, the cycle's first kernel resets them all.
+struct StepHandles {
+  cudaGraphConditionalHandle h[65];
+};
+void launch_gctl_cycle(GraphCtl* g, const StepHandles& ha, int m, cudaStream_t s);
+void launch_gctl_step(GraphCtl* g, int j, int m, const double* est, const int* brk, cudaGraphConditionalHandle next,
+                      cudaStream_t s);
 
 // Kernels launched by the library so far (process-wide counter, for measurement).
 void note_launch(int n = 1);

@@ -87,8 +87,12 @@ struct V2<double> {
 template <typename TI, typename TO, bool VEC>
 __global__ void __launch_bounds__(RB) lincomb_kernel(const TI* __restrict__ V, int64_t vstride, int count,
                                                      const double* __restrict__ y, double scale,
-                                                     TO* __restrict__ out, int64_t N, int accumulate) {
+                                                     TO* __restrict__ out, int64_t N, int accumulate,
+                                                     const int* __restrict__ count_dev,
+                                                     const double* __restrict__ scale_dev) {
   __shared__ TI yr[64], yi[64];
+  if (count_dev) count = *count_dev;  // device-driven solves: the cycle's column count
+  if (scale_dev) scale = *scale_dev;
   for (int c = threadIdx.x; c < count; c += blockDim.x) {
     yr[c] = (TI)(y[2 * c] * scale);
     yi[c] = (TI)(y[2 * c + 1] * scale);
@@ -148,7 +152,9 @@ __global__ void __launch_bounds__(RB) lincomb_kernel(const TI* __restrict__ V, i
 }
 
 template <typename TI, typename TO>
-__global__ void convert_kernel(const TI* __restrict__ x, TO* __restrict__ y, int64_t n2, double scale) {
+__global__ void convert_kernel(const TI* __restrict__ x, TO* __restrict__ y, int64_t n2, double scale,
+                               const double* __restrict__ scale_dev) {
+  if (scale_dev) scale = *scale_dev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += stride)
     y[idx] = (TO)((double)x[idx] * scale);
@@ -738,8 +744,9 @@ __global__ void __launch_bounds__(STEP_T) dcgs_step_kernel(int j, int has_w, con
 }
 
 // q = T[0..k-1, 0..k-1] y (T upper triangular, column-major, leading dimension ldt).
-__global__ void tri_mul_kernel(const double* T, int ldt, int k, const double* y, double* q) {
+__global__ void tri_mul_kernel(const double* T, int ldt, int k, const double* y, double* q, const int* k_dev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (k_dev) k = *k_dev;
   for (int r = 0; r < k; ++r) {
     zc acc = zc{0.0, 0.0};
     for (int i = r; i < k; ++i) acc = zadd(acc, zmul(ld(T + 2 * ((int64_t)i * ldt + r)), ld(y + 2 * i)));
@@ -756,8 +763,9 @@ __global__ void set_subdiag_kernel(double* H, int ldh, int j, const double* sums
   *inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
 }
 
-__global__ void backsolve_kernel(const double* H, int ldh, int j, const double* g, double* y) {
+__global__ void backsolve_kernel(const double* H, int ldh, int j, const double* g, double* y, const int* j_dev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (j_dev) j = *j_dev;
   for (int r = j - 1; r >= 0; --r) {
     zc acc = ld(g + 2 * r);
     for (int c = r + 1; c < j; ++c) {
@@ -833,18 +841,20 @@ void launch_scale_copy(const T* x, T* y, int64_t N, const double* inv_dev, doubl
 
 template <typename TI, typename TO>
 void launch_lincomb(const TI* V, int64_t vstride, int count, const double* y, double scale, TO* out,
-                    int64_t N, int accumulate, cudaStream_t s) {
+                    int64_t N, int accumulate, cudaStream_t s, const int* count_dev, const double* scale_dev) {
   note_launch();
   if ((N & 1) == 0 && (vstride & 1) == 0)
-    lincomb_kernel<TI, TO, true><<<grid_for(N / 2, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
+    lincomb_kernel<TI, TO, true><<<grid_for(N / 2, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate,
+                                                                      count_dev, scale_dev);
   else
-    lincomb_kernel<TI, TO, false><<<grid_for(N, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate);
+    lincomb_kernel<TI, TO, false><<<grid_for(N, RB), RB, 0, s>>>(V, vstride, count, y, scale, out, N, accumulate,
+                                                                   count_dev, scale_dev);
 }
 
 template <typename TI, typename TO>
-void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s) {
+void launch_convert(const TI* x, TO* y, int64_t N, double scale, cudaStream_t s, const double* scale_dev) {
   note_launch();
-  convert_kernel<TI, TO><<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, scale);
+  convert_kernel<TI, TO><<<grid_for(2 * N, RB), RB, 0, s>>>(x, y, 2 * N, scale, scale_dev);
 }
 
 void launch_interleaved_to_planar(const double* zin, double* out, int64_t N, cudaStream_t s) {
@@ -892,9 +902,9 @@ void launch_dcgs_step(int j, int has_w, const double* red, double* Hr, double* R
   dcgs_step_kernel<<<1, STEP_T, 0, s>>>(j, has_w, red, Hr, R, ldh, T, ldt, cs, sn, g, coef, est, brk);
 }
 
-void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s) {
+void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q, cudaStream_t s, const int* k_dev) {
   note_launch();
-  tri_mul_kernel<<<1, 32, 0, s>>>(T, ldt, k, y, q);
+  tri_mul_kernel<<<1, 32, 0, s>>>(T, ldt, k, y, q, k_dev);
 }
 
 void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* inv, cudaStream_t s) {
@@ -902,9 +912,9 @@ void launch_set_subdiag(double* H, int ldh, int j, const double* sumsq, double* 
   set_subdiag_kernel<<<1, 32, 0, s>>>(H, ldh, j, sumsq, inv);
 }
 
-void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s) {
+void launch_backsolve(const double* H, int ldh, int j, const double* g, double* y, cudaStream_t s, const int* j_dev) {
   note_launch();
-  backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y);
+  backsolve_kernel<<<1, 32, 0, s>>>(H, ldh, j, g, y, j_dev);
 }
 
 __global__ void axpby_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n, double a, double b) {
@@ -1004,13 +1014,94 @@ INST_CGS(double, double)
 INST_T(float)
 INST_T(double)
 template void launch_lincomb<float, double>(const float*, int64_t, int, const double*, double, double*,
-                                            int64_t, int, cudaStream_t);
+                                            int64_t, int, cudaStream_t, const int*, const double*);
 template void launch_lincomb<double, double>(const double*, int64_t, int, const double*, double,
-                                             double*, int64_t, int, cudaStream_t);
+                                             double*, int64_t, int, cudaStream_t, const int*, const double*);
 template void launch_lincomb<float, float>(const float*, int64_t, int, const double*, double, float*,
-                                           int64_t, int, cudaStream_t);
-template void launch_convert<double, float>(const double*, float*, int64_t, double, cudaStream_t);
-template void launch_convert<float, double>(const float*, double*, int64_t, double, cudaStream_t);
-template void launch_convert<double, double>(const double*, double*, int64_t, double, cudaStream_t);
+                                           int64_t, int, cudaStream_t, const int*, const double*);
+template void launch_convert<double, float>(const double*, float*, int64_t, double, cudaStream_t, const double*);
+template void launch_convert<float, double>(const float*, double*, int64_t, double, cudaStream_t, const double*);
+template void launch_convert<double, double>(const double*, double*, int64_t, double, cudaStream_t, const double*);
+
+// ---- control of device-driven solves (graph with conditional nodes) ----
+namespace {
+
+// After a true residual: its norm, the solve's status and whether another cycle follows.
+__global__ void gctl_residual_kernel(GraphCtl* g, const double* sumsq, const int* zst, const int* tcerr, int first,
+                                     cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double beta = sqrt(fmax(*sumsq, 0.0));
+  if (first) {
+    g->iters = 0;
+    g->outer = 0;
+    g->nhist = 0;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    g->t0 = t;
+    if (g->nhist < HELM6_MAX_HIST) g->hist[g->nhist++] = beta / g->normF;
+  } else {
+    g->outer++;
+    if (g->nhist > 0) g->hist[g->nhist - 1] = beta / g->normF;  // the true residual replaces the estimate
+  }
+  g->beta = beta;
+  int st = -1;
+  if (!first && *tcerr) st = HELM6_ERR_CUDA;
+  else if (!first && *zst == HELM6_BREAKDOWN) st = HELM6_BREAKDOWN;
+  else if (!isfinite(beta)) st = HELM6_NONFINITE;
+  else if (beta <= g->tol_abs) st = HELM6_OK;
+  else if (g->iters >= g->maxit) st = HELM6_NOT_CONVERGED;
+  if (st == -1) {
+    g->inv_beta = 1.0 / beta;
+    g->itol = fmax(g->inner, g->itol_num / beta);
+  } else {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    g->t1 = t;
+  }
+  g->status = st;
+  cudaGraphSetConditional(hw, st == -1 ? 1u : 0u);
+}
+
+// A cycle starts: step 0 runs, the later steps only when their predecessor enables them.
+__global__ void gctl_cycle_kernel(GraphCtl* g, StepHandles ha, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  g->k = 0;
+  for (int j = 0; j <= m; ++j) cudaGraphSetConditional(ha.h[j], j == 0 ? 1u : 0u);
+}
+
+// After Arnoldi step j (its estimate is that of column j - 1): whether step j + 1 runs.
+__global__ void gctl_step_kernel(GraphCtl* g, int j, int m, const double* est, const int* brk,
+                                 cudaGraphConditionalHandle next) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double e = *est;
+  const int b = *brk;
+  bool stop;
+  if (j == 0) {
+    stop = b || !isfinite(e);
+  } else {
+    g->iters++;
+    if (g->nhist < HELM6_MAX_HIST) g->hist[g->nhist++] = e * g->beta / g->normF;
+    stop = !(e > g->itol) || !isfinite(e) || b || j >= m || g->iters >= g->maxit;
+  }
+  if (stop) g->k = j;
+  if (j < m) cudaGraphSetConditional(next, stop ? 0u : 1u);
+}
+
+}  // namespace
+
+void launch_gctl_residual(GraphCtl* g, const double* sumsq, const int* zst, const int* tcerr, int first,
+                          cudaGraphConditionalHandle hw, cudaStream_t s) {
+  note_launch();
+  gctl_residual_kernel<<<1, 32, 0, s>>>(g, sumsq, zst, tcerr, first, hw);
+}
+void launch_gctl_cycle(GraphCtl* g, const StepHandles& ha, int m, cudaStream_t s) {
+  note_launch();
+  gctl_cycle_kernel<<<1, 32, 0, s>>>(g, ha, m);
+}
+void launch_gctl_step(GraphCtl* g, int j, int m, const double* est, const int* brk, cudaGraphConditionalHandle next,
+                      cudaStream_t s) {
+  note_launch();
+  gctl_step_kernel<<<1, 32, 0, s>>>(g, j, m, est, brk, next);
+}
 
 }  // namespace helm6

@@ -201,25 +201,21 @@ __device__ __forceinline__ void line_coef(const Geom& g, int l, bool rev, double
   sup = rev ? a_l : c_l;
 }
 
-// Pivot tables of the z lines, FP64 arithmetic stored in FP32 (once per context).  For
-// each (p, q) line and step r of the elimination order, rinv_r = 1 / (d_r - sub_r c'_{r-1})
-// with c'_r = sup_r rinv_r.  Away from the ends the recursion is that of a constant
-// tridiagonal matrix, whose pivots converge (geometrically, except on the few resonant
-// lines): rc is the first step from which every stored pivot of steps < m - 1 equals that of
-// step m - 2, rconv that pivot, rlast the pivot of the last step.  The apply kernel reads the
-// table only for steps < rc.
+// Pivot table of the z lines, FP64 arithmetic stored in FP32 (once per context): for each
+// (p, q) line (planes x-mode-major with q pitch z.ldq) and step r of the elimination order,
+// rinv_r = 1 / (d_r - sub_r c'_{r-1}) with c'_r = sup_r rinv_r.
 __global__ void ztri_table_kernel(Geom g, const double* __restrict__ lamx, const double* __restrict__ lamy,
-                                  c64d diag0, c64d alpha, ZLines z, int* status, int xmajor) {
-  const int64_t plane = (int64_t)g.mx * g.my;
+                                  c64d diag0, c64d alpha, ZLines z, int* status) {
+  const int64_t plane = (int64_t)g.mx * z.ldq;
   const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pq >= plane) return;
-  const int p = xmajor ? (int)(pq / g.my) : (int)(pq % g.mx);
-  const int q = xmajor ? (int)(pq % g.my) : (int)(pq / g.mx);
+  const int p = (int)(pq / z.ldq), q = (int)(pq % z.ldq);
+  if (q >= g.my) return;
   const double sig = lamx[p] + lamy[q];
   const int m = g.mz;
   const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
   const bool rev = (!lo_s && hi_s);
-  const int64_t N = g.N;
+  const int64_t Np = (int64_t)m * plane;
   double cr = 0.0, ci = 0.0;
   bool bad = false;
   for (int r = 0; r < m; ++r) {
@@ -243,26 +239,8 @@ __global__ void ztri_table_kernel(Geom g, const double* __restrict__ lamx, const
     ci = sup * ii;
     const int64_t idx = (int64_t)l * plane + pq;
     z.rinv[idx] = (float)ir;
-    z.rinv[N + idx] = (float)ii;
-    if (r == m - 1) z.rlast[pq] = make_float2((float)ir, (float)ii);
+    z.rinv[Np + idx] = (float)ii;
   }
-  // the converged tail: steps [rc, m - 2] all store the pivot of step m - 2
-  int rc = 0;
-  float2 cv = make_float2(0.f, 0.f);
-  if (m >= 2) {
-    const int lref = rev ? 1 : m - 2;
-    cv = make_float2(z.rinv[(int64_t)lref * plane + pq], z.rinv[N + (int64_t)lref * plane + pq]);
-    for (int r = m - 3; r >= 0; --r) {
-      const int l = rev ? (m - 1 - r) : r;
-      const int64_t idx = (int64_t)l * plane + pq;
-      if (z.rinv[idx] != cv.x || z.rinv[N + idx] != cv.y) {
-        rc = r + 1;
-        break;
-      }
-    }
-  }
-  z.rc[pq] = rc;
-  z.rconv[pq] = cv;
   if (bad) atomicExch(status, (int)HELM6_BREAKDOWN);
 }
 
@@ -277,27 +255,23 @@ __device__ __forceinline__ void line_coef_f(const Geom& g, int l, bool rev, floa
   sup = rev ? a_l : c_l;
 }
 
-// Pivot reciprocal of step r (< m - 1 uses the table only before rc).
-__device__ __forceinline__ cpx<float> zpivot(const ZLines& z, int64_t N, int64_t idx, int r, int m, int rc,
-                                             float2 rconv, float2 rlast) {
-  if (r == m - 1) return mk(rlast.x, rlast.y);
-  if (r >= rc) return mk(rconv.x, rconv.y);
-  return mk(__ldg(z.rinv + idx), __ldg(z.rinv + N + idx));
-}
-
-// Reference sweep (any geometry): one thread per line, forward then backward through
-// global memory (the forward results are re-read by the backward sweep).
-__global__ void ztri_apply_kernel(Geom g, ZLines z, const float* __restrict__ x, float* __restrict__ y) {
-  const int64_t plane = (int64_t)g.mx * g.my;
+// The z-line sweeps: one thread per line (every line in flight), forward then backward,
+// the forward results written to y and read back by the backward sweep (which overwrites
+// them).  Both sweeps load U steps ahead before using them; c' = sup rinv is formed on the
+// fly from the pivot table (sup is 0, 1 or 2: exact).  Measured alternatives that read the
+// table only where the pivots have not converged (per line or per warp), or that bound the
+// lines in flight so that the forward results stay in L2, were 1.3 to 4 times slower: the
+// sweep is bound by the loads in flight, which conditional loads and fewer lines reduce.
+template <int U>
+__global__ void __launch_bounds__(128) ztri_lines_kernel(Geom g, ZLines z, const float* __restrict__ x,
+                                                         float* __restrict__ y) {
+  const int64_t plane = (int64_t)g.mx * z.ldq;
   const int64_t pq = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pq >= plane) return;
+  if (pq >= plane || (int)(pq % z.ldq) >= g.my) return;
   const int m = g.mz;
   const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
   const bool rev = (!lo_s && hi_s);
-  const int64_t N = g.N;
-  const int rc = z.rc[pq];
-  const float2 rconv = z.rconv[pq], rlast = z.rlast[pq];
-  constexpr int U = 8;
+  const int64_t N = (int64_t)m * plane;
   cpx<float> yprev = mk(0.f, 0.f);
   for (int r0 = 0; r0 < m; r0 += U) {
     cpx<float> xv[U], iv[U];
@@ -305,17 +279,16 @@ __global__ void ztri_apply_kernel(Geom g, ZLines z, const float* __restrict__ x,
     for (int u = 0; u < U; ++u) {
       const int r = r0 + u;
       if (r < m) {
-        const int l = rev ? (m - 1 - r) : r;
-        const int64_t idx = (int64_t)l * plane + pq;
+        const int64_t idx = (int64_t)(rev ? m - 1 - r : r) * plane + pq;
         xv[u] = mk(x[idx], x[N + idx]);
-        iv[u] = zpivot(z, N, idx, r, m, rc, rconv, rlast);
+        iv[u] = mk(z.rinv[idx], z.rinv[N + idx]);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int r = r0 + u;
       if (r >= m) break;
-      const int l = rev ? (m - 1 - r) : r;
+      const int l = rev ? m - 1 - r : r;
       float sub, sup;
       line_coef_f(g, l, rev, sub, sup);
       const cpx<float> yp = (xv[u] - sub * yprev) * iv[u];
@@ -332,11 +305,11 @@ __global__ void ztri_apply_kernel(Geom g, ZLines z, const float* __restrict__ x,
     for (int u = 0; u < U; ++u) {
       const int r = r0 - u;
       if (r >= 0) {
-        const int l = rev ? (m - 1 - r) : r;
+        const int l = rev ? m - 1 - r : r;
         const int64_t idx = (int64_t)l * plane + pq;
         float sub, sup;
         line_coef_f(g, l, rev, sub, sup);
-        cv[u] = sup * zpivot(z, N, idx, r, m, rc, rconv, rlast);
+        cv[u] = sup * mk(z.rinv[idx], z.rinv[N + idx]);
         yv[u] = mk(y[idx], y[N + idx]);
       }
     }
@@ -344,7 +317,7 @@ __global__ void ztri_apply_kernel(Geom g, ZLines z, const float* __restrict__ x,
     for (int u = 0; u < U; ++u) {
       const int r = r0 - u;
       if (r < 0) break;
-      const int l = rev ? (m - 1 - r) : r;
+      const int l = rev ? m - 1 - r : r;
       const int64_t idx = (int64_t)l * plane + pq;
       const cpx<float> v = yv[u] - cv[u] * next;
       y[idx] = v.re;
@@ -353,159 +326,6 @@ __global__ void ztri_apply_kernel(Geom g, ZLines z, const float* __restrict__ x,
     }
   }
 }
-
-// Blocked sweep: a persistent CTA takes 64 consecutive lines at a time.  One producer
-// thread streams the lines' input, 16 planes (steps) per chunk, into a ring in shared memory
-// with bulk copies (one per plane and component, 4 x lines bytes each); each of the two
-// compute warps runs the forward sweep of its 32 lines into shared memory (the forward
-// results never leave the SM) and then the backward sweep, writing y once.  DRAM traffic is
-// x and y (16 bytes per unknown) plus the table entries before rc.  Every wait is bounded;
-// a timeout sets *err and ends the CTA's loops.
-constexpr int ZB_LINES = 64;                   // lines per block (two compute warps)
-constexpr int ZB_CH = 16;                      // planes per chunk
-constexpr int ZB_RING = 4;                     // chunks in flight
-constexpr int ZB_CHUNK = ZB_CH * 2 * ZB_LINES * 4;  // bytes of one chunk (8 KB)
-constexpr int ZB_THREADS = 96;                 // 2 compute warps + 1 producer warp
-constexpr int kZMaxPolls = 1 << 22;
-
-__device__ __forceinline__ bool zwait(uint32_t bar, uint32_t parity, volatile int* fail) {
-  for (int it = 0; it < kZMaxPolls; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((it & 255) == 255 && *fail) return false;
-  }
-  *fail = 1;
-  return false;
-}
-
-__global__ void __launch_bounds__(ZB_THREADS, 1)
-    ztri_block_kernel(Geom g, ZLines z, const float* __restrict__ x, float* __restrict__ y, int* err) {
-  extern __shared__ __align__(16) uint8_t zsm[];
-  const int m = g.mz;
-  const int64_t plane = (int64_t)g.mx * g.my;
-  const int64_t N = g.N;
-  const int nblocks = (int)((plane + ZB_LINES - 1) / ZB_LINES);
-  const int nchunks = (m + ZB_CH - 1) / ZB_CH;
-  const bool lo_s = g.face[4] == HELM6_SOMMERFELD, hi_s = g.face[5] == HELM6_SOMMERFELD;
-  const bool rev = (!lo_s && hi_s);
-  float2* ys = (float2*)zsm;                                        // [m][64] forward results
-  uint8_t* ring = zsm + (size_t)m * ZB_LINES * sizeof(float2);     // [ZB_RING] chunks
-  uint64_t* bars = (uint64_t*)(ring + ZB_RING * ZB_CHUNK);         // full[ZB_RING], empty[ZB_RING]
-  volatile int* fail = (volatile int*)(bars + 2 * ZB_RING);
-  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(bars);
-  auto full = [&](int s) { return bar0 + 8u * s; };
-  auto empty = [&](int s) { return bar0 + 8u * (ZB_RING + s); };
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) {
-    for (int s = 0; s < ZB_RING; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full(s)), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty(s)), "r"(2));
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;");
-    *fail = 0;
-  }
-  __syncthreads();
-  const int nmine = (int)blockIdx.x < nblocks ? (nblocks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-
-  if (warp == 2) {
-    // ---- producer: chunk j of block i into ring slot (i * nchunks + j) % ZB_RING ----
-    if (lane == 0) {
-      int gch = 0, last = -1;
-      for (int i = 0; i < nmine && !*fail; ++i) {
-        const int64_t pq0 = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * ZB_LINES;
-        const int nl = (int)min((int64_t)ZB_LINES, plane - pq0);
-        for (int j = 0; j < nchunks; ++j, ++gch) {
-          const int s = gch % ZB_RING, u = gch / ZB_RING;
-          if (u >= 1 && !zwait(empty(s), (u - 1) & 1, fail)) break;
-          const int r0 = j * ZB_CH, np = min(ZB_CH, m - r0);
-          const uint32_t bytes = (uint32_t)(np * 2 * nl * 4);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full(s)), "r"(bytes) : "memory");
-          const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(ring + (size_t)s * ZB_CHUNK);
-          for (int e = 0; e < np; ++e) {
-            const int r = r0 + e, l = rev ? (m - 1 - r) : r;
-            for (int c = 0; c < 2; ++c) {
-              const float* src = x + (int64_t)c * N + (int64_t)l * plane + pq0;
-              const uint32_t dst = dst0 + (uint32_t)((e * 2 + c) * ZB_LINES * 4);
-              asm volatile(
-                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                  "l"(src), "r"((uint32_t)(nl * 4)), "r"(full(s))
-                  : "memory");
-            }
-          }
-          last = gch;
-        }
-      }
-      if (last >= 0) zwait(full(last % ZB_RING), (last / ZB_RING) & 1, fail);
-    }
-    __syncwarp();
-  } else {
-    // ---- compute: thread t <-> line pq0 + t ----
-    const int t = tid;  // 0..63
-    int gch = 0;
-    for (int i = 0; i < nmine; ++i) {
-      const int64_t pq0 = (int64_t)((int)blockIdx.x + i * (int)gridDim.x) * ZB_LINES;
-      const int64_t pq = pq0 + t;
-      const bool live = pq < plane;
-      const int rc = live ? z.rc[pq] : 0;
-      const float2 rconv = live ? z.rconv[pq] : make_float2(0.f, 0.f);
-      const float2 rlast = live ? z.rlast[pq] : make_float2(0.f, 0.f);
-      const int64_t pqs = live ? pq : pq0;  // a valid index for the (unused) table reads
-      cpx<float> yprev = mk(0.f, 0.f);
-      bool ok = true;
-      for (int j = 0; j < nchunks; ++j, ++gch) {
-        const int s = gch % ZB_RING, u = gch / ZB_RING;
-        int w = 0;
-        if (lane == 0) w = zwait(full(s), u & 1, fail) ? 1 : 0;
-        if (!__shfl_sync(0xffffffffu, w, 0)) {
-          ok = false;
-          break;
-        }
-        const float* cx = (const float*)(ring + (size_t)s * ZB_CHUNK);
-        const int r0 = j * ZB_CH, np = min(ZB_CH, m - r0);
-#pragma unroll 4
-        for (int e = 0; e < np; ++e) {
-          const int r = r0 + e, l = rev ? (m - 1 - r) : r;
-          float sub, sup;
-          line_coef_f(g, l, rev, sub, sup);
-          const cpx<float> xv = mk(cx[(e * 2) * ZB_LINES + t], cx[(e * 2 + 1) * ZB_LINES + t]);
-          const cpx<float> iv = zpivot(z, N, (int64_t)l * plane + pqs, r, m, rc, rconv, rlast);
-          const cpx<float> yp = (xv - sub * yprev) * iv;
-          ys[r * ZB_LINES + t] = make_float2(yp.re, yp.im);
-          yprev = yp;
-        }
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty(s)) : "memory");
-      }
-      if (!ok) break;
-      cpx<float> next = mk(0.f, 0.f);
-#pragma unroll 4
-      for (int r = m - 1; r >= 0; --r) {
-        const int l = rev ? (m - 1 - r) : r;
-        float sub, sup;
-        line_coef_f(g, l, rev, sub, sup);
-        const int64_t idx = (int64_t)l * plane + pqs;
-        const cpx<float> cv = sup * zpivot(z, N, idx, r, m, rc, rconv, rlast);
-        const float2 yv = ys[r * ZB_LINES + t];
-        const cpx<float> v = mk(yv.x, yv.y) - cv * next;
-        if (live) {
-          y[idx] = v.re;
-          y[N + idx] = v.im;
-        }
-        next = v;
-      }
-    }
-  }
-  __syncthreads();
-  if (tid == 0 && *fail) atomicExch(err, 1);
-}
-
-size_t ztri_block_smem(int m) { return (size_t)m * ZB_LINES * sizeof(float2) + ZB_RING * ZB_CHUNK + 2 * ZB_RING * 8 + 16; }
 
 }  // namespace
 
@@ -532,44 +352,17 @@ void launch_ztri(const Geom& g, const double* lamx, const double* lamy, c64d dia
 
 
 void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c64d diag0, c64d alpha, ZLines z,
-                       int* status, cudaStream_t s, int xmajor) {
-  const int64_t lines = (int64_t)g.mx * g.my;
+                       int* status, cudaStream_t s) {
+  const int64_t lines = (int64_t)g.mx * z.ldq;
   note_launch();
-  ztri_table_kernel<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, lamx, lamy, diag0, alpha, z, status, xmajor);
+  ztri_table_kernel<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, lamx, lamy, diag0, alpha, z, status);
 }
 
-// The blocked kernel needs 16-byte aligned rows of lines (plane a multiple of 4 floats) and
-// its forward results in shared memory; other geometries take the reference sweep.
-bool ztri_blocked_ok(const Geom& g) {
-  const int64_t plane = (int64_t)g.mx * g.my;
-  return plane % 4 == 0 && ztri_block_smem(g.mz) <= 227 * 1024;
-}
-
-// The attribute is the kernel's (process-wide), so it is set once to the largest size any
-// geometry may ask for: contexts of different sizes share it.
-int ztri_configure(const Geom& g) {
-  static int done = 0;
-  if (done || !ztri_blocked_ok(g)) return HELM6_OK;
-  if (cudaFuncSetAttribute(ztri_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
-      cudaSuccess)
-    return HELM6_ERR_CUDA;
-  done = 1;
-  return HELM6_OK;
-}
-
-void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, int* err, cudaStream_t s) {
-  const int64_t lines = (int64_t)g.mx * g.my;
+void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, cudaStream_t s) {
+  const int64_t lines = (int64_t)g.mx * z.ldq;
   note_launch();
-  if (ztri_blocked_ok(g) && ((uintptr_t)x % 16) == 0) {
-    static int sms = 0;
-    if (!sms) sms = device_sm_count();
-    const int nblocks = (int)((lines + ZB_LINES - 1) / ZB_LINES);
-    ztri_block_kernel<<<(unsigned)std::min(nblocks, sms), ZB_THREADS, ztri_block_smem(g.mz), s>>>(g, z, x, y, err);
-  } else {
-    ztri_apply_kernel<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, z, x, y);
-  }
+  ztri_lines_kernel<8><<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(g, z, x, y);
 }
-
 
 template void launch_axis_gemm<float>(const float*, const float*, float*, int, int, int, int64_t, int,
                                       bool, cudaStream_t);

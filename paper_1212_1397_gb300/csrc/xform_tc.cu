@@ -10,23 +10,26 @@
 // Persistent and warp-specialised: one CTA per SM walks the work items (128-row tile x
 // column group) blockIdx.x, + gridDim.x, ...; K is streamed in 32-element stages through
 // three rings in shared memory:
-//   * converter warps (4 x 32 threads, thread t <-> row t of the tile) copy their row's 32
-//     FP32 values of a stage into a private slot of an FP32 ring with cp.async, three
-//     stages ahead, then split them into the BF16 hi/lo operand ring (no-swizzle K-major
-//     core matrices: 8 rows x 16 bytes, 8-row groups 128 B apart, K step one column of
-//     core matrices) and arrive on the stage's `afull` mbarrier.  Output columns beyond
-//     256 (at most 8, the 258-point Neumann axes) are accumulated in FP32 by the same
-//     threads from the values they already hold, and written by them;
+//   * eight converter warps (warp w <-> rows 16 w .. 16 w + 15 of the tile) copy their rows'
+//     32 FP32 values of a stage into an FP32 ring with cp.async, three stages ahead (each
+//     instruction of a warp covers whole 128-byte row segments), then split them (half a
+//     row per thread) into the BF16 hi/lo operand ring (no-swizzle K-major core matrices:
+//     8 rows x 16 bytes, 8-row groups 128 B apart, K step one column of core matrices) and
+//     arrive on the stage's `afull` mbarrier.  Output columns beyond 256 (at most 8, the
+//     258-point Neumann axes) are accumulated in FP32 by the same threads from the values
+//     they already hold, and written by them;
 //   * one producer thread streams the basis stage (hi and lo tiles, prepared on the host)
 //     into the basis ring with cp.async.bulk completing on `bfull`;
 //   * one MMA thread waits for both, issues the tcgen05.mma's of the stage into one of two
 //     256-column tensor-memory accumulators and commits them to `sfree` (which releases the
 //     stage's operand slots) and, after a tile's last stage, to `tfull`;
-//   * four epilogue warps drain the other accumulator (tcgen05.ld, 32 lanes = 32 rows per
-//     warp) while the next tile's MMAs run, store it either transposed within planes of R
-//     rows (out[(row/R)*R*P + p*R + row%R]: consecutive lanes on consecutive addresses) or
-//     row-major through a per-warp shared-memory transpose (out[row*P + p]: each row
-//     segment written by consecutive lanes), and release it on `tempty`.
+//   * eight epilogue warps drain the other accumulator (tcgen05.ld, 32 lanes = 32 rows per
+//     warp, two warps per lane quarter taking alternate 16-column chunks) while the next
+//     tile's MMAs run, store it either transposed within planes of R rows
+//     (out[(row/R)*R*P + p*R + row%R]: consecutive lanes on consecutive addresses) or
+//     row-major through a per-warp shared-memory transpose (out[row*P + p]: row segments
+//     written by consecutive lanes), and release it on `tempty`.  The global stores are
+//     the slowest part of a tile (measured), hence eight warps issuing them.
 // Every mbarrier wait is bounded and warp-uniform; a timeout sets a shared flag that ends
 // every role's loop, and *err for the host.  Whatever the path, the MMA thread waits
 // (bounded) for all of its committed MMAs, the producer for its last bulk copy and the
@@ -49,28 +52,31 @@ constexpr int TC_GMAX = 256;             // output columns of one work item (MMA
 constexpr int TC_TAILMAX = 8;            // FP32 columns beyond 256 done by the converters
 constexpr int NS = 3;                    // operand ring stages (data hi/lo and basis)
 constexpr int ND = 3;                    // FP32 data ring stages (cp.async in flight)
-constexpr int EPI_WARPS = 4;             // warps 0-3: epilogue (tensor-memory lane quarters)
-constexpr int CONV_WARPS = 4;            // warps 4-7: converters
-constexpr int W_PROD = 8, W_MMA = 9;     // basis producer, MMA issuer + TMEM owner
-constexpr int TC_THREADS = 320;
+constexpr int EPI_WARPS = 8;             // warps 0-7: epilogue (lane quarter w % 4, column half w / 4)
+constexpr int CONV_WARPS = 8;            // warps 8-15: converters (16 tile rows each)
+constexpr int W_PROD = 16, W_MMA = 17;   // basis producer, MMA issuer + TMEM owner
+constexpr int TC_THREADS = 576;
 constexpr int A_TILE = TC_M * TC_KT * 2;            // bytes of one BF16 term of a data stage
 constexpr int A_STAGE = 2 * A_TILE;                 // hi + lo
 constexpr int A_LBO = (TC_M / 8) * 128;             // K step of the data stage
 constexpr int B_STAGE = 2 * TC_KC * TC_GMAX * 16;   // hi + lo basis, 256 rows
 constexpr int D_STAGE = TC_M * TC_KT * 4;           // FP32 data, 128 B per row
-constexpr int STG_LD = 33;                          // epilogue transpose stride (floats)
+constexpr int EPI_COLS = 16;                        // columns per epilogue chunk
+constexpr int STG_TLD = 36;                         // staged column stride of the transposed store
+constexpr int STG_FLOATS = EPI_COLS * STG_TLD;      // per-warp staging (>= 32 rows x 16 columns)
 constexpr int OFF_A = 0;
 constexpr int OFF_B = OFF_A + NS * A_STAGE;
 constexpr int OFF_D = OFF_B + NS * B_STAGE;
 constexpr int OFF_T = OFF_D + ND * D_STAGE;
-constexpr int TAIL_FLOATS = TC_TAILMAX * (TC_GMAX + TC_TAILMAX);
+constexpr int TAIL_LD = ((TC_GMAX + TC_TAILMAX + TC_KT - 1) / TC_KT) * TC_KT;  // tail row stride (288)
+constexpr int TAIL_FLOATS = TC_TAILMAX * TAIL_LD;
 constexpr int OFF_S = OFF_T + TAIL_FLOATS * 4;
-constexpr int OFF_BAR = OFF_S + EPI_WARPS * 32 * STG_LD * 4;
+constexpr int OFF_BAR = OFF_S + EPI_WARPS * STG_FLOATS * 4;
 constexpr int NBAR = 3 * NS + 5;  // afull, bfull, sfree per stage; tfull, tempty per buffer; drain
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int SMEM_BYTES = OFF_MISC + 16 + 1024;  // + alignment of the base to 1024
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
-static_assert(OFF_B % 1024 == 0 && OFF_D % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(OFF_B % 1024 == 0 && OFF_D % 16 == 0 && OFF_T % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 constexpr int kMaxPolls = 1 << 22;
 
 struct TcArgs {
@@ -79,7 +85,10 @@ struct TcArgs {
   const uint8_t* W;   // per column group: [kt][term][kc][Npad_g / 8][8 rows][16 B]
   const float* Bt;    // tail basis rows (FP32, tail x K) or null
   int M_total, K, P, nk, terms, transposed, R;
+  int ldin;  // input row pitch (floats, >= K)
+  int ldo;   // output pitch: of a row (row-major, >= P) or of a plane row of R (transposed, >= R)
   int ngroups, gcols, tail, nwork;
+  int vec;  // floats per store of the epilogue: 4, 2 or 1 (from the output pitch and alignment)
   int* err;
 };
 
@@ -137,6 +146,16 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+
+// 16 consecutive tensor-memory columns of the warp's 32 lanes (one row per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int VEC>
 __device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes) {
@@ -210,8 +229,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     asm volatile("fence.proxy.async.shared::cta;");
     *fail = 0;
   }
+  // tail basis rows, zero beyond K up to the last stage's end (K stages of 32)
   float* sBt = (float*)(smem + OFF_T);
-  for (int i = tid; i < p.tail * p.K; i += TC_THREADS) sBt[i] = p.Bt[i];
+  for (int i = tid; i < p.tail * TAIL_LD; i += TC_THREADS) {
+    const int c = i / TAIL_LD, k = i - c * TAIL_LD;
+    sBt[i] = k < p.K ? p.Bt[c * p.K + k] : 0.f;
+  }
   if (warp == W_MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(tslot)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -293,10 +316,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     }
     __syncwarp();
   } else if (warp >= EPI_WARPS) {
-    // ---- converters: thread t holds row t of the tile ----
-    const int t = tid - EPI_WARPS * 32;
-    const uint32_t ring = s_addr(smem + OFF_D) + (uint32_t)t * 128;
-    const int sw = t & 7;  // 16-byte chunk swizzle of the private slot (conflict-free reads)
+    // ---- converters: warp cw copies rows 16 cw .. 16 cw + 15 of each stage into the FP32
+    // ring (each cp.async instruction of the warp covers whole 128-byte row segments:
+    // coalesced) and converts them: lane l takes row 16 cw + l % 16, k half l / 16 ----
+    const int cw = warp - EPI_WARPS;
+    const uint32_t ring = s_addr(smem + OFF_D);
+    const int r = 16 * cw + (lane & 15), hk = lane >> 4;  // this thread's tile row and k half
+    const int sw = r & 7;  // 16-byte chunk swizzle of a row (conflict-free row reads)
     float tacc[TC_TAILMAX];
 #pragma unroll
     for (int c = 0; c < TC_TAILMAX; ++c) tacc[c] = 0.f;
@@ -304,49 +330,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     auto issue = [&](int q) {
       if (q < nstages) {
         const Item it = item(p, (int)blockIdx.x + (q / p.nk) * (int)gridDim.x);
-        const int row = it.m0 + t, k0 = (q % p.nk) * TC_KT;
+        const int k0 = (q % p.nk) * TC_KT;
         const uint32_t slot = ring + (uint32_t)((q % ND) * D_STAGE);
-        const bool rvalid = row < p.M_total;
-        const float* rsrc = p.in + (rvalid ? (int64_t)row * p.K : 0);
 #pragma unroll
-        for (int c = 0; c < 128 / VEC; ++c) {
-          const int k = k0 + c * (VEC / 4);
-          const bool valid = rvalid && k < p.K;
-          const int c16 = (c * VEC) / 16, within = (c * VEC) % 16;
-          cp_async<VEC>(slot + (uint32_t)(((c16 ^ sw) << 4) + within), valid ? (const void*)(rsrc + k) : (const void*)p.in,
+        for (int c = 0; c < 64 / VEC; ++c) {
+          const int o = (c * 32 + lane) * VEC;             // byte within the warp's 16 x 128 B
+          const int rr = 16 * cw + (o >> 7), bb = o & 127;  // tile row, byte within its segment
+          const int row = it.m0 + rr, k = k0 + (bb >> 2);
+          const bool valid = row < p.M_total && k < p.K;
+          const float* src = valid ? p.in + (int64_t)row * p.ldin + k : p.in;
+          cp_async<VEC>(slot + (uint32_t)(rr * 128 + (((bb >> 4) ^ (rr & 7)) << 4) + (bb & 15)), src,
                         valid ? VEC : 0);
         }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
     for (int q = 0; q < ND; ++q) issue(q);
-    const int rg = t >> 3, r8 = t & 7;
     for (int g = 0; g < nstages; ++g) {
       const int s = g % NS, u = g / NS, kt = g % p.nk;
       asm volatile("cp.async.wait_group %0;" ::"n"(ND - 1) : "memory");
+      __syncwarp();  // the warp's rows, copied by all of its lanes, are visible to each lane
       if (u >= 1 && !pollw(sfree(s), (u - 1) & 1, fail, lane)) break;
-      const uint8_t* dslot = smem + OFF_D + (size_t)(g % ND) * D_STAGE + (size_t)t * 128;
+      const uint8_t* dslot = smem + OFF_D + (size_t)(g % ND) * D_STAGE + (size_t)r * 128;
       uint8_t* sA = smem + OFF_A + s * A_STAGE;
       const int k0 = kt * TC_KT;
 #pragma unroll
-      for (int kg = 0; kg < TC_KC; ++kg) {
+      for (int e = 0; e < 2; ++e) {
+        const int kg = 2 * hk + e;
         const float4 a = *(const float4*)(dslot + (((2 * kg) ^ sw) << 4));
         const float4 b = *(const float4*)(dslot + (((2 * kg + 1) ^ sw) << 4));
         uint4 hi, lo;
         split8(a, b, hi, lo);
-        const int off = kg * A_LBO + rg * 128 + r8 * 16;
+        const int off = kg * A_LBO + (r >> 3) * 128 + (r & 7) * 16;
         *(uint4*)(sA + off) = hi;
         *(uint4*)(sA + A_TILE + off) = lo;
         if (p.tail) {
-          const float x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
           for (int c = 0; c < TC_TAILMAX; ++c) {
             if (c < p.tail) {
-#pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int k = k0 + 8 * kg + e;
-                if (k < p.K) tacc[c] = fmaf(x[e], sBt[c * p.K + k], tacc[c]);
-              }
+              const float4 w0 = *(const float4*)(sBt + c * TAIL_LD + k0 + 8 * kg);
+              const float4 w1 = *(const float4*)(sBt + c * TAIL_LD + k0 + 8 * kg + 4);
+              float acc = tacc[c];
+              acc = fmaf(a.x, w0.x, acc);
+              acc = fmaf(a.y, w0.y, acc);
+              acc = fmaf(a.z, w0.z, acc);
+              acc = fmaf(a.w, w0.w, acc);
+              acc = fmaf(b.x, w1.x, acc);
+              acc = fmaf(b.y, w1.y, acc);
+              acc = fmaf(b.z, w1.z, acc);
+              acc = fmaf(b.w, w1.w, acc);
+              tacc[c] = acc;
             }
           }
         }
@@ -356,13 +389,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(afull(s)) : "memory");
       issue(g + ND);
       if (p.tail && kt == p.nk - 1) {
+        // the two k halves of a row are in lanes l and l + 16
+#pragma unroll
+        for (int c = 0; c < TC_TAILMAX; ++c) tacc[c] += __shfl_xor_sync(0xffffffffu, tacc[c], 16);
         const Item it = item(p, (int)blockIdx.x + (g / p.nk) * (int)gridDim.x);
-        const int row = it.m0 + t;
-        if (row < p.M_total) {
+        const int row = it.m0 + r;
+        if (hk == 0 && row < p.M_total) {
           const int plane = row / p.R, rr = row - plane * p.R;
-          float* o = p.transposed ? p.out + (int64_t)plane * p.R * p.P + rr + (int64_t)TC_GMAX * p.R
-                                  : p.out + (int64_t)row * p.P + TC_GMAX;
-          const int64_t cs = p.transposed ? p.R : 1;
+          float* o = p.transposed ? p.out + (int64_t)plane * p.ldo * p.P + rr + (int64_t)TC_GMAX * p.ldo
+                                  : p.out + (int64_t)row * p.ldo + TC_GMAX;
+          const int64_t cs = p.transposed ? p.ldo : 1;
 #pragma unroll
           for (int c = 0; c < TC_TAILMAX; ++c)
             if (c < p.tail) o[c * cs] = tacc[c];
@@ -373,9 +409,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
-    // ---- epilogue: warp q reads tensor-memory lanes 32 q .. 32 q + 31 (tile rows) ----
-    const int q = warp;
-    float* stg = (float*)(smem + OFF_S) + q * 32 * STG_LD;
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and the
+    // 16-column chunks of parity w / 4 ----
+    const int q = warp & 3, h = warp >> 2;
+    float* stg = (float*)(smem + OFF_S) + warp * STG_FLOATS;
     for (int i = 0; i < nitems; ++i) {
       const Item it = item(p, (int)blockIdx.x + i * (int)gridDim.x);
       const int b = i & 1, v = i >> 1;
@@ -389,37 +426,101 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
       int64_t obase = 0;
       if (p.transposed) {
         const int plane = row / p.R, rr = row - plane * p.R;
-        obase = (int64_t)plane * p.R * p.P + rr;
+        obase = (int64_t)plane * p.ldo * p.P + rr;
       }
-      for (int cc = 0; cc < it.npad; cc += 32) {
-        uint32_t r[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-              "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr + (uint32_t)cc));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int ncol = min(32, it.pc - cc);
+      // the tensor-memory load of the next chunk is in flight while a chunk is stored;
+      // a chunk goes through the warp's staging area so that each store instruction writes
+      // p.vec consecutive floats per lane (4 or 2 where the output pitch allows it)
+      auto store = [&](const uint32_t(&v16)[EPI_COLS], int cc) {
+        const int ncol = min(EPI_COLS, it.pc - cc);
+        const int64_t col0 = it.c0 + cc;
         if (p.transposed) {
-          if (live) {
-            float* o = p.out + obase + (int64_t)(it.c0 + cc) * p.R;
+          if (p.vec == 1) {
+            if (live) {
+              float* o = p.out + obase + col0 * p.ldo;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < ncol) o[(int64_t)j * p.R] = __uint_as_float(r[j]);
+              for (int j = 0; j < EPI_COLS; ++j)
+                if (j < ncol) o[(int64_t)j * p.ldo] = __uint_as_float(v16[j]);
+            }
+            return;
           }
+          // staged as [column][row]; a lane then stores vec consecutive rows of one column
+          // (rows of a plane are consecutive in the output; R % vec == 0 keeps them in one)
+#pragma unroll
+          for (int j = 0; j < EPI_COLS; ++j) stg[j * STG_TLD + lane] = __uint_as_float(v16[j]);
+          __syncwarp();
+          if (p.vec == 4) {
+#pragma unroll
+            for (int i = 0; i < EPI_COLS / 4; ++i) {
+              const int j = 4 * i + (lane >> 3), a = 4 * (lane & 7), rw = row0 + a;
+              if (j < ncol && rw < p.M_total) {
+                const int plane = rw / p.R, rr = rw - plane * p.R;
+                *(float4*)(p.out + (int64_t)plane * p.ldo * p.P + (col0 + j) * p.ldo + rr) =
+                    *(const float4*)(stg + j * STG_TLD + a);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < EPI_COLS / 2; ++i) {
+              const int j = 2 * i + (lane >> 4), a = 2 * (lane & 15), rw = row0 + a;
+              if (j < ncol && rw < p.M_total) {
+                const int plane = rw / p.R, rr = rw - plane * p.R;
+                *(float2*)(p.out + (int64_t)plane * p.ldo * p.P + (col0 + j) * p.ldo + rr) =
+                    *(const float2*)(stg + j * STG_TLD + a);
+              }
+            }
+          }
+          __syncwarp();
         } else {
+          // staged as [row][column], 4-float chunks swizzled by row (c4 ^ (row & 3))
 #pragma unroll
-          for (int j = 0; j < 32; ++j) stg[lane * STG_LD + j] = __uint_as_float(r[j]);
+          for (int c4 = 0; c4 < EPI_COLS / 4; ++c4)
+            *(float4*)(stg + lane * EPI_COLS + ((c4 ^ (lane & 3)) << 2)) =
+                make_float4(__uint_as_float(v16[4 * c4]), __uint_as_float(v16[4 * c4 + 1]),
+                            __uint_as_float(v16[4 * c4 + 2]), __uint_as_float(v16[4 * c4 + 3]));
           __syncwarp();
-          if (lane < ncol) {
-            float* o = p.out + (int64_t)row0 * p.P + it.c0 + cc + lane;
-            for (int rr = 0; rr < nrows; ++rr) o[(int64_t)rr * p.P] = stg[rr * STG_LD + lane];
+          if (p.vec == 4) {
+#pragma unroll
+            for (int i = 0; i < 32 / 8; ++i) {
+              const int rr = 8 * i + (lane >> 2), c4 = lane & 3;
+              if (rr < nrows && 4 * c4 < ncol)
+                *(float4*)(p.out + (int64_t)(row0 + rr) * p.ldo + col0 + 4 * c4) =
+                    *(const float4*)(stg + rr * EPI_COLS + ((c4 ^ (rr & 3)) << 2));
+            }
+          } else if (p.vec == 2) {
+#pragma unroll
+            for (int i = 0; i < 32 / 4; ++i) {
+              const int rr = 4 * i + (lane >> 3), c2 = lane & 7;
+              if (rr < nrows && 2 * c2 < ncol)
+                *(float2*)(p.out + (int64_t)(row0 + rr) * p.ldo + col0 + 2 * c2) =
+                    *(const float2*)(stg + rr * EPI_COLS + (((c2 >> 1) ^ (rr & 3)) << 2) + 2 * (c2 & 1));
+            }
+          } else {
+            const int cl = lane & 15, rh = lane >> 4;
+            if (cl < ncol) {
+              float* o = p.out + (int64_t)row0 * p.ldo + col0 + cl;
+              for (int rr = rh; rr < nrows; rr += 2)
+                o[(int64_t)rr * p.ldo] = stg[rr * EPI_COLS + (((cl >> 2) ^ (rr & 3)) << 2) + (cl & 3)];
+            }
           }
           __syncwarp();
+        }
+      };
+      uint32_t ra[EPI_COLS], rb[EPI_COLS];
+      int cc = EPI_COLS * h;
+      if (cc < it.npad) {
+        tmem_ld16(taddr + (uint32_t)cc, ra);
+        tmem_wait();
+      }
+      for (; cc < it.npad; cc += 4 * EPI_COLS) {
+        const int c1 = cc + 2 * EPI_COLS, c2 = cc + 4 * EPI_COLS;
+        if (c1 < it.npad) tmem_ld16(taddr + (uint32_t)c1, rb);
+        store(ra, cc);
+        if (c1 < it.npad) {
+          tmem_wait();
+          if (c2 < it.npad) tmem_ld16(taddr + (uint32_t)c2, ra);
+          store(rb, c1);
+          if (c2 < it.npad) tmem_wait();
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -519,7 +620,7 @@ int tc_configure() {
 }
 
 void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total, int K, int P, int terms,
-                     int transposed, int R, int* err, cudaStream_t s) {
+                     int transposed, int R, int* err, cudaStream_t s, int ldin, int ldo) {
   TcArgs a;
   a.in = in;
   a.out = out;
@@ -531,21 +632,33 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   a.terms = terms;
   a.transposed = transposed;
   a.R = R;
+  a.ldin = ldin > 0 ? ldin : K;
+  a.ldo = ldo > 0 ? ldo : (transposed ? R : P);
   a.ngroups = tc_groups(P, K);
   a.gcols = tc_gcols(P, K);
   a.tail = tc_tail(P, K);
   a.Bt = a.tail ? (const float*)(W + tc_tile_bytes(P, K)) : nullptr;
   a.nwork = ((M_total + TC_M - 1) / TC_M) * a.ngroups;
   a.err = err;
+  {
+    // transposed: a lane stores vec consecutive rows of a column (R % vec == 0, so they
+    // stay in one plane); row-major: vec consecutive columns (P % vec == 0); both need
+    // the output aligned to vec floats
+    // (measured: the staged vector stores pay for the row-major output with a pitch that is
+    // a multiple of 4, not for the transposed one, whose scalar stores are coalesced already)
+    const uintptr_t oa = (uintptr_t)out;
+    a.vec = (!transposed && a.ldo % 4 == 0 && oa % 16 == 0) ? 4 : 1;
+    if (!transposed && a.ngroups > 1 && (a.gcols % a.vec)) a.vec = 1;
+  }
   if (a.nwork == 0) return;
   static int sms = 0;
   if (!sms) sms = device_sm_count();
   const unsigned grid = (unsigned)std::min(a.nwork, sms);
   note_launch();
   const uintptr_t ia = (uintptr_t)in;
-  if (K % 4 == 0 && ia % 16 == 0)
+  if (a.ldin % 4 == 0 && ia % 16 == 0)
     xform_tc_kernel<16><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
-  else if (K % 2 == 0 && ia % 8 == 0)
+  else if (a.ldin % 2 == 0 && ia % 8 == 0)
     xform_tc_kernel<8><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
   else
     xform_tc_kernel<4><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);

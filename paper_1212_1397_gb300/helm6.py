@@ -206,7 +206,8 @@ class Solver:
         lib.helm6_opts_default(C.byref(o))
         o.precision, o.method, o.max_restart = precision, method, max_restart
         o.inner_tol, o.xform_terms = inner_tol, xform_terms
-        o.use_graphs, o.dot_blocks, o.update_blocks = int(bool(use_graphs)), int(dot_blocks), int(update_blocks)
+        o.use_graphs = 2 if (use_graphs == 2 or use_graphs == "solve") else int(bool(use_graphs))
+        o.dot_blocks, o.update_blocks = int(dot_blocks), int(update_blocks)
         o.own_stream = int(bool(own_stream))
         o.basis = int(basis)
         o.cheb_lo, o.cheb_hi = float(cheb_bounds[0]), float(cheb_bounds[1])

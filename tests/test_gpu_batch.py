@@ -114,6 +114,67 @@ def test_shared_streams_and_own_streams(H):
                 s.close()
 
 
+@pytest.mark.parametrize("n,k,faces", [(21, 9.0 + 0.09j, "DNNDSN"), (33, 14.0, "DDNNSS")])
+def test_device_driven_solve_equals_host_driven(H, n, k, faces):
+    """use_graphs = 2: the whole mixed FGMRES solve as one graph launch, every convergence
+    decision on the device (conditional nodes): the same iterations, cycles and solution as
+    the host-driven solve (same kernels, no wasted step), twice in a row (graph reused), and
+    the oracle's solution."""
+    prob, F = _rhs(n, k, faces, 11)
+    ref = O.solve(prob, F, tol=1e-12)[0]
+    Fd = torch.from_numpy(F).cuda()
+    out = {}
+    for mode in (0, 2):
+        with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=12,
+                      stream=torch.cuda.Stream(), use_graphs=mode) as s:
+            torch.cuda.synchronize()
+            u1, st1 = s.solve(Fd, tol=1e-9, restart=12, maxit=400)
+            u2, st2 = s.solve(Fd, tol=1e-9, restart=12, maxit=400)
+            out[mode] = (u1.cpu().numpy(), st1, u2.cpu().numpy(), st2)
+    h, d = out[0], out[2]
+    assert h[1]["rc"] == 0 and d[1]["rc"] == 0 and d[3]["rc"] == 0
+    assert d[1]["iters"] == h[1]["iters"] == d[3]["iters"] and d[1]["outer"] == h[1]["outer"]
+    assert np.array_equal(d[0], h[0]) and np.array_equal(d[0], d[2])
+    assert abs(d[1]["relres"] - h[1]["relres"]) <= 1e-12 * h[1]["relres"]
+    assert np.allclose(d[1]["history"], h[1]["history"], rtol=1e-12, atol=0)
+    assert rel2(d[0], ref) < 1e-6
+
+
+def test_device_driven_batch_is_one_launch_and_matches(H):
+    """helm6_solve_batch over device-driven contexts of different sizes, wavenumbers and faces
+    (one graph launch for the whole batch): every solution equals the host-driven solve of
+    the same problem (bitwise) and the oracle's, per-problem device times are reported, and
+    a second call reuses the batch graph."""
+    specs = [(12, 6.0 + 0.06j, "DDDDDD"), (17, 9.5 + 0.1j, "NNDDSS"), (9, 4.0 + 0.04j, "DNNDDN"),
+             (20, 12.0 + 0.12j, "NDDNNS"), (14, 7.0 + 0.07j, "DDNNSD"), (24, 11.0, "DDNNSS")]
+    solvers, Fs, us, refs, host = [], [], [], [], []
+    for i, (n, k, faces) in enumerate(specs):
+        prob, F = _rhs(n, k, faces, 60 + i)
+        refs.append(O.solve(prob, F, tol=1e-12)[0])
+        solvers.append(H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=16,
+                                own_stream=True, use_graphs=2))
+        Fs.append(torch.from_numpy(F).cuda())
+        us.append(solvers[-1].empty())
+        with H.Solver(n, k, faces, precision=H.MIXED, method=H.FGMRES, max_restart=16) as s0:
+            uh, sth = s0.solve(Fs[-1], tol=1e-9, restart=16, maxit=400)
+            host.append((uh.cpu().numpy(), sth))
+    torch.cuda.synchronize()
+    try:
+        for call in range(2):
+            for u in us:
+                u.zero_()
+            rc, stats = H.solve_batch(solvers, Fs, us, tol=1e-9, restart=16, maxit=400, nthreads=4)
+            assert rc == 0, [st["status"] for st in stats]
+            for u, ref, st, (uh, sth) in zip(us, refs, stats, host):
+                assert st["relres"] <= 1e-9 and st["iters"] == sth["iters"], (st["iters"], sth["iters"])
+                assert np.array_equal(u.cpu().numpy(), uh)
+                assert rel2(u.cpu().numpy(), ref) < 1e-6
+                assert st["t_total_ms"] > 0
+    finally:
+        for s in solvers:
+            s.close()
+
+
 def test_block_options_are_checked(H):
     with pytest.raises(H.Helm6Error):
         H.Solver(8, 3.0, "DDDDDD", dot_blocks=-1)
