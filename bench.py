@@ -78,7 +78,15 @@ KERNEL_OF = {
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) per launch and unknown of a
 # kernel, from a capture of the kernel as it is now built (a kernel absent here was changed
 # since its last capture: traffic null).
-NCU_DRAM_BYTES_PER_UNKNOWN = {}
+# Captured on the 256 x 258 x 258 grid with `bench.py --ops 3` (mixed precision, tensor-core
+# transforms): the x/y transform writes partly stay in the 129 MB L2 for the next kernel, so its
+# DRAM bytes fall below the 16 B per unknown it reads and writes; the z lines read their input,
+# the pivot table twice (once per sweep) and their own forward results back.
+NCU_DRAM_BYTES_PER_UNKNOWN = {
+    "xform_tc_kernel": 12.747,
+    "ztri_lines_kernel<8>": 40.752,
+    "stencil4_kernel": 13.844,
+}
 
 
 def peaks():
@@ -293,14 +301,17 @@ def run_oracle_full(args, cfg):
 
 def run_ops(args, cfg):
     """--ops R: R applications each of the operator and of the preconditioner at the
-    workload's size (mixed precision), device-timed per application; for kernel profiling."""
+    workload's size (--ops-precision, --ops-transform), device-timed per application; for
+    kernel profiling."""
     import torch
     from paper_1212_1397_gb300 import build
     from paper_1212_1397_gb300 import helm6 as H
     build.build()
     H.load()
     torch.cuda.set_device(0)
-    with H.Solver(cfg["n"], cfg["k"], cfg["faces"], precision=H.MIXED, method=H.SKS) as s:
+    prec = H.FP64 if args.ops_precision == "fp64" else H.MIXED
+    with H.Solver(cfg["n"], cfg["k"], cfg["faces"], precision=prec, method=H.SKS,
+                  transform=args.ops_transform) as s:
         x = torch.from_numpy(inputs.complex_normal(5, s.shape)).cuda()
         y, z = s.apply_A(x), s.apply_Pinv(x)
         torch.cuda.synchronize()
@@ -313,7 +324,8 @@ def run_ops(args, cfg):
             e1.record()
             torch.cuda.synchronize()
             out[name + "_ms"] = e0.elapsed_time(e1) / args.ops
-        out.update(workload=args.workload, dims=list(s.dims), reps=args.ops,
+        out.update(workload=args.workload, dims=list(s.dims), reps=args.ops, precision=args.ops_precision,
+                   transforms="/".join(s.transforms),
                    max_abs_Ax=float(y.abs().max()), max_abs_Pinv_x=float(z.abs().max()))
     print(json.dumps({"ops": out}), flush=True)
 
@@ -334,6 +346,8 @@ def main():
     ap.add_argument("--no-f32", action="store_true", help="skip the FP32-basis solve")
     ap.add_argument("--no-sks", action="store_true", help="skip the GMRES(20) vs SKS comparison")
     ap.add_argument("--ops", type=int, default=0, help="only apply A and A_p^-1 this many times each")
+    ap.add_argument("--ops-precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ops-transform", default="auto", choices=["auto", "dense", "fft"])
     ap.add_argument("--oracle-full", action="store_true", help="only the oracle's complete solve, timed once")
     ap.add_argument("--oracle-maxit", type=int, default=2000)
     args = ap.parse_args()
@@ -518,8 +532,22 @@ def main():
         diff = float(torch.linalg.vector_norm(u_mixed - u64) / torch.linalg.vector_norm(u64))
         plain = {"ms": reduce_max(p0.elapsed_time(p1), dist), "iters": st64["iters"],
                  "relres": st64["relres"], "status": st64["status"],
-                 "mixed_vs_fp64_rel_l2": diff}
+                 "mixed_vs_fp64_rel_l2": diff, "transforms": "/".join(solver64.transforms)}
+        plain["ms_per_iter"] = plain["ms"] / max(1, st64["iters"])
         solver64.close()
+        # the same solver with the dense m x m transforms, over its first 10 iterations
+        solverd = H.Solver(n, k, faces, precision=H.FP64, method=H.GMRES, max_restart=restart,
+                           stream=stream, transform="dense")
+        u64.zero_()
+        solverd.solve(F, u64, tol=tol, restart=restart, maxit=2)  # warm-up
+        u64.zero_()
+        sync_all(dist)
+        p0.record(stream)
+        _, std = solverd.solve(F, u64, tol=tol, restart=restart, maxit=10)
+        p1.record(stream)
+        sync_all(dist)
+        plain["dense_ms_per_iter"] = reduce_max(p0.elapsed_time(p1), dist) / max(1, std["iters"])
+        solverd.close()
         del u64
 
     # ---- batched workload: 64 heterogeneous problems, tuned grids and schedule ----

@@ -72,6 +72,20 @@ enum { HELM6_BASIS_AUTO = 0, /* the default below */
                                 bytes; each v_i is rounded once, when written, and later steps
                                 orthogonalise against the rounded vectors */ };
 
+/* x/y transforms of the preconditioner (Section 3.3: the direct solver of A_p is FFT-type).
+   The FFT form applies an axis' closed-form sine/cosine eigenbasis through a complex DFT of
+   length L = 2(n+1) (D-D, N-N faces) or 4(n+1) (D-N, N-D) of the line's odd or even
+   extension; it exists when L = 2^a * Q with Q = 1 or a prime with Q - 1 a power of two
+   (Q <= 257): n + 1 a power of two, or n + 1 = 257, 17, 5, 3 times a power of two. */
+enum { HELM6_XFORM_AUTO = 0,   /* FP64: FFT on every axis that has one, else dense.  MIXED:
+                                  dense on tensor cores while both axes fit them (<= 264
+                                  unknowns), else FFT where it exists, else dense FP32 */
+       HELM6_XFORM_DENSE = 1,  /* the dense m x m basis matrices (tensor cores where MIXED and
+                                  the axes fit them) */
+       HELM6_XFORM_FFT = 2,    /* FFT on every axis that has one (MIXED: FP32, no tensor
+                                  cores), dense on the others */
+       HELM6_XFORM_TENSOR = 3  /* reported by helm6_transform only: dense on tensor cores */ };
+
 /* return codes */
 enum {
   HELM6_OK = 0,
@@ -121,6 +135,7 @@ typedef struct {
                         concurrently while staying ordered with default-stream work */
   int basis;         /* MIXED Krylov methods: HELM6_BASIS_*; AUTO = F16 from 2^23 unknowns
                         (mx*my*mz), F32 below.  F16 with FP64 is INVALID */
+  int transform;     /* x/y transforms of the preconditioner: HELM6_XFORM_* (AUTO default) */
 } helm6_opts;
 
 #define HELM6_MAX_HIST 1024
@@ -155,6 +170,12 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
 
 /* Unknowns per axis: dims = {mx, my, mz}. */
 int helm6_dims(const helm6_ctx* ctx, int64_t dims[3]);
+
+/* The transform the context applies along axis 0 (internal x) or 1 (internal y):
+ * HELM6_XFORM_DENSE, HELM6_XFORM_FFT or HELM6_XFORM_TENSOR; INVALID for a null context or
+ * another axis.  With Sommerfeld-like faces on x or y the internal axes are the exchanged
+ * ones (that pair becomes the internal z). */
+int helm6_transform(const helm6_ctx* ctx, int axis);
 
 /* Storage of the context's Krylov basis as resolved at creation: HELM6_BASIS_F32 or
  * HELM6_BASIS_F16 for a MIXED GMRES/FGMRES context, HELM6_BASIS_AUTO (0) where the basis is

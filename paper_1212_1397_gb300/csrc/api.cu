@@ -53,6 +53,9 @@ struct helm6_ctx {
   uint8_t *Wx_tc = nullptr, *Wy_tc = nullptr, *Vx_tc = nullptr, *Vy_tc = nullptr;
   int* tcerr = nullptr;
   ZLines zl;  // z-line pivot tables (tensor-core path)
+  // x/y transforms: HELM6_XFORM_DENSE, _FFT or _TENSOR per internal axis, and the FFT plans
+  int xform[2] = {HELM6_XFORM_DENSE, HELM6_XFORM_DENSE};
+  FftDev fft[2] = {};
   // FP64 vectors (2N doubles each)
   double *F64 = nullptr, *U64 = nullptr, *R64 = nullptr, *E64 = nullptr;
   double* D64 = nullptr;           // Chebyshev direction
@@ -303,20 +306,33 @@ void precond(helm6_ctx* c, const T* in, T* out, T* tA, T* tB, T* cw, const T* Vx
   const Geom& g = c->g;
   cudaStream_t s = c->stream;
   const int64_t plane = (int64_t)g.mx * g.my;
+  const bool fx = c->xform[0] == HELM6_XFORM_FFT, fy = c->xform[1] == HELM6_XFORM_FFT;
   cudaEvent_t e = prof_start(c);
-  launch_axis_gemm<T>(Wx, in, tA, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+  if (fx)
+    launch_fft_axis<T>(c->fft[0], 0, 0, g, in, tA, s);
+  else
+    launch_axis_gemm<T>(Wx, in, tA, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
   prof_stop(c, HELM6_PH_XFWD, e);
   e = prof_start(c);
-  launch_axis_gemm<T>(Wy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  if (fy)
+    launch_fft_axis<T>(c->fft[1], 1, 0, g, tA, tB, s);
+  else
+    launch_axis_gemm<T>(Wy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
   prof_stop(c, HELM6_PH_YFWD, e);
   e = prof_start(c);
   launch_ztri<T>(g, c->lamx, c->lamy, c->diag0, c->alpha, tB, tA, cw, c->status, s);
   prof_stop(c, HELM6_PH_ZTRI, e);
   e = prof_start(c);
-  launch_axis_gemm<T>(Vy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
+  if (fy)
+    launch_fft_axis<T>(c->fft[1], 1, 1, g, tA, tB, s);
+  else
+    launch_axis_gemm<T>(Vy, tA, tB, g.my, g.mx, g.mx, plane, 2 * g.mz, false, s);
   prof_stop(c, HELM6_PH_YINV, e);
   e = prof_start(c);
-  launch_axis_gemm<T>(Vx, tB, out, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
+  if (fx)
+    launch_fft_axis<T>(c->fft[0], 0, 1, g, tB, out, s);
+  else
+    launch_axis_gemm<T>(Vx, tB, out, g.mx, 2 * g.my * g.mz, g.mx, 0, 1, true, s);
   prof_stop(c, HELM6_PH_XINV, e);
 }
 
@@ -1229,6 +1245,7 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   }
   if (o.basis < HELM6_BASIS_AUTO || o.basis > HELM6_BASIS_F16) return HELM6_ERR_INVALID;
   if (o.basis == HELM6_BASIS_F16 && o.precision != HELM6_MIXED) return HELM6_ERR_INVALID;
+  if (o.transform < HELM6_XFORM_AUTO || o.transform > HELM6_XFORM_FFT) return HELM6_ERR_INVALID;
   if (o.xform_terms == 0) o.xform_terms = 3;
   if (o.xform_terms < 1 || o.xform_terms > 3) return HELM6_ERR_INVALID;
   if (o.max_restart == 0) o.max_restart = 30;
@@ -1301,6 +1318,34 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   if (up64(c->Vx64, Vx) || up64(c->Wx64, Wx) || up64(c->Vy64, Vy) || up64(c->Wy64, Wy) || up64(c->lamx, lx) ||
       up64(c->lamy, ly) || up32(c->Vx32, Vx) || up32(c->Wx32, Wx) || up32(c->Vy32, Vy) || up32(c->Wy32, Wy))
     return fail(HELM6_ERR_CUDA);
+  // transforms: dense on tensor cores (MIXED, both axes fit, not FFT-forced), else the FFT
+  // form where the axis length has one (unless dense is asked for), else dense
+  const bool use_tc = o.precision == HELM6_MIXED && o.transform != HELM6_XFORM_FFT && c->g.mx <= tc_max_axis() &&
+                      c->g.my <= tc_max_axis();
+  for (int a = 0; a < 2; ++a) {
+    c->xform[a] = use_tc ? HELM6_XFORM_TENSOR : HELM6_XFORM_DENSE;
+    FftHostPlan fp;
+    if (use_tc || o.transform == HELM6_XFORM_DENSE || !fft_make_plan(n, c->g.face[2 * a], c->g.face[2 * a + 1], fp))
+      continue;
+    double2* t64 = nullptr;
+    float2* t32 = nullptr;
+    int* gi = nullptr;
+    const size_t nt = fp.tw.size() / 2;
+    if ((rc = dalloc(c, &t64, nt)) || (rc = dalloc(c, &t32, nt)) || (rc = dalloc(c, &gi, std::max<size_t>(1, fp.gidx.size()))))
+      return fail(rc);
+    std::vector<float> f32(fp.tw.begin(), fp.tw.end());
+    if (cudaMemcpy(t64, fp.tw.data(), fp.tw.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t32, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!fp.gidx.empty() &&
+         cudaMemcpy(gi, fp.gidx.data(), fp.gidx.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+      return fail(HELM6_ERR_CUDA);
+    fp.d.tw64 = t64;
+    fp.d.tw32 = t32;
+    fp.d.gidx = gi;
+    c->fft[a] = fp.d;
+    c->xform[a] = HELM6_XFORM_FFT;
+    fft_configure();
+  }
 
   // workspace
   const int64_t N = c->g.N;
@@ -1370,7 +1415,7 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
     return fail(rc);
   if ((rc = dalloc(c, &c->tcerr, 1))) return fail(rc);
   if (cudaMemset(c->tcerr, 0, sizeof(int)) != cudaSuccess) return fail(HELM6_ERR_CUDA);
-  if (o.precision == HELM6_MIXED && c->g.mx <= tc_max_axis() && c->g.my <= tc_max_axis()) {
+  if (use_tc) {
     if (tc_configure() != HELM6_OK) return fail(HELM6_ERR_CUDA);
     std::vector<uint8_t> t;
     auto upt = [&](uint8_t** d, const std::vector<double>& B, int m) -> int {
@@ -1407,6 +1452,11 @@ int helm6_dims(const helm6_ctx* c, int64_t dims[3]) {
   dims[1] = c->gu.my;
   dims[2] = c->gu.mz;
   return HELM6_OK;
+}
+
+int helm6_transform(const helm6_ctx* c, int axis) {
+  if (!c || axis < 0 || axis > 1) return HELM6_ERR_INVALID;
+  return c->xform[axis];
 }
 
 int helm6_basis(const helm6_ctx* c) {

@@ -143,6 +143,32 @@ void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c6
 // y = the z-line solve of x (planar FP32 in that layout; y may not alias x).
 void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, cudaStream_t s);
 
+// FFT-type x/y transforms (fft.cu): the closed-form 1D eigenbasis of one axis applied through a
+// complex DFT of length L = P * Q of the line's odd (sine) or even (cosine) extension.
+struct FftDev {
+  int kind;        // 0 D-D (sine), 1 N-N (cosine), 2 D-N, 3 N-D (quarter-wave)
+  int N;           // intervals n + 1
+  int m;           // unknowns on the axis
+  int L, P, Q, M;  // L = P Q, P a power of two, Q = 1 or a prime with M = Q - 1 a power of two
+  int logP, logM;
+  const double2* tw64;  // [w_P^k: P/2][w_M^k: M/2][kernel spectrum / M: M][w_L^t: L if Q > 1]
+  const float2* tw32;   // the same in FP32
+  const int* gidx;      // [g^q mod Q: M][g^-q mod Q: M]
+};
+struct FftHostPlan {
+  FftDev d;                // sizes; device pointers null
+  std::vector<double> tw;  // the complex tables, interleaved
+  std::vector<int> gidx;
+};
+// Plan for n interior nodes and the axis' faces lo, hi (helm6_bc); false when L has no
+// factorisation of the form above or a line does not fit in shared memory.
+bool fft_make_plan(int n, int lo, int hi, FftHostPlan& plan);
+void fft_configure();  // once per process: the kernels' dynamic shared memory limit
+// out = W in (inv = 0, forward) or V in (inv = 1) along axis 0 (x) or 1 (y) of the planar
+// field (same layout in and out; out may not alias in).
+template <typename T>
+void launch_fft_axis(const FftDev& f, int axis, int inv, const Geom& g, const T* in, T* out, cudaStream_t s);
+
 // BLAS-1 style kernels on planar complex vectors of N points.
 void launch_reduce_cols(const double* partial, int nblocks, int ncols, double* out, int accumulate,
                         cudaStream_t s);  // out[i] (+)= sum_b partial[b][i], complex double

@@ -19,6 +19,9 @@ MAX_HIST = 1024
 CNN_NPARAMS = 15602
 CNN_OFF, CNN_ON, CNN_AUTO = 0, 1, 2
 BASIS_AUTO, BASIS_F32, BASIS_F16 = 0, 1, 2
+XFORM_AUTO, XFORM_DENSE, XFORM_FFT, XFORM_TENSOR = 0, 1, 2, 3
+_XFORM_CODE = {"auto": XFORM_AUTO, "dense": XFORM_DENSE, "fft": XFORM_FFT}
+_XFORM_NAME = {XFORM_DENSE: "dense", XFORM_FFT: "fft", XFORM_TENSOR: "tensor"}
 
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "DIVERGED", 3: "BREAKDOWN", 4: "NONFINITE",
           -1: "ERR_INVALID", -2: "ERR_NOMEM", -3: "ERR_CUDA", -4: "ERR_UNSUPPORTED"}
@@ -32,7 +35,7 @@ EXPORTS = ("helm6_opts_default", "helm6_create", "helm6_dims", "helm6_basis", "h
            "helm6_apply_stage2", "helm6_cnn_trainer_create", "helm6_cnn_forward", "helm6_cnn_gradient",
            "helm6_cnn_train_step", "helm6_cnn_set_residual_loss", "helm6_cnn_get_params",
            "helm6_cnn_trainer_destroy", "helm6_solve_batch", "helm6_rhs_separable",
-           "helm6_lift_dirichlet")
+           "helm6_lift_dirichlet", "helm6_transform")
 
 PHASES = ("stencil", "xform_x_fwd", "xform_y_fwd", "ztri", "xform_y_inv", "xform_x_inv", "gs_dot",
           "gs_update", "gs_small", "resid64", "other", "cnn")
@@ -47,7 +50,7 @@ class Opts(C.Structure):
                 ("max_restart", C.c_int), ("inner_tol", C.c_double), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int), ("dot_blocks", C.c_int), ("update_blocks", C.c_int),
                 ("cheb_lo", C.c_double), ("cheb_hi", C.c_double), ("own_stream", C.c_int),
-                ("basis", C.c_int)]
+                ("basis", C.c_int), ("transform", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -93,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.helm6_dims.restype = I
     lib.helm6_basis.argtypes = [P]
     lib.helm6_basis.restype = I
+    lib.helm6_transform.argtypes = [P, I]
+    lib.helm6_transform.restype = I
     lib.helm6_apply_A.argtypes = [P, P, P]
     lib.helm6_apply_A.restype = I
     lib.helm6_apply_Pinv.argtypes = [P, P, P]
@@ -199,7 +204,8 @@ class Solver:
 
     def __init__(self, n, k, faces="DDDDDD", h=0.0, precision=FP64, method=GMRES,
                  max_restart=30, inner_tol=1e-5, xform_terms=3, stream=None, use_graphs=False,
-                 dot_blocks=0, update_blocks=0, own_stream=False, cheb_bounds=(0.0, 0.0), basis=BASIS_AUTO):
+                 dot_blocks=0, update_blocks=0, own_stream=False, cheb_bounds=(0.0, 0.0), basis=BASIS_AUTO,
+                 transform="auto"):
         lib = load()
         self._lib = lib
         o = Opts()
@@ -210,6 +216,7 @@ class Solver:
         o.dot_blocks, o.update_blocks = int(dot_blocks), int(update_blocks)
         o.own_stream = int(bool(own_stream))
         o.basis = int(basis)
+        o.transform = _XFORM_CODE[transform] if isinstance(transform, str) else int(transform)
         o.cheb_lo, o.cheb_hi = float(cheb_bounds[0]), float(cheb_bounds[1])
         if stream is not None:
             o.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -232,6 +239,13 @@ class Solver:
         """Storage of the Krylov basis as resolved at creation: BASIS_F32 or BASIS_F16 (MIXED
         GMRES/FGMRES), BASIS_AUTO where it is FP64 or there is none."""
         return _check(self._lib.helm6_basis(self._ctx), "helm6_basis")
+
+    @property
+    def transforms(self):
+        """The x/y transforms as resolved at creation, per internal axis: "dense", "fft" or
+        "tensor" (dense on tensor cores)."""
+        return tuple(_XFORM_NAME[_check(self._lib.helm6_transform(self._ctx, a), "helm6_transform")]
+                     for a in (0, 1))
 
     def close(self):
         if getattr(self, "_ctx", None):

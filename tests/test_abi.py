@@ -76,6 +76,12 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib_path):
     lib.helm6_opts_default(ctypes.byref(o))
     o.max_restart = 1000
     assert lib.helm6_create(ctypes.byref(ctx), 8, 0.0, k, faces, ctypes.byref(o)) == -1
+    lib.helm6_opts_default(ctypes.byref(o))
+    assert o.transform == H.XFORM_AUTO
+    for bad in (-1, H.XFORM_TENSOR):   # TENSOR is a reported value, not an option
+        o.transform = bad
+        assert lib.helm6_create(ctypes.byref(ctx), 8, 0.0, k, faces, ctypes.byref(o)) == -1
+    assert lib.helm6_transform(None, 0) == -1
 
 
 def test_noalloc_binding_rejects_wrong_sizes_before_any_launch():
