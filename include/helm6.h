@@ -73,10 +73,11 @@ enum { HELM6_BASIS_AUTO = 0, /* the default below */
                                 orthogonalise against the rounded vectors */ };
 
 /* x/y transforms of the preconditioner (Section 3.3: the direct solver of A_p is FFT-type).
-   The FFT form applies an axis' closed-form sine/cosine eigenbasis through a complex DFT of
-   length L = 2(n+1) (D-D, N-N faces) or 4(n+1) (D-N, N-D) of the line's odd or even
-   extension; it exists when L = 2^a * Q with Q = 1 or a prime with Q - 1 a power of two
-   (Q <= 257): n + 1 a power of two, or n + 1 = 257, 17, 5, 3 times a power of two. */
+   The FFT form applies an axis' closed-form sine/cosine eigenbasis through one complex DFT
+   per line, of length L = n+1 (D-D, N-N faces: the sine and cosine transforms with pre- and
+   post-processing) or 4(n+1) (D-N, N-D: the line's odd or even extension); it exists when
+   n + 1 = 2^a * Q with Q = 1 or a prime with Q - 1 a power of two (Q <= 257): n + 1 a power
+   of two, or 257, 17, 5, 3 times a power of two. */
 enum { HELM6_XFORM_AUTO = 0,   /* FP64: FFT on every axis that has one, else dense.  MIXED:
                                   dense on tensor cores while both axes fit them (<= 264
                                   unknowns), else FFT where it exists, else dense FP32 */

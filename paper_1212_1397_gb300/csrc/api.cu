@@ -1325,7 +1325,10 @@ int helm6_create(helm6_ctx** out, int n, double h, helm6_c64 k, const int faces[
   for (int a = 0; a < 2; ++a) {
     c->xform[a] = use_tc ? HELM6_XFORM_TENSOR : HELM6_XFORM_DENSE;
     FftHostPlan fp;
-    if (use_tc || o.transform == HELM6_XFORM_DENSE || !fft_make_plan(n, c->g.face[2 * a], c->g.face[2 * a + 1], fp))
+    // FP64: the half-length sine/cosine form (the FP64 pipe bounds the kernel); FP32: the
+    // extension form, whose rounding costs the mixed solve fewer iterations
+    if (use_tc || o.transform == HELM6_XFORM_DENSE ||
+        !fft_make_plan(n, c->g.face[2 * a], c->g.face[2 * a + 1], o.precision == HELM6_FP64, fp))
       continue;
     double2* t64 = nullptr;
     float2* t32 = nullptr;

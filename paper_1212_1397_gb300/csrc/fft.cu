@@ -3,13 +3,27 @@
 //
 // Each of the four closed-form eigenbases of the 1D second-difference matrix (D-D sine,
 // N-N cosine, D-N and N-D quarter-wave) is a sine or cosine sum sum_l x_l trig(pi a l j / N)
-// with N = n + 1 intervals.  Extending a line oddly (sine) or evenly (cosine) to the length
-// L = 2N (D-D, N-N) or L = 4N (D-N, N-D) turns that sum into one complex DFT of length L:
+// with N = n + 1 intervals.  The basis matrices are real, so a complex line (real plane +
+// i * imaginary plane) goes through one complex DFT and both planes are transformed at once.
+//
+// Extending the line oddly (sine) or evenly (cosine) to the length L = 2N (D-D, N-N) or
+// L = 4N (D-N, N-D) turns the sum into one complex DFT of length L,
 //     E_j = sum_l e_l w^{l j},  w = exp(-2 pi i / L),
-// sum e_l (w^{lj} - w^{-lj}) = -2i sum e_l sin(2 pi l j / L) for an odd extension and
-// 2 sum w_l e_l cos(2 pi l j / L) for an even one.  The basis matrices are real, so a complex
-// line (real plane + i * imaginary plane) goes through one complex DFT and both planes are
-// transformed at once.
+// since sum e_l (w^{lj} - w^{-lj}) = -2i sum e_l sin(2 pi l j / L) for an odd extension and
+// 2 sum w_l e_l cos(2 pi l j / L) for an even one.
+//
+// D-D and N-N take the same extension form (L = 2N) or, in the half-length form, a DFT of
+// length L = N.  With s_j = sin(pi j / N), the line
+//     y_j = s_j (x_j + x_{N-j}) + (x_j - x_{N-j}) / 2            (sine, x_0 = x_N = 0)
+//     y_j = (x_j + x_{N-j}) / 2 - s_j (x_j - x_{N-j})            (cosine, nodes 0..N)
+// has DFT Z with A_k = (Z_k + Z_{N-k}) / 2 and B_k = i (Z_k - Z_{N-k}) / 2 such that
+//     sine:   S_2k = B_k,  S_2k+1 - S_2k-1 = A_k,  S_1 = A_0 / 2,
+//     cosine: C_2k = A_k,  C_2k+1 - C_2k-1 = B_k,  C_1 = sum_j w_j x_j cos(pi j / N)
+// (the symmetric part of y carries the cosines of even multiples, the antisymmetric part,
+// through 2 sin a sin b = cos(a - b) - cos(a + b), the differences of the odd ones), so the
+// odd outputs are a prefix sum over k.  This halves the DFT length of the extension form; the
+// library takes it in FP64, where the FP64 pipe bounds the kernel, and keeps the extension
+// form in FP32, where its rounding (no prefix sum) costs fewer iterations.
 //
 // The DFT of length L = P * Q (P a power of two, Q = 1 or an odd prime with Q - 1 a power of
 // two, which covers n + 1 = 2^k and the prime n + 1 = 257 of the 256^3 grid) is a
@@ -132,10 +146,13 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(FftDev f, const T* __rest
   V* sE = sBh + M;
   V* sW = sE + (size_t)B * L;
   V* sAux = sW + (size_t)B * P * M;
-  int* sG = reinterpret_cast<int*>(sAux + (Q > 1 ? 2 * B * P : 0));
+  V* sX = sAux + (Q > 1 ? 2 * B * P : 0);  // sine/cosine: the lines by node 0..N
+  const bool half = f.half;
+  int* sG = reinterpret_cast<int*>(sX + (half ? (size_t)B * (f.N + 1) : 0));
   int* sGi = sG + M;
   const V* gtw = reinterpret_cast<const V*>(sizeof(T) == 8 ? (const void*)f.tw64 : (const void*)f.tw32);
   const V* gTwL = gtw + hP + hM + M;
+  const V* gCS = gTwL + (Q > 1 ? L : 0);  // sine/cosine: (cos, sin)(pi j / N), j = 0..N
   const int tid = threadIdx.x, nt = blockDim.x;
 
   for (int e = tid; e < hP + hM + M; e += nt) sTwP[e] = gtw[e];
@@ -145,44 +162,85 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(FftDev f, const T* __rest
   const int nb = min(B, ln.rows - r0);
   const int m = f.m, N = f.N, kind = f.kind;
   const bool odd = kind == 0 || kind == 2, quarter = kind >= 2;
-  for (int e = tid; e < nb * L; e += nt) sE[e] = V{T(0), T(0)};
-  __syncthreads();
+  const int X1 = N + 1;
 
-  // load: stored index p -> extension position pos (and its mirror L - pos)
-  for (int e = tid; e < nb * m; e += nt) {
-    int r, p;
-    if (ALONG) {
-      r = e / m;
-      p = e - r * m;
-    } else {
-      p = e / nb;
-      r = e - p * nb;
-    }
-    const int gr = r0 + r;
-    const int64_t g = (int64_t)(gr / ln.rdiv) * ln.hi + (int64_t)(gr % ln.rdiv) * ln.lo + (int64_t)p * ln.es;
-    T wgt = T(1);
-    int pos;
-    if (!inv) {
-      pos = p + ((kind == 0 || kind == 2) ? 1 : 0);  // node l
-      if (kind == 2 && pos == N) wgt = T(0.5);
-    } else {
-      const int j = p + (kind == 1 ? 0 : 1);  // mode j
-      pos = quarter ? 2 * j - 1 : j;
-      if (kind == 1 && (j == 0 || j == N)) wgt = T(2);
-    }
-    V x;
-    x.x = wgt * in[g];
-    x.y = wgt * in[g + ln.N];
-    sE[r * L + pos] = x;
-    if (pos != 0 && 2 * pos != L) {
-      if (odd) {
-        x.x = -x.x;
-        x.y = -x.y;
+  if (half) {
+    // load the line by node into sX (sine: x_0 = x_N = 0), then y_j into sE
+    if (kind == 0)
+      for (int e = tid; e < nb; e += nt) sX[e * X1] = sX[e * X1 + N] = V{T(0), T(0)};
+    for (int e = tid; e < nb * m; e += nt) {
+      int r, p;
+      if (ALONG) {
+        r = e / m;
+        p = e - r * m;
+      } else {
+        p = e / nb;
+        r = e - p * nb;
       }
-      sE[r * L + L - pos] = x;
+      const int gr = r0 + r;
+      const int64_t g = (int64_t)(gr / ln.rdiv) * ln.hi + (int64_t)(gr % ln.rdiv) * ln.lo + (int64_t)p * ln.es;
+      const int j = p + (kind == 0 ? 1 : 0);
+      const T wgt = (kind == 1 && inv && (j == 0 || j == N)) ? T(2) : T(1);
+      V x;
+      x.x = wgt * in[g];
+      x.y = wgt * in[g + ln.N];
+      sX[r * X1 + j] = x;
     }
+    __syncthreads();
+    for (int e = tid; e < nb * N; e += nt) {
+      const int r = e / N, j = e - r * N;
+      const V a = sX[r * X1 + j], b = sX[r * X1 + N - j];
+      const T sn = gCS[j].y;
+      V y;
+      if (kind == 0) {
+        y.x = sn * (a.x + b.x) + T(0.5) * (a.x - b.x);
+        y.y = sn * (a.y + b.y) + T(0.5) * (a.y - b.y);
+      } else {
+        y.x = T(0.5) * (a.x + b.x) - sn * (a.x - b.x);
+        y.y = T(0.5) * (a.y + b.y) - sn * (a.y - b.y);
+      }
+      sE[r * L + j] = y;
+    }
+    __syncthreads();
+  } else {
+    for (int e = tid; e < nb * L; e += nt) sE[e] = V{T(0), T(0)};
+    __syncthreads();
+    // load: stored index p -> extension position pos (and its mirror L - pos)
+    for (int e = tid; e < nb * m; e += nt) {
+      int r, p;
+      if (ALONG) {
+        r = e / m;
+        p = e - r * m;
+      } else {
+        p = e / nb;
+        r = e - p * nb;
+      }
+      const int gr = r0 + r;
+      const int64_t g = (int64_t)(gr / ln.rdiv) * ln.hi + (int64_t)(gr % ln.rdiv) * ln.lo + (int64_t)p * ln.es;
+      T wgt = T(1);
+      int pos;
+      if (!inv) {
+        pos = p + ((kind == 0 || kind == 2) ? 1 : 0);  // node l
+        if (kind == 2 && pos == N) wgt = T(0.5);
+      } else {
+        const int j = p + (kind == 1 ? 0 : 1);  // mode j
+        pos = quarter ? 2 * j - 1 : j;
+        if (kind == 1 && (j == 0 || j == N)) wgt = T(2);
+      }
+      V x;
+      x.x = wgt * in[g];
+      x.y = wgt * in[g + ln.N];
+      sE[r * L + pos] = x;
+      if (pos != 0 && 2 * pos != L) {
+        if (odd) {
+          x.x = -x.x;
+          x.y = -x.y;
+        }
+        sE[r * L + L - pos] = x;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
 
   if (Q > 1) {
     // Rader: the DFT of length Q of u_l2 = e_{l1 + P l2} is U_0 = u_0 + sum_q a_q and
@@ -227,8 +285,97 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(FftDev f, const T* __rest
   // j2 * P + bitrev(j1)
   fft_dif(sE, nb * Q, P, logP, sTwP);
 
-  // store: stored index o -> E index and the scale of the transform
   const T invN = T(1) / T(N);
+  if (half) {
+    // one warp per line: A_k, B_k for k = 0..N/2, the even outputs directly and the odd ones
+    // as the base plus a running (warp-scanned) sum of the increments, written by node into sX
+    const int lane = tid & 31, nw = nt >> 5, kmax = N / 2;
+    for (int r = tid >> 5; r < nb; r += nw) {
+      V* X = sX + r * X1;
+      const V* E = sE + r * L;
+      V carry;
+      if (kind == 0) {
+        const V z0 = E[0];  // Z_0 sits at position 0 in every split
+        carry.x = T(0.5) * z0.x;
+        carry.y = T(0.5) * z0.y;
+      } else {
+        T cx = T(0), cy = T(0);
+        for (int j = lane; j <= N; j += 32) {
+          const T c = gCS[j].x * ((j == 0 || j == N) ? T(0.5) : T(1));
+          cx += c * X[j].x;
+          cy += c * X[j].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          cx += __shfl_xor_sync(0xffffffffu, cx, o);
+          cy += __shfl_xor_sync(0xffffffffu, cy, o);
+        }
+        carry.x = cx;
+        carry.y = cy;
+      }
+      __syncwarp();
+      for (int k0 = 0; k0 <= kmax; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k <= kmax;
+        V a{T(0), T(0)}, bb{T(0), T(0)};
+        if (valid) {
+          const int km = k ? N - k : 0;
+          const V zk = E[(k % Q) * P + brev(k / Q, logP)];
+          const V zm = E[(km % Q) * P + brev(km / Q, logP)];
+          a.x = T(0.5) * (zk.x + zm.x);
+          a.y = T(0.5) * (zk.y + zm.y);
+          bb.x = T(-0.5) * (zk.y - zm.y);
+          bb.y = T(0.5) * (zk.x - zm.x);
+        }
+        V inc{T(0), T(0)};
+        if (valid && k >= 1) inc = (kind == 0) ? a : bb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const T tx = __shfl_up_sync(0xffffffffu, inc.x, o), ty = __shfl_up_sync(0xffffffffu, inc.y, o);
+          if (lane >= o) {
+            inc.x += tx;
+            inc.y += ty;
+          }
+        }
+        if (valid) {
+          V od;
+          od.x = carry.x + inc.x;
+          od.y = carry.y + inc.y;
+          if (kind == 0) {
+            if (k >= 1 && 2 * k <= N - 1) X[2 * k] = bb;
+            if (2 * k + 1 <= N - 1) X[2 * k + 1] = od;
+          } else {
+            if (2 * k <= N) X[2 * k] = a;
+            if (2 * k + 1 <= N) X[2 * k + 1] = od;
+          }
+        }
+        carry.x += __shfl_sync(0xffffffffu, inc.x, 31);
+        carry.y += __shfl_sync(0xffffffffu, inc.y, 31);
+      }
+    }
+    __syncthreads();
+    // store: sine forward 2/N, cosine forward (2/N) w_j, inverses 1
+    for (int e = tid; e < nb * m; e += nt) {
+      int r, o;
+      if (ALONG) {
+        r = e / m;
+        o = e - r * m;
+      } else {
+        o = e / nb;
+        r = e - o * nb;
+      }
+      const int j = o + (kind == 0 ? 1 : 0);
+      const T sc = inv ? T(1) : ((kind == 1 && (j == 0 || j == N)) ? invN : T(2) * invN);
+      const V v = sX[r * X1 + j];
+      const int gr = r0 + r;
+      const int64_t g = (int64_t)(gr / ln.rdiv) * ln.hi + (int64_t)(gr % ln.rdiv) * ln.lo + (int64_t)o * ln.es;
+      out[g] = sc * v.x;
+      out[g + ln.N] = sc * v.y;
+    }
+    return;
+  }
+
+  // extension store: stored index o -> E index and the scale of the transform
   for (int e = tid; e < nb * m; e += nt) {
     int r, o;
     if (ALONG) {
@@ -241,11 +388,11 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(FftDev f, const T* __rest
     int eidx;
     T sc;
     if (!inv) {
-      const int j = o + (kind == 1 ? 0 : 1);
+      const int j = o + (kind == 1 ? 0 : 1);  // mode j
       eidx = quarter ? 2 * j - 1 : j;
       sc = (kind == 1 && (j == 0 || j == N)) ? T(0.5) * invN : invN;
     } else {
-      eidx = o + ((kind == 0 || kind == 2) ? 1 : 0);
+      eidx = o + ((kind == 0 || kind == 2) ? 1 : 0);  // node l
       sc = T(0.5);
     }
     const int j1 = eidx / Q, j2 = eidx - j1 * Q;
@@ -317,6 +464,7 @@ size_t smem_of(const FftDev& f, int B, int eb) {
   const size_t V = 2 * (size_t)eb;
   size_t c = (size_t)f.P / 2 + f.M / 2 + f.M + (size_t)B * f.L + (size_t)B * f.P * f.M;
   if (f.Q > 1) c += 2 * (size_t)B * f.P;
+  if (f.half) c += (size_t)B * (f.N + 1);
   return c * V + 2 * (size_t)f.M * sizeof(int);
 }
 
@@ -324,14 +472,15 @@ constexpr size_t kFftSmemMax = 227 * 1024;
 
 }  // namespace
 
-bool fft_make_plan(int n, int lo, int hi, FftHostPlan& h) {
+bool fft_make_plan(int n, int lo, int hi, bool half, FftHostPlan& h) {
   const bool nlo = lo != HELM6_DIRICHLET, nhi = hi != HELM6_DIRICHLET;
   FftDev& f = h.d;
   f = FftDev{};
   f.kind = (!nlo && !nhi) ? 0 : (nlo && nhi) ? 1 : (!nlo) ? 2 : 3;
   f.N = n + 1;
   f.m = n + (nlo ? 1 : 0) + (nhi ? 1 : 0);
-  f.L = (f.kind >= 2 ? 4 : 2) * f.N;
+  f.half = half && f.kind < 2;
+  f.L = f.half ? f.N : (f.kind >= 2 ? 4 : 2) * f.N;
   f.P = 1;
   while (f.L % (2 * f.P) == 0) f.P *= 2;
   f.Q = f.L / f.P;
@@ -345,7 +494,8 @@ bool fft_make_plan(int n, int lo, int hi, FftHostPlan& h) {
   if (smem_of(f, 1, 8) > kFftSmemMax) return false;
 
   // complex tables, interleaved: [w_P^k: P/2][w_M^k: M/2][bhat: M][w_L^t: L when Q > 1]
-  const int nt = f.P / 2 + f.M / 2 + f.M + (f.Q > 1 ? f.L : 0);
+  // [(cos, sin)(pi j / N), j = 0..N: sine and cosine axes]
+  const int nt = f.P / 2 + f.M / 2 + f.M + (f.Q > 1 ? f.L : 0) + (f.half ? f.N + 1 : 0);
   h.tw.assign(2 * (size_t)nt, 0.0);
   double* t = h.tw.data();
   for (int k = 0; k < f.P / 2; ++k, t += 2) unit_root(k, f.P, t[0], t[1]);
@@ -375,6 +525,11 @@ bool fft_make_plan(int n, int lo, int hi, FftHostPlan& h) {
     t += 2 * f.M;
     for (int k = 0; k < f.L; ++k, t += 2) unit_root(k, f.L, t[0], t[1]);
   }
+  if (f.half)
+    for (int j = 0; j <= f.N; ++j, t += 2) {
+      unit_root(j, 2 * f.N, t[0], t[1]);  // exp(-i pi j / N) = (cos, -sin)
+      t[1] = -t[1];
+    }
   return true;
 }
 

@@ -143,15 +143,19 @@ void launch_ztri_table(const Geom& g, const double* lamx, const double* lamy, c6
 // y = the z-line solve of x (planar FP32 in that layout; y may not alias x).
 void launch_ztri_apply(const Geom& g, const ZLines& z, const float* x, float* y, cudaStream_t s);
 
-// FFT-type x/y transforms (fft.cu): the closed-form 1D eigenbasis of one axis applied through a
-// complex DFT of length L = P * Q of the line's odd (sine) or even (cosine) extension.
+// FFT-type x/y transforms (fft.cu): the closed-form 1D eigenbasis of one axis applied through
+// one complex DFT of length L = P * Q per line: of the line's odd or even extension, L = 2(n+1)
+// (sine, cosine) or 4(n+1) (quarter-wave), or, in the half-length form of the sine and cosine
+// axes, L = n + 1 with pre- and post-processing.
 struct FftDev {
   int kind;        // 0 D-D (sine), 1 N-N (cosine), 2 D-N, 3 N-D (quarter-wave)
+  int half;        // half-length form (kinds 0, 1)
   int N;           // intervals n + 1
   int m;           // unknowns on the axis
   int L, P, Q, M;  // L = P Q, P a power of two, Q = 1 or a prime with M = Q - 1 a power of two
   int logP, logM;
   const double2* tw64;  // [w_P^k: P/2][w_M^k: M/2][kernel spectrum / M: M][w_L^t: L if Q > 1]
+                        // [(cos, sin)(pi j / N), j = 0..N: sine and cosine axes]
   const float2* tw32;   // the same in FP32
   const int* gidx;      // [g^q mod Q: M][g^-q mod Q: M]
 };
@@ -160,9 +164,10 @@ struct FftHostPlan {
   std::vector<double> tw;  // the complex tables, interleaved
   std::vector<int> gidx;
 };
-// Plan for n interior nodes and the axis' faces lo, hi (helm6_bc); false when L has no
+// Plan for n interior nodes and the axis' faces lo, hi (helm6_bc), in the half-length form
+// where `half` asks for it and the faces allow it; false when L has no
 // factorisation of the form above or a line does not fit in shared memory.
-bool fft_make_plan(int n, int lo, int hi, FftHostPlan& plan);
+bool fft_make_plan(int n, int lo, int hi, bool half, FftHostPlan& plan);
 void fft_configure();  // once per process: the kernels' dynamic shared memory limit
 // out = W in (inv = 0, forward) or V in (inv = 1) along axis 0 (x) or 1 (y) of the planar
 // field (same layout in and out; out may not alias in).

@@ -1,8 +1,10 @@
 """The FFT-type x/y transforms of the preconditioner (Section 3.3, Eq. 3DAP: the direct solver
 of A_p is "FFT-type"; Section 1: O(N^2 N_z log N) per application), through the C-ABI.
 
-Each axis' closed-form sine/cosine eigenbasis is applied as a complex DFT of length
-L = 2(n+1) (D-D, N-N) or 4(n+1) (D-N, N-D) of the line's odd or even extension, split as
+Each axis' closed-form sine/cosine eigenbasis is applied as one complex DFT per line: of the
+line's odd or even extension, of length L = 2(n+1) for D-D and N-N and 4(n+1) for D-N and
+N-D (FP32), or, for D-D and N-N in FP64, of length n+1 (the sine and cosine transforms
+through pre- and post-processing and a prefix sum), split as
 L = P * Q with P a power of two and Q = 1 or a prime with Q - 1 a power of two (Rader's
 convolution).  The cases below cover every such Q the grids meet (1, 3, 5, 17, 257), the four
 face pairs of an axis, both internal axes, and a problem whose Sommerfeld-like pair is on x
@@ -45,18 +47,20 @@ def rel2(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-# (n, faces): the DFT lengths of the internal x and y axes in the comments
+# (n, faces): the FP64 DFT lengths of the internal x and y axes in the comments (FP32: D-D and
+# N-N twice as long)
 FFT_CASES = [
     (1, "DNNDSS"),     # 8, 8 (P = 8)
-    (2, "DDNNSS"),     # 6, 6 (Q = 3)
+    (2, "DDNNSS"),     # 3, 3 (Q = 3, P = 1)
     (4, "DNNDDD"),     # 20, 20 (Q = 5, P = 4)
-    (15, "NNDDSN"),    # 32, 32
-    (16, "DDNNSS"),    # 34, 34 (Q = 17)
+    (15, "NNDDSN"),    # 16, 16
+    (16, "DDNNSS"),    # 17, 17 (Q = 17)
     (16, "NDDNNN"),    # 68, 68 (Q = 17, P = 4)
-    (31, "SSDDNN"),    # Sommerfeld-like x pair: internal x = the N-N pair, y = D-D: 64, 64
-    (63, "DDDDSS"),    # 128, 128
-    (127, "NNNNDD"),   # 256, 256
-    (256, "DDNNSS"),   # 514, 514 (Q = 257): the 256 x 258 x 258 grid
+    (31, "SSDDNN"),    # Sommerfeld-like x pair: internal x = the N-N pair, y = D-D: 32, 32
+    (33, "NNDDSS"),    # 34, 34 (Q = 17, P = 2)
+    (63, "DDDDSS"),    # 64, 64
+    (127, "NNNNDD"),   # 128, 128
+    (256, "DDNNSS"),   # 257, 257 (Q = 257): the 256 x 258 x 258 grid
 ]
 
 
@@ -71,7 +75,7 @@ def test_fft_apply_Pinv_fp64(H, n, faces):
     assert relmax(y, O.Preconditioner(prob)(x)) < 1e-10
 
 
-@pytest.mark.parametrize("n,faces", [FFT_CASES[i] for i in (1, 2, 4, 5, 8, 9)])
+@pytest.mark.parametrize("n,faces", [FFT_CASES[i] for i in (1, 2, 4, 5, 7, 9, 10)])
 def test_fft_apply_Pinv_fp32(H, n, faces):
     """MIXED with the FFT asked for: FP32 DFTs in place of the tensor-core transforms."""
     k = 9.0 + 0.3j
@@ -84,16 +88,16 @@ def test_fft_apply_Pinv_fp32(H, n, faces):
 
 
 def test_transform_selection(H):
-    """AUTO takes the FFT in FP64 where the length factors (n = 16: L = 34), dense where it
-    does not (n = 20: L = 42 = 2 * 3 * 7); MIXED AUTO keeps the tensor-core transform while
+    """AUTO takes the FFT in FP64 where the length factors (n = 16: L = 17), dense where it
+    does not (n = 20: L = 21 = 3 * 7); MIXED AUTO keeps the tensor-core transform while
     the axes fit it; DENSE keeps the matrices."""
     with H.Solver(16, 5.0, "DDNNSS") as s:
         assert s.transforms == ("fft", "fft")
     with H.Solver(20, 5.0, "DDNNSS") as s:
         assert s.transforms == ("dense", "dense")
-    with H.Solver(18, 5.0, "DDDNSS") as s:     # x: L = 38 = 2 * 19 (no plan), y: D-N, L = 76
+    with H.Solver(18, 5.0, "DDDNSS") as s:     # x: L = 19 (no plan), y: D-N, L = 76 = 4 * 19
         assert s.transforms == ("dense", "dense")
-    with H.Solver(15, 5.0, "DDDNSS") as s:     # x: 32, y: D-N 64
+    with H.Solver(15, 5.0, "DDDNSS") as s:     # x: 16, y: D-N 64
         assert s.transforms == ("fft", "fft")
     with H.Solver(16, 5.0, "DDNNSS", transform="dense") as s:
         assert s.transforms == ("dense", "dense")
@@ -121,8 +125,8 @@ def test_fft_and_dense_solves_agree(H):
 
 def test_fft_1024_point_axes(H, capsys):
     """h = 1/1024: 1023 x 1023 x 1025 = 1.07e9 unknowns with Sommerfeld-like z faces, k = 20,
-    the corrected Table 7/8 test function; the x/y axes (1023 points) go through DFTs of length
-    2048.  MIXED SKS (Algorithm 1) to a relative residual of 1e-10; the error against the exact
+    the corrected Table 7/8 test function; the x/y axes (1023 points) go through FP32 DFTs of
+    length 2048.  MIXED SKS (Algorithm 1) to a relative residual of 1e-10; the error against the exact
     solution at the nodes is reported and must stay below 1e-6 (the sixth-order truncation error
     at this step is far smaller, so this bounds the algebraic error)."""
     n, k = 1023, 20.0
