@@ -316,6 +316,7 @@ def run_ops(args, cfg):
         y, z = s.apply_A(x), s.apply_Pinv(x)
         torch.cuda.synchronize()
         out = {}
+        s.profile(True)
         for name, fn in (("apply_A", lambda: s.apply_A(x, y)), ("apply_Pinv", lambda: s.apply_Pinv(x, z))):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -324,6 +325,10 @@ def run_ops(args, cfg):
             e1.record()
             torch.cuda.synchronize()
             out[name + "_ms"] = e0.elapsed_time(e1) / args.ops
+        prof = s.profile_read()["phases"]
+        s.profile(False)
+        # device time per call of each kernel phase (CUDA events around the launches)
+        out["phase_us"] = {k: 1e3 * v["ms"] / v["count"] for k, v in prof.items() if v["count"] > 0}
         out.update(workload=args.workload, dims=list(s.dims), reps=args.ops, precision=args.ops_precision,
                    transforms="/".join(s.transforms),
                    max_abs_Ax=float(y.abs().max()), max_abs_Pinv_x=float(z.abs().max()))

@@ -1474,10 +1474,14 @@ int helm6_apply_A(helm6_ctx* c, const void* x, void* y) {
   const int64_t N = c->g.N;
   launch_caller_to_planar(c->g, c->xaxis, (const double*)x, c->R64, s);
   if (c->opts.precision == HELM6_FP64) {
+    cudaEvent_t e = prof_start(c);
     launch_stencil<double>(c->g, c->coef, c->R64, c->E64, nullptr, nullptr, 0, nullptr, nullptr, s);
+    prof_stop(c, HELM6_PH_STENCIL, e);
   } else {
     launch_convert<double, float>(c->R64, c->w32, N, 1.0, s);
+    cudaEvent_t e = prof_start(c);
     launch_stencil<float>(c->g, c->coef, c->w32, c->zt32, nullptr, nullptr, 0, nullptr, nullptr, s);
+    prof_stop(c, HELM6_PH_STENCIL, e);
     launch_convert<float, double>(c->zt32, c->E64, N, 1.0, s);
   }
   launch_planar_to_caller(c->g, c->xaxis, c->E64, (double*)y, s);

@@ -227,13 +227,21 @@ __device__ __forceinline__ int ghost_index(int gi, int m, int lo_neumann, int hi
   return gi;
 }
 
+// The FP32 kernel's weights, rounded to FP32 once on the host (a conversion per thread and
+// weight would run on the FP64 pipe): the four interior class weights and the two
+// Sommerfeld-like face rows.
+struct StencilCoef32 {
+  cpx<float> c[4];
+  cpx<float> lo[3][3], hi[3][3];
+};
+
 // NORM: accumulate the block's |y|^2 (FP64) into sumsq; a compile-time flag so that the
 // FP32 path carries no FP64 arithmetic when no norm is wanted.
 // RW: the interior weights are real (a real wavenumber), so each class term is two real
 // FMAs instead of a complex multiply-add.
 template <int MODE, bool NORM, bool RW>
 __global__ void __launch_bounds__(T4X* T4Y / T4R)
-    stencil4_kernel(Geom g, StencilCoef coef, const float* __restrict__ x, float* __restrict__ y,
+    stencil4_kernel(Geom g, StencilCoef32 coef, const float* __restrict__ x, float* __restrict__ y,
                     const float* __restrict__ f, double* __restrict__ sumsq) {
   constexpr int DIST = 3, NBUF = DIST + 2;
   constexpr int NT = T4X * T4Y / T4R;  // 128 threads
@@ -321,20 +329,7 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
     }
   };
 
-  const cpx<float> c0 = cast<float>(coef.interior.w[1][0]);
-  const cpx<float> c1 = cast<float>(coef.interior.w[1][1]);
-  const cpx<float> c2 = cast<float>(coef.interior.w[1][2]);
-  const cpx<float> c3 = cast<float>(coef.interior.w[0][2]);
-  // Sommerfeld-like face rows of this block, if any (one z chunk holds at most one such
-  // face plane when Z4CH < mz; both when the chunk spans the whole axis)
-  cpx<float> wlo[3][3], whi[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      wlo[a][b] = cast<float>(coef.s_lo.w[a][b]);
-      whi[a][b] = cast<float>(coef.s_hi.w[a][b]);
-    }
+  const cpx<float> c0 = coef.c[0], c1 = coef.c[1], c2 = coef.c[2], c3 = coef.c[3];
   const cpx<float> zero = {0.f, 0.f};
   // plane sums of three consecutive planes, rotated by renaming: the loop below is
   // unrolled by three so that no register moves are needed
@@ -407,9 +402,9 @@ __global__ void __launch_bounds__(T4X* T4Y / T4R)
           out = zero;
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            const cpx<float> wc = slo ? wlo[0][a] : whi[0][a];
-            const cpx<float> wm = slo ? wlo[1][a] : whi[1][a];
-            const cpx<float> wp = slo ? wlo[2][a] : whi[2][a];
+            const cpx<float> wc = slo ? coef.lo[0][a] : coef.hi[0][a];
+            const cpx<float> wm = slo ? coef.lo[1][a] : coef.hi[1][a];
+            const cpx<float> wp = slo ? coef.lo[2][a] : coef.hi[2][a];
             const cpx<float> s0 = (a == 0) ? P0[r].c : (a == 1) ? P0[r].n : P0[r].d;
             const cpx<float> s1 = (a == 0) ? P1[r].c : (a == 1) ? P1[r].n : P1[r].d;
             const cpx<float> s2 = (a == 0) ? PN[r].c : (a == 1) ? PN[r].n : PN[r].d;
@@ -470,15 +465,23 @@ void launch_stencil(const Geom& g, const StencilCoef& c, const T* x, T* y, const
     const float* xf = (const float*)x;
     float* yf = (float*)y;
     const float* ff = (const float*)f;
+    StencilCoef32 c32;
+    const c64d* cw[4] = {&c.interior.w[1][0], &c.interior.w[1][1], &c.interior.w[1][2], &c.interior.w[0][2]};
+    for (int q = 0; q < 4; ++q) c32.c[q] = cpx<float>{(float)cw[q]->re, (float)cw[q]->im};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        c32.lo[a][b] = cpx<float>{(float)c.s_lo.w[a][b].re, (float)c.s_lo.w[a][b].im};
+        c32.hi[a][b] = cpx<float>{(float)c.s_hi.w[a][b].re, (float)c.s_hi.w[a][b].im};
+      }
     const bool nrm = sumsq != nullptr;
     const bool rw = c.interior.w[1][0].im == 0.0 && c.interior.w[1][1].im == 0.0 &&
                     c.interior.w[1][2].im == 0.0 && c.interior.w[0][2].im == 0.0;
 #define HELM6_S4(M, N)                                                                   \
   do {                                                                                   \
     if (rw)                                                                              \
-      stencil4_kernel<M, N, true><<<grid, block, 0, s>>>(g, c, xf, yf, ff, N ? sumsq : nullptr);  \
+      stencil4_kernel<M, N, true><<<grid, block, 0, s>>>(g, c32, xf, yf, ff, N ? sumsq : nullptr);  \
     else                                                                                 \
-      stencil4_kernel<M, N, false><<<grid, block, 0, s>>>(g, c, xf, yf, ff, N ? sumsq : nullptr); \
+      stencil4_kernel<M, N, false><<<grid, block, 0, s>>>(g, c32, xf, yf, ff, N ? sumsq : nullptr); \
   } while (0)
     if (mode == 0 && !nrm)
       HELM6_S4(0, false);
