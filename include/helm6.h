@@ -225,17 +225,23 @@ int helm6_rhs_gaussians(helm6_ctx* ctx, int nsrc, const double* centers,
 int helm6_rhs_separable(helm6_ctx* ctx, int nterms, const helm6_c64* coef, const helm6_c64* tables,
                         void* F);
 
-/* Inhomogeneous Dirichlet data on a z face (Section 4.2: u = u_b at z = 1 with the Neumann
+/* Inhomogeneous Dirichlet data on a face (Section 4.2: u = u_b at z = 1 with the Neumann
  * face at z = 0, Tables 5 and 6): the face's nodes are known, so their contribution to the
- * rows of the neighbouring plane moves to the right side,
- *     F(l, j, i) -= sum_{|di|,|dj| <= 1} w(di, dj) u_b(j + dj, i + di),
- * w the weights of the interior rows' z +- 1 plane in Eq. scheme (centre, 4 neighbours, 4
- * diagonals).  face: 4 (z = 0) or 5 (z = top), a Dirichlet face of the context; data: DEVICE
- * complex128 array of (my + 2) x (mx + 2) values on the face's node layer, x fastest, with
- * its ring (entry (j + 1, i + 1) is the node above/below unknown (i, j); the ring holds the
- * nodes on the neighbouring faces' ghost columns and rows); F: DEVICE complex128, updated in
- * place.  Stream-ordered.  Returns OK, INVALID (NULL argument, face not Dirichlet),
- * UNSUPPORTED (an x or y face, or a context with Sommerfeld-like faces on x or y) or CUDA. */
+ * rows next to the face moves to the right side,
+ *     F(row) -= sum over the face's nodes in the row's 3 x 3 window of w * u_b(node),
+ * w the row's 27-point weight for the node's offset (Eq. scheme's class weights; on a
+ * Sommerfeld-like z face row, that row's weights, Eq. 3DDISCS).  face: 0..5 = x0 x1 y0 y1 z0
+ * z1, a Dirichlet face of the context.  data: DEVICE complex128 node layer of the face, x
+ * fastest, with a one-node ring in the tangential axes that come before the face's own in the
+ * order x, y, z (so that a node on an edge belongs to one face only; where a neighbouring
+ * face without a ring entry is Neumann, the ghost node is its reflection, U_-1 = U_1, and its
+ * value is read from the data):
+ *     x faces  [mz][my]            entry (l, j): the node beside unknown row (j, l)
+ *     y faces  [mz][mx + 2]        entry (l, i + 1): beside unknown (i, l); ring in x
+ *     z faces  [my + 2][mx + 2]    entry (j + 1, i + 1): beside unknown (i, j); ring in x, y
+ * F: DEVICE complex128, updated in place.  Stream-ordered.  Returns OK, INVALID (NULL
+ * argument, face out of range or not Dirichlet), UNSUPPORTED (a context with
+ * Sommerfeld-like faces on x or y) or CUDA. */
 int helm6_lift_dirichlet(helm6_ctx* ctx, int face, const void* data, void* F);
 
 /* ---- Measurement (not part of the method) ----

@@ -1685,10 +1685,10 @@ int helm6_rhs_separable(helm6_ctx* c, int nterms, const helm6_c64* coef, const h
 
 int helm6_lift_dirichlet(helm6_ctx* c, int face, const void* data, void* F) {
   if (!c || !data || !F) return HELM6_ERR_INVALID;
-  if (face != 4 && face != 5) return HELM6_ERR_UNSUPPORTED;
+  if (face < 0 || face > 5) return HELM6_ERR_INVALID;
   if (c->xaxis >= 0) return HELM6_ERR_UNSUPPORTED;
   if (c->gu.face[face] != HELM6_DIRICHLET) return HELM6_ERR_INVALID;
-  return lift_dirichlet_z(c->gu, c->coef, face - 4, (const double*)data, (double*)F, c->stream);
+  return lift_dirichlet(c->gu, c->coef, face, (const double*)data, (double*)F, c->stream);
 }
 
 }  // extern "C"

@@ -220,10 +220,11 @@ int rhs_gaussians(const Geom& g, double h, cd k, int nsrc, const double* centers
 int rhs_separable(const Geom& g, double h, cd k, int nterm, const double* coef, const double* tables, double* F,
                   cudaStream_t s);
 
-// F -= the contribution of known Dirichlet values ub ((my + 2) x (mx + 2) complex128, the
-// face's node layer with its ring) on the z face `side` (0: z = 0, 1: z = top) to the
-// neighbouring plane's rows; F complex128 interleaved in geometry g.
-int lift_dirichlet_z(const Geom& g, const StencilCoef& coef, int side, const double* ub, double* F, cudaStream_t s);
+// F -= the contribution of known Dirichlet values ub on face `face` (0..5 = x0 x1 y0 y1 z0 z1)
+// to the rows next to it; ub complex128, the face's node layer x fastest with a ring in the
+// tangential axes padded before the face's own (x faces [mz][my], y faces [mz][mx + 2], z faces
+// [my + 2][mx + 2]); F complex128 interleaved in geometry g.
+int lift_dirichlet(const Geom& g, const StencilCoef& coef, int face, const double* ub, double* F, cudaStream_t s);
 
 // y += alpha x (planar, 2N reals), mixed input/output precision.
 template <typename TI, typename TO>

@@ -16,6 +16,8 @@
 
 #include "helm6_internal.h"
 
+#include <climits>
+
 namespace helm6 {
 
 namespace {
@@ -216,30 +218,64 @@ namespace {
 // w = the interior rows' weights of the z +- 1 plane (centre c1, 4 neighbours c2, 4
 // diagonals c3 of Eq. scheme).  ub: (my + 2) x (mx + 2) complex128 values on the face's
 // node layer, ring included (the nodes of the neighbouring faces' ghost columns and rows).
-__global__ void lift_z_kernel(Geom g, c64d w0, c64d w1, c64d w2, int l, const double* __restrict__ ub,
-                              double* __restrict__ F) {
+// Rows next to a Dirichlet face with known values u_b: the face's nodes enter those rows
+// through the 27-point weights of the row (interior, or the Sommerfeld-like face rows on z),
+// F -= sum over the face's nodes in the row's 3 x 3 window of w * u_b.  A node's weight is the
+// row's class weight for its offset: the plane offset along z and the number of nonzero
+// in-plane (x, y) offsets (the interior weights are the same for any axis).  The face data
+// holds a ring in the tangential axes that are padded before the face's own axis (x, then y,
+// then z), so an edge node belongs to exactly one face: x faces [mz][my], y faces
+// [mz][mx + 2], z faces [my + 2][mx + 2].
+__global__ void lift_face_kernel(Geom g, RowWeights win, RowWeights wlo, RowWeights whi, int axis, int side,
+                                 const double* __restrict__ ub, double* __restrict__ F) {
+  const int m[3] = {g.mx, g.my, g.mz};
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;  // tangential axes, a1 < a2
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)g.mx * g.my) return;
-  const int i = (int)(t % g.mx), j = (int)(t / g.mx);
-  const int ld = g.mx + 2;
-  auto at = [&](int jj, int ii) { const int64_t o = (int64_t)jj * ld + ii; return Z{ub[2 * o], ub[2 * o + 1]}; };
-  const Z c = at(j + 1, i + 1);
-  const Z n = at(j, i + 1) + at(j + 2, i + 1) + at(j + 1, i) + at(j + 1, i + 2);
-  const Z d = at(j, i) + at(j, i + 2) + at(j + 2, i) + at(j + 2, i + 2);
-  const Z s = zc(w0) * c + zc(w1) * n + zc(w2) * d;
-  const int64_t o = (int64_t)l * g.mx * g.my + t;
+  if (t >= (int64_t)m[a1] * m[a2]) return;
+  const int u1 = (int)(t % m[a1]), u2 = (int)(t / m[a1]);
+  int c[3];
+  c[axis] = side ? m[axis] - 1 : 0;
+  c[a1] = u1;
+  c[a2] = u2;
+  const RowWeights& W = (c[2] == 0 && g.face[4] == HELM6_SOMMERFELD)            ? wlo
+                        : (c[2] == m[2] - 1 && g.face[5] == HELM6_SOMMERFELD) ? whi
+                                                                              : win;
+  const int r1 = a1 < axis ? 1 : 0, r2 = a2 < axis ? 1 : 0;
+  const int ld = m[a1] + 2 * r1;
+  // a node beyond the data along a tangential axis: a Neumann face there reflects the ghost
+  // onto the data (U_{-1} = U_1); otherwise it belongs to another face's data or is zero
+  auto fold = [&](int q, int a, int ring) -> int {
+    if (q >= -ring && q < m[a] + ring) return q;
+    if (q < 0) return g.face[2 * a] == HELM6_NEUMANN ? 1 : INT_MIN;
+    return g.face[2 * a + 1] == HELM6_NEUMANN ? m[a] - 2 : INT_MIN;
+  };
+  Z s{0.0, 0.0};
+  for (int d2 = -1; d2 <= 1; ++d2)
+    for (int d1 = -1; d1 <= 1; ++d1) {
+      const int p1 = fold(u1 + d1, a1, r1), p2 = fold(u2 + d2, a2, r2);
+      if (p1 == INT_MIN || p2 == INT_MIN) continue;
+      int o[3];
+      o[axis] = side ? 1 : -1;
+      o[a1] = d1;
+      o[a2] = d2;
+      const int cls = (o[0] != 0) + (o[1] != 0);
+      const int64_t q = (int64_t)(p2 + r2) * ld + (p1 + r1);
+      s = s + zc(W.w[o[2] + 1][cls]) * Z{ub[2 * q], ub[2 * q + 1]};
+    }
+  const int64_t o = ((int64_t)c[2] * m[1] + c[1]) * m[0] + c[0];
   F[2 * o] -= s.re;
   F[2 * o + 1] -= s.im;
 }
 
 }  // namespace
 
-int lift_dirichlet_z(const Geom& g, const StencilCoef& coef, int side, const double* ub, double* F, cudaStream_t s) {
-  const RowWeights& w = coef.interior;
-  const int l = side ? g.mz - 1 : 0;
-  const int64_t n = (int64_t)g.mx * g.my;
+int lift_dirichlet(const Geom& g, const StencilCoef& coef, int face, const double* ub, double* F, cudaStream_t s) {
+  const int axis = face / 2, side = face % 2;
+  const int m[3] = {g.mx, g.my, g.mz};
+  const int64_t n = (int64_t)m[axis == 0 ? 1 : 0] * m[axis == 2 ? 1 : 2];
   note_launch();
-  lift_z_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, w.w[2][0], w.w[2][1], w.w[2][2], l, ub, F);
+  lift_face_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, coef.interior, coef.s_lo, coef.s_hi, axis, side,
+                                                                ub, F);
   return cudaGetLastError() == cudaSuccess ? (int)HELM6_OK : (int)HELM6_ERR_CUDA;
 }
 

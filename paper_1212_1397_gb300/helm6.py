@@ -330,13 +330,15 @@ class Solver:
         return F
 
     def lift_dirichlet(self, face, data, F):
-        """F -= the contribution of Dirichlet values `data` ((my+2) x (mx+2) complex128 CUDA
-        tensor, the face's node layer with its ring) on z face `face` ("z0" or "z1")."""
+        """F -= the contribution of Dirichlet values `data` (complex128 CUDA tensor, the face's
+        node layer: x faces (mz, my), y faces (mz, mx+2), z faces (my+2, mx+2)) on face
+        `face` ("x0", "x1", "y0", "y1", "z0" or "z1")."""
         import torch
-        fi = {"z0": 4, "z1": 5}[face]
-        mx, my, _ = self.dims
-        if not isinstance(data, torch.Tensor) or tuple(data.shape) != (my + 2, mx + 2):
-            raise ValueError(f"data must have shape {(my + 2, mx + 2)}")
+        fi = {"x0": 0, "x1": 1, "y0": 2, "y1": 3, "z0": 4, "z1": 5}[face]
+        mx, my, mz = self.dims
+        shape = [(mz, my), (mz, mx + 2), (my + 2, mx + 2)][fi // 2]
+        if not isinstance(data, torch.Tensor) or tuple(data.shape) != shape:
+            raise ValueError(f"data must have shape {shape}")
         _check(self._lib.helm6_lift_dirichlet(self._ctx, fi, _ptr(data), _ptr(F)), "helm6_lift_dirichlet")
         return F
 

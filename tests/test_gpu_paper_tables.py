@@ -225,24 +225,33 @@ def table5_boundary(prob, k):
     return (X3(xs)[None, :] * S.poly_times([0, 1, -1], S.cos1d(k * np.pi))(xs)[:, None]) * S.cos1d(k * np.pi)(1.0)
 
 
-@pytest.mark.parametrize("n,k,faces", [(13, 20.0, "DDDDND"), (11, 7.0 + 0.5j, "NNDDDD"), (9, 3.0, "DNNDSD")])
+@pytest.mark.parametrize("n,k,faces", [(13, 20.0, "DDDDND"), (11, 7.0 + 0.5j, "NNDDDD"), (9, 3.0, "DNNDSD"),
+                                       (10, 6.0 + 0.2j, "DDDDSS"), (8, 4.0, "DDNDSN")])
 def test_lift_dirichlet_matches_oracle(H, n, k, faces):
     """helm6_lift_dirichlet against the oracle's lifting (F - A(0; u_b)), elementwise, on
-    random face data for either z face."""
+    random face data for every Dirichlet face, one face at a time and all of them together
+    (the data layouts follow the oracle's padding order x, y, z: an edge node belongs to the
+    later face's ring)."""
     import helm6_inputs as inputs
     prob = O.Problem(n, k, faces)
     mx, my, mz = prob.dims
+    shapes = {0: (mz, my), 1: (mz, mx + 2), 2: (my + 2, mx + 2)}
+    names = ["x0", "x1", "y0", "y1", "z0", "z1"]
     F = inputs.complex_normal(40 + n, prob.shape)
-    for side in (0, 1):
-        if faces[4 + side] != "D":
-            continue
-        ub = inputs.complex_normal(50 + n + side, (my + 2, mx + 2))
-        ref = O.lift_dirichlet(prob, F, {(2, side): ub})
-        with H.Solver(n, k, faces, precision=H.FP64) as s:
+    data = {}
+    for f in range(6):
+        if faces[f] == "D":
+            data[(f // 2, f % 2)] = inputs.complex_normal(50 + n + f, shapes[f // 2])
+    assert data
+    with H.Solver(n, k, faces, precision=H.FP64) as s:
+        for key, ub in list(data.items()) + [("all", None)]:
+            items = data.items() if key == "all" else [(key, ub)]
+            ref = O.lift_dirichlet(prob, F, dict(items))
             Fd = torch.from_numpy(F.copy()).cuda()
-            s.lift_dirichlet("z1" if side else "z0", torch.from_numpy(ub).cuda(), Fd)
+            for (axis, side), u in items:
+                s.lift_dirichlet(names[2 * axis + side], torch.from_numpy(u).cuda(), Fd)
             got = Fd.cpu().numpy()
-        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (faces, side)
+            assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), (faces, key)
 
 
 def sks_ratio(H, prob, F):
