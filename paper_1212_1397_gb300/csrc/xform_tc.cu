@@ -198,7 +198,10 @@ __device__ __forceinline__ void split8(const float4& a, const float4& b, uint4& 
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <int VEC>
+// TAIL: whether the kernel forms FP32 tail columns at all (a compile-time switch: the tail code
+// left in the converter loop of a transform without tail columns costs it 10-15 %, measured;
+// with tail columns the runtime test on p.tail stays, which measured faster than without)
+template <int VEC, bool TAIL>
 __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -364,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
         const int off = kg * A_LBO + (r >> 3) * 128 + (r & 7) * 16;
         *(uint4*)(sA + off) = hi;
         *(uint4*)(sA + A_TILE + off) = lo;
-        if (p.tail) {
+        if (TAIL && p.tail) {
 #pragma unroll
           for (int c = 0; c < TC_TAILMAX; ++c) {
             if (c < p.tail) {
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) xform_tc_kernel(TcArgs p) {
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(afull(s)) : "memory");
       issue(g + ND);
-      if (p.tail && kt == p.nk - 1) {
+      if (TAIL && p.tail && kt == p.nk - 1) {
         // the two k halves of a row are in lanes l and l + 16
 #pragma unroll
         for (int c = 0; c < TC_TAILMAX; ++c) tacc[c] += __shfl_xor_sync(0xffffffffu, tacc[c], 16);
@@ -605,16 +608,27 @@ void tc_prepare_basis(const std::vector<double>& B, int P, int K, std::vector<ui
 // Largest axis length the tensor-core transform takes (two column groups of 256).
 int tc_max_axis() { return 2 * TC_GMAX; }
 
+namespace {
+template <int VEC>
+int set_smem() {
+  return cudaFuncSetAttribute(xform_tc_kernel<VEC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+             cudaSuccess ||
+         cudaFuncSetAttribute(xform_tc_kernel<VEC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
+             cudaSuccess;
+}
+template <int VEC>
+void launch_vec(const TcArgs& a, unsigned grid, cudaStream_t s) {
+  if (a.tail)
+    xform_tc_kernel<VEC, true><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+  else
+    xform_tc_kernel<VEC, false><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+}
+}  // namespace
+
 int tc_configure() {
   static int done = 0;
   if (done) return HELM6_OK;
-  if (cudaFuncSetAttribute(xform_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(xform_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(xform_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) !=
-          cudaSuccess)
-    return HELM6_ERR_CUDA;
+  if (set_smem<16>() || set_smem<8>() || set_smem<4>()) return HELM6_ERR_CUDA;
   done = 1;
   return HELM6_OK;
 }
@@ -657,11 +671,11 @@ void launch_xform_tc(const float* in, float* out, const uint8_t* W, int M_total,
   note_launch();
   const uintptr_t ia = (uintptr_t)in;
   if (a.ldin % 4 == 0 && ia % 16 == 0)
-    xform_tc_kernel<16><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+    launch_vec<16>(a, grid, s);
   else if (a.ldin % 2 == 0 && ia % 8 == 0)
-    xform_tc_kernel<8><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+    launch_vec<8>(a, grid, s);
   else
-    xform_tc_kernel<4><<<grid, TC_THREADS, SMEM_BYTES, s>>>(a);
+    launch_vec<4>(a, grid, s);
 }
 
 }  // namespace helm6
