@@ -10,16 +10,21 @@
 // flat FP32 vector (per layer W[c_out][c_in][dz][dy][dx], then b[c_out]); the kernels use
 // BF16-rounded weights, BF16 activations between layers, FP32 accumulation, FP32 biases.
 //
-// Kernels (SIMT, one output point per thread, 32x4x2-point tiles with the input halo and
-// all taps of a layer staged in shared memory as FP32):
-//   conv_kernel   forward layer; also the input gradient (the transpose of a zero-padded
-//                 correlation is the correlation with the flipped, channel-transposed taps)
-//   wgrad_kernel  weight and bias gradients, block partials over persistent tiles
-//   mse_kernel, adam_kernel, prep_kernel (BF16 taps in both layouts from the master vector)
+// Kernels:
+//   conv_tc_kernel  a layer as a tensor-core implicit GEMM (tcgen05, TMEM accumulators): the
+//                   field path's four layers, the trainer's forward layers (FP32
+//                   pre-activations kept) and its input gradients (the transpose of a
+//                   zero-padded correlation is the correlation with the flipped,
+//                   channel-transposed taps; the FP32 gradient split into BF16 hi + lo)
+//   wgrad_kernel    weight and bias gradients (SIMT, 32x4x2-point tiles with the input halo
+//                   staged in shared memory), block partials over persistent tiles
+//   mse_kernel, adam_kernel, prep_tc_kernel / prep_tcb_kernel (BF16 taps in the layouts the
+//   tensor-core kernel reads, from the master vector)
 #include <cuda_bf16.h>
 
 #include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "helm6_internal.h"
@@ -40,20 +45,16 @@ struct PStride {
   static constexpr int v = (C == 16) ? 20 : C;
 };
 
-enum { IN_F32 = 0, IN_BF16 = 1, IN_PLANAR = 2 };
+// IN_G32 (tensor-core kernel only): FP32 gradients split into BF16 hi + lo operand copies
+enum { IN_F32 = 0, IN_BF16 = 1, IN_PLANAR = 2, IN_G32 = 3 };
 enum { OUT_HIDDEN = 0, OUT_F32 = 1, OUT_FIELD = 2, OUT_GRAD = 3 };
 
+// The SIMT weight-gradient kernel's view of a batch of images.
 struct ConvArgs {
   int nb, nz, ny, nx;  // images and their size (x fastest, channel-last)
   int tx, ty, tz;      // tiles per axis
-  const void* in;
+  const void* in;      // the layer's input activations: IN_F32 [N][CIN] or IN_BF16 [N][16]
   int round_in;        // IN_F32: round the input to BF16 first
-  const float* w;      // taps [27][CIN][COUT]
-  const float* bias;   // [COUT] or null
-  float* pre;          // OUT_HIDDEN: FP32 pre-activations written (nullable); OUT_GRAD: read
-  void* out;
-  const double* sumsq;  // IN_PLANAR and OUT_FIELD: sum of |t|^2 over the input field
-  float out_scale;      // OUT_FIELD: c
 };
 
 __device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -84,28 +85,17 @@ __device__ __forceinline__ void tile_origin(const ConvArgs& a, int64_t tile, int
   z0 = bz * TZc;
 }
 
-__device__ __forceinline__ float plane_scale(const ConvArgs& a, int64_t npts) {
-  const double ss = *a.sumsq;
-  return ss > 0.0 ? (float)(1.0 / sqrt(ss / (double)npts)) : 0.f;
-}
-
 // Stage the input halo of one tile into sx (HP points x PStride<CIN> floats).
 template <int CIN, int IN>
-__device__ __forceinline__ void load_halo(const ConvArgs& a, int img, int z0, int y0, int x0, float sc,
-                                          float* sx) {
+__device__ __forceinline__ void load_halo(const ConvArgs& a, int img, int z0, int y0, int x0, float* sx) {
   constexpr int PS = PStride<CIN>::v;
-  const int64_t npts = (int64_t)a.nb * a.nz * a.ny * a.nx;
   for (int i = threadIdx.x; i < HP; i += NT) {
     const int hx = i % HX, r = i / HX, hy = r % HY, hz = r / HY;
     const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
     const bool ok = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
     const int64_t p = (((int64_t)img * a.nz + gz) * a.ny + gy) * a.nx + gx;
     float* d = sx + i * PS;
-    if constexpr (IN == IN_PLANAR) {
-      const float* f = (const float*)a.in;
-      d[0] = ok ? bf16r(f[p] * sc) : 0.f;
-      d[1] = ok ? bf16r(f[npts + p] * sc) : 0.f;
-    } else if constexpr (IN == IN_BF16) {
+    if constexpr (IN == IN_BF16) {
       static_assert(IN != IN_BF16 || CIN == 16, "BF16 activations carry 16 channels");
       uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
       if (ok) {
@@ -139,99 +129,6 @@ __device__ __forceinline__ void load_halo(const ConvArgs& a, int img, int z0, in
   }
 }
 
-template <int CIN, int COUT, int IN, int OUT>
-__global__ void __launch_bounds__(NT, 2) conv_kernel(ConvArgs a) {
-  extern __shared__ __align__(16) float smem[];
-  constexpr int PS = PStride<CIN>::v;
-  float* sw = smem;                  // 27 * CIN * COUT
-  float* sx = smem + 27 * CIN * COUT;  // HP * PS (27*CIN*COUT is a multiple of 4)
-  const int tid = threadIdx.x;
-  const int64_t npts = (int64_t)a.nb * a.nz * a.ny * a.nx;
-  for (int i = tid; i < 27 * CIN * COUT; i += NT) sw[i] = a.w[i];
-  int img, z0, y0, x0;
-  tile_origin(a, blockIdx.x, img, z0, y0, x0);
-  const float sc = (IN == IN_PLANAR) ? plane_scale(a, npts) : 1.f;
-  load_halo<CIN, IN>(a, img, z0, y0, x0, sc, sx);
-  __syncthreads();
-
-  const int lx = tid % TXc, ly = (tid / TXc) % TYc, lz = tid / (TXc * TYc);
-  float acc[COUT];
-#pragma unroll
-  for (int o = 0; o < COUT; ++o) acc[o] = a.bias ? a.bias[o] : 0.f;
-  const int base = (lz * HY + ly) * HX + lx;
-#pragma unroll 1
-  for (int t = 0; t < 27; ++t) {
-    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
-    const float* xp = sx + (base + (dz * HY + dy) * HX + dx) * PS;
-    const float* wp = sw + t * CIN * COUT;
-    float xv[CIN];
-    if constexpr (CIN == 16) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float4 v = ((const float4*)xp)[c];
-        xv[4 * c] = v.x;
-        xv[4 * c + 1] = v.y;
-        xv[4 * c + 2] = v.z;
-        xv[4 * c + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CIN; ++c) xv[c] = xp[c];
-    }
-#pragma unroll
-    for (int ci = 0; ci < CIN; ++ci) {
-      if constexpr (COUT == 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 w4 = ((const float4*)(wp + ci * COUT))[q];
-          acc[4 * q] = fmaf(xv[ci], w4.x, acc[4 * q]);
-          acc[4 * q + 1] = fmaf(xv[ci], w4.y, acc[4 * q + 1]);
-          acc[4 * q + 2] = fmaf(xv[ci], w4.z, acc[4 * q + 2]);
-          acc[4 * q + 3] = fmaf(xv[ci], w4.w, acc[4 * q + 3]);
-        }
-      } else {
-#pragma unroll
-        for (int o = 0; o < COUT; ++o) acc[o] = fmaf(xv[ci], wp[ci * COUT + o], acc[o]);
-      }
-    }
-  }
-
-  const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-  if (gx >= a.nx || gy >= a.ny || gz >= a.nz) return;
-  const int64_t p = (((int64_t)img * a.nz + gz) * a.ny + gy) * a.nx + gx;
-  if constexpr (OUT == OUT_HIDDEN) {
-    static_assert(OUT != OUT_HIDDEN || COUT == 16, "hidden layers have 16 channels");
-    if (a.pre) {
-      float4* pr = (float4*)(a.pre + p * 16);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) pr[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-    }
-    uint32_t pk[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) pk[q] = pack_bf16(gelu_f(acc[2 * q]), gelu_f(acc[2 * q + 1]));
-    uint4* o4 = (uint4*)a.out + 2 * p;
-    o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-  } else if constexpr (OUT == OUT_F32) {
-    float* o = (float*)a.out + p * COUT;
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) o[c] = acc[c];
-  } else if constexpr (OUT == OUT_GRAD) {
-    const float* pr = a.pre + p * COUT;
-    float* o = (float*)a.out + p * COUT;
-#pragma unroll
-    for (int c = 0; c < COUT; ++c) o[c] = acc[c] * gelu_df(pr[c]);
-  } else {  // OUT_FIELD: z += c s y on the planar complex field
-    static_assert(OUT != OUT_FIELD || COUT == 2, "the field output has 2 channels");
-    const double ss = *a.sumsq;
-    if (!(ss > 0.0)) return;
-    const float cs = a.out_scale * (float)sqrt(ss / (double)npts);
-    float* z = (float*)a.out;
-    z[p] = fmaf(cs, acc[0], z[p]);
-    z[npts + p] = fmaf(cs, acc[1 % COUT], z[npts + p]);
-  }
-}
-
 // Weight and bias gradients of one layer: dW[t][ci][co] = sum_p in[p + d_t][ci] g[p][co],
 // db[co] = sum_p g[p][co].  Persistent blocks over tiles, one partial row per block.
 template <int CIN, int COUT, int IN>
@@ -260,7 +157,7 @@ __global__ void __launch_bounds__(NT) wgrad_kernel(ConvArgs a, const float* __re
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int img, z0, y0, x0;
     tile_origin(a, tile, img, z0, y0, x0);
-    load_halo<CIN, IN>(a, img, z0, y0, x0, 1.f, sx);
+    load_halo<CIN, IN>(a, img, z0, y0, x0, sx);
     {
       const int lx = tid % TXc, ly = (tid / TXc) % TYc, lz = tid / (TXc * TYc);
       const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
@@ -420,13 +317,17 @@ __global__ void resid_loss_kernel(int nb, int nz, int ny, int nx, const float* _
 // is 128 B, so every tap's A operand is the same descriptor with its start address moved
 // by the tap offset.  The 8 tiles (4 halo rows x 32 points each: y rows 1-4 and 5-8 of
 // z planes 1-4) accumulate in 8 x 16 TMEM columns; outputs at halo columns are computed
-// and dropped.
+// and dropped.  The same kernel serves the trainer on batches of images (zero padding at
+// every image face): its forward layers (FP32 pre-activations kept) and the input gradients
+// of the backward pass, whose FP32 gradient operand is split into BF16 hi + lo copies (two
+// more channel planes; 54 MMAs per tile) so that it keeps FP32-like accuracy.
 constexpr int BX = 30, BY = 8, BZ = 4;                       // output points of a brick
 constexpr int GX = BX + 2, GY = BY + 2, GZ = BZ + 2, GP = GX * GY * GZ;  // halo (GX = 32)
 constexpr int TC_TILES = BZ * BY / 4;                         // 128-point tiles of a brick
 constexpr int PLANE_B = (GP + 2) * 16;                        // one point of padding each end
 constexpr int TCW_TAP = 512;                                  // bytes of one tap's 16 x 16 BF16
 constexpr size_t TC_SMEM = 1024 + 2 * (size_t)PLANE_B + 27 * TCW_TAP + 256;
+constexpr size_t TC_SMEM4 = 1024 + 4 * (size_t)PLANE_B + 27 * TCW_TAP + 256;  // IN_G32: hi and lo planes
 constexpr int kConvPolls = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -452,12 +353,17 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool ok) {
 }
 
 struct TcConvArgs {
-  int nz, ny, nx;
-  int bx, by, bz;        // bricks per axis
-  const void* in;        // IN_BF16: [N][16] BF16; IN_PLANAR: planar FP32 complex field
+  int nb;                // images (1 for the field path)
+  int nz, ny, nx;        // size of an image
+  int bx, by, bz;        // bricks per axis of an image
+  const void* in;        // IN_BF16: [N][16] BF16; IN_PLANAR: planar FP32 complex field;
+                         // IN_F32 (rounded to BF16) / IN_G32: [N][cin] FP32, channel-last
+  int cin;               // IN_F32 / IN_G32: input channels (2 or 16)
   const uint16_t* w;     // 27 taps of 16 x 16 BF16 in the canonical layout
-  const float* bias;     // [c_out] (c_out = 16, or 2 for the field output)
-  void* out;             // OUT_HIDDEN: [N][16] BF16; OUT_FIELD: planar FP32 z (updated)
+  const float* bias;     // [c_out] (c_out = 16, or 2 for the field output) or null
+  float* pre;            // OUT_HIDDEN: FP32 pre-activations [N][16] written (nullable); OUT_GRAD: read
+  void* out;             // OUT_HIDDEN: [N][16] BF16; OUT_FIELD: planar FP32 z (updated);
+                         // OUT_F32: [N][2] FP32; OUT_GRAD: [N][16] FP32 (times GELU'(pre))
   const double* sumsq;   // IN_PLANAR / OUT_FIELD: sum |t|^2
   float out_scale;
   int* err;              // set if the MMA completion wait timed out
@@ -466,10 +372,11 @@ struct TcConvArgs {
 template <int IN, int OUT>
 __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
   extern __shared__ uint8_t smem_raw[];
+  constexpr int NPL = IN == IN_G32 ? 4 : 2;  // channel planes: 0-7, 8-15 (hi), then lo
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* plane0 = sm + 16;               // point -1 at sm, point 0 at sm + 16
   uint8_t* plane1 = plane0 + PLANE_B;
-  uint8_t* wts = sm + 2 * PLANE_B;         // 27 x 512 B (1024-aligned base + 2 * PLANE_B: 16-aligned)
+  uint8_t* wts = sm + NPL * PLANE_B;       // 27 x 512 B (1024-aligned base + NPL * PLANE_B: 16-aligned)
   uint64_t* bar = (uint64_t*)(wts + 27 * TCW_TAP);
   uint32_t* tslot = (uint32_t*)(bar + 1);
   int* fail = (int*)(tslot + 1);
@@ -480,7 +387,9 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
   const int ibx = (int)(b % a.bx);
   b /= a.bx;
   const int iby = (int)(b % a.by);
-  const int ibz = (int)(b / a.by);
+  b /= a.by;
+  const int ibz = (int)(b % a.bz);
+  const int64_t img = b / a.bz;
   const int x0 = ibx * BX - 1, y0 = iby * BY - 1, z0 = ibz * BZ - 1;  // global coordinate of halo (0,0,0)
 
   // weights: 27 x 512 B
@@ -495,11 +404,29 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
     const int hx = i % GX, r = i / GX, hy = r % GY, hz = r / GY;
     const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
     const bool ok = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
-    const int64_t p = ok ? ((int64_t)gz * a.ny + gy) * a.nx + gx : 0;
+    const int64_t p = ok ? ((img * a.nz + gz) * a.ny + gy) * a.nx + gx : 0;
     if constexpr (IN == IN_BF16) {
       const uint4* src = (const uint4*)a.in + 2 * p;
       cp16(smem_u32(plane0) + 16u * i, src, ok);
       cp16(smem_u32(plane1) + 16u * i, src + 1, ok);
+    } else if constexpr (IN == IN_F32 || IN == IN_G32) {
+      // channel-last FP32: BF16 (IN_F32), or BF16 hi + lo = the value to 16 bits (IN_G32)
+      const float* f = (const float*)a.in + p * a.cin;
+      float v[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = (ok && c < a.cin) ? f[c] : 0.f;
+      uint32_t hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        hi[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+        lo[q] = pack_bf16(v[2 * q] - bf16_lo(hi[q]), v[2 * q + 1] - bf16_hi(hi[q]));
+      }
+      *(uint4*)(plane0 + 16 * i) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *(uint4*)(plane1 + 16 * i) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+      if constexpr (IN == IN_G32) {
+        *(uint4*)(plane0 + 2 * PLANE_B + 16 * i) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        *(uint4*)(plane0 + 3 * PLANE_B + 16 * i) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+      }
     } else {
       const float* f = (const float*)a.in;
       const float re = ok ? f[p] * sc : 0.f, im = ok ? f[npts + p] * sc : 0.f;
@@ -507,7 +434,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
       *(uint4*)(plane1 + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
     }
   }
-  if (tid < 2) {  // the padding points before and after each plane
+  if (tid < NPL) {  // the padding points before and after each plane
     *(uint4*)(sm + tid * PLANE_B) = make_uint4(0u, 0u, 0u, 0u);
     *(uint4*)(plane0 + tid * PLANE_B + 16 * GP) = make_uint4(0u, 0u, 0u, 0u);
   }
@@ -541,6 +468,8 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
         const uint64_t ad = desc_noswz(p0 + (uint32_t)(q * 16), PLANE_B, 128);
         const uint64_t bd = desc_noswz(smem_u32(wts) + (uint32_t)(t * TCW_TAP), 128, 256);
         mma_bf16(tmem + 16u * tile, ad, bd, id, t > 0 ? 1u : 0u);
+        if constexpr (IN == IN_G32)  // the lo copy of the operand
+          mma_bf16(tmem + 16u * tile, desc_noswz(p0 + 2u * PLANE_B + (uint32_t)(q * 16), PLANE_B, 128), bd, id, 1u);
       }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -567,7 +496,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
   } else {
     float bias[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) bias[c] = (OUT == OUT_HIDDEN || c < 2) ? a.bias[c] : 0.f;
+    for (int c = 0; c < 16; ++c) bias[c] = (a.bias && (OUT == OUT_HIDDEN || c < 2)) ? a.bias[c] : 0.f;
     float cs = 0.f;
     if constexpr (OUT == OUT_FIELD) {
       const double ss = *a.sumsq;
@@ -585,8 +514,16 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
       const int hx = r % GX, hz = 1 + tile / (BY / 4), hy = 1 + 4 * (tile % (BY / 4)) + r / GX;
       const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
       if (hx < 1 || hx > BX || gx >= a.nx || gy >= a.ny || gz >= a.nz) continue;
-      const int64_t p = ((int64_t)gz * a.ny + gy) * a.nx + gx;
+      const int64_t p = ((img * a.nz + gz) * a.ny + gy) * a.nx + gx;
       if constexpr (OUT == OUT_HIDDEN) {
+        if (a.pre) {
+          float4* pr = (float4*)(a.pre + p * 16);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            pr[q] = make_float4(__uint_as_float(v[4 * q]) + bias[4 * q], __uint_as_float(v[4 * q + 1]) + bias[4 * q + 1],
+                                __uint_as_float(v[4 * q + 2]) + bias[4 * q + 2],
+                                __uint_as_float(v[4 * q + 3]) + bias[4 * q + 3]);
+        }
         uint32_t pk[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
@@ -595,6 +532,20 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
         uint4* o4 = (uint4*)a.out + 2 * p;
         o4[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         o4[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      } else if constexpr (OUT == OUT_F32) {
+        float* o = (float*)a.out + p * 2;
+        o[0] = __uint_as_float(v[0]) + bias[0];
+        o[1] = __uint_as_float(v[1]) + bias[1];
+      } else if constexpr (OUT == OUT_GRAD) {
+        const float4* pr = (const float4*)(a.pre + p * 16);
+        float4* o = (float4*)((float*)a.out + p * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 pv = pr[q];
+          o[q] = make_float4(__uint_as_float(v[4 * q]) * gelu_df(pv.x), __uint_as_float(v[4 * q + 1]) * gelu_df(pv.y),
+                             __uint_as_float(v[4 * q + 2]) * gelu_df(pv.z),
+                             __uint_as_float(v[4 * q + 3]) * gelu_df(pv.w));
+        }
       } else {
         float* z = (float*)a.out;
         z[p] = fmaf(cs, __uint_as_float(v[0]) + bias[0], z[p]);
@@ -625,6 +576,24 @@ __global__ void prep_tc_kernel(const float* __restrict__ theta, uint16_t* __rest
   wtc[(l * 27 + t) * 256 + ((co / 8) * 2 + ci / 8) * 64 + (co % 8) * 8 + (ci % 8)] = u;
 }
 
+// The same for the input gradient of every layer (the transpose of a zero-padded correlation
+// is the correlation with the flipped, channel-transposed taps): layer l, tap t' = 26 - t,
+// c_out' = the layer's c_in rows and c_in' = its c_out columns.
+__global__ void prep_tcb_kernel(const float* __restrict__ theta, uint16_t* __restrict__ wtcb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NL * 27 * 256) return;
+  const int l = i / (27 * 256), t2 = (i / 256) % 27, e = i % 256;
+  const int co2 = e / 16, ci2 = e % 16;  // co2: the layer's input channel, ci2: its output channel
+  int toff = 0;
+  for (int q = 0; q < l; ++q) toff += 27 * ch(q) * ch(q + 1) + ch(q + 1);
+  const int cin = ch(l), cout = ch(l + 1);
+  const float w = (co2 < cin && ci2 < cout) ? theta[toff + (ci2 * cin + co2) * 27 + (26 - t2)] : 0.f;
+  const __nv_bfloat16 b16 = __float2bfloat16_rn(w);
+  uint16_t u;
+  memcpy(&u, &b16, 2);
+  wtcb[(l * 27 + t2) * 256 + ((co2 / 8) * 2 + ci2 / 8) * 64 + (co2 % 8) * 8 + (ci2 % 8)] = u;
+}
+
 struct LayerDims {
   int cin[NL], cout[NL], toff[NL], boff[NL], woff[NL];
 };
@@ -644,54 +613,12 @@ __host__ __device__ inline LayerDims layer_dims() {
   return d;
 }
 
-// BF16-rounded taps of every layer in the forward layout [t][ci][co] (wf) and in the
-// input-gradient layout [t'][co][ci] with t' = 26 - t (wb).
-__global__ void prep_kernel(const float* __restrict__ theta, float* __restrict__ wf, float* __restrict__ wb) {
-  const LayerDims d = layer_dims();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int l = 0; l < NL; ++l) {
-    const int n = 27 * d.cin[l] * d.cout[l];
-    if (i >= n) continue;
-    const int ci_n = d.cin[l], co_n = d.cout[l];
-    // forward entry i = (t * cin + ci) * cout + co
-    {
-      const int t = i / (ci_n * co_n), r = i % (ci_n * co_n), ci = r / co_n, co = r % co_n;
-      wf[d.woff[l] + i] = bf16r(theta[d.toff[l] + (co * ci_n + ci) * 27 + t]);
-    }
-    // input-gradient entry i = (t' * cout + co) * cin + ci
-    {
-      const int t2 = i / (ci_n * co_n), r = i % (ci_n * co_n), co = r / ci_n, ci = r % ci_n;
-      wb[d.woff[l] + i] = bf16r(theta[d.toff[l] + (co * ci_n + ci) * 27 + (26 - t2)]);
-    }
-  }
-}
-
 constexpr int kWeights = 27 * (2 * 16 + 16 * 16 + 16 * 16 + 16 * 2);  // 15552 taps
 static_assert(kWeights + 16 + 16 + 16 + 2 == HELM6_CNN_NPARAMS, "parameter count");
 
 template <int CIN, int COUT>
-constexpr size_t conv_smem() {
-  return sizeof(float) * (27 * CIN * COUT + HP * PStride<CIN>::v);
-}
-template <int CIN, int COUT>
 constexpr size_t wgrad_smem() {
   return sizeof(float) * (HP * PStride<CIN>::v + NT * COUT);
-}
-
-template <int CIN, int COUT, int IN, int OUT>
-cudaError_t launch_conv(const ConvArgs& a, cudaStream_t s) {
-  const size_t sm = conv_smem<CIN, COUT>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, IN, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  const int64_t tiles = (int64_t)a.tx * a.ty * a.tz * a.nb;
-  note_launch();
-  conv_kernel<CIN, COUT, IN, OUT><<<(unsigned)tiles, NT, sm, s>>>(a);
-  return cudaGetLastError();
 }
 
 template <int CIN, int COUT, int IN>
@@ -728,52 +655,52 @@ ConvArgs vol_args(int nb, int nz, int ny, int nx) {
 // Library-internal interface (helm6_internal.h)
 // ---------------------------------------------------------------------------------------
 
-int cnn_alloc(CnnNet& net) {
+int cnn_alloc(CnnNet& net, bool backward) {
   if (cudaMalloc((void**)&net.wtc, sizeof(uint16_t) * NL * 27 * 256) != cudaSuccess) return HELM6_ERR_NOMEM;
+  if (backward && cudaMalloc((void**)&net.wtcb, sizeof(uint16_t) * NL * 27 * 256) != cudaSuccess)
+    return HELM6_ERR_NOMEM;
   if (cudaMalloc((void**)&net.theta, sizeof(float) * HELM6_CNN_NPARAMS) != cudaSuccess) return HELM6_ERR_NOMEM;
-  if (cudaMalloc((void**)&net.wf, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
-  if (cudaMalloc((void**)&net.wb, sizeof(float) * kWeights) != cudaSuccess) return HELM6_ERR_NOMEM;
   return HELM6_OK;
 }
 
 void cnn_free(CnnNet& net) {
   cudaFree(net.theta);
-  cudaFree(net.wf);
-  cudaFree(net.wb);
   cudaFree(net.wtc);
+  cudaFree(net.wtcb);
   net = CnnNet{};
 }
 
 int cnn_configure() {
   // the field kernels' shared-memory limits, set once before any launch (and so never
   // inside a stream capture)
-  if (cudaFuncSetAttribute(conv_tc_kernel<IN_PLANAR, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)TC_SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_tc_kernel<IN_BF16, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)TC_SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_tc_kernel<IN_BF16, OUT_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)TC_SMEM) != cudaSuccess)
-    return HELM6_ERR_CUDA;
-  if (cudaFuncSetAttribute(conv_kernel<2, 16, IN_PLANAR, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_smem<2, 16>()) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_kernel<16, 16, IN_BF16, OUT_HIDDEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_smem<16, 16>()) != cudaSuccess ||
-      cudaFuncSetAttribute(conv_kernel<16, 2, IN_BF16, OUT_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)conv_smem<16, 2>()) != cudaSuccess)
-    return HELM6_ERR_CUDA;
+  static bool done = false;
+  if (done) return HELM6_OK;
+  const std::pair<const void*, size_t> ks[] = {
+      {(const void*)conv_tc_kernel<IN_PLANAR, OUT_HIDDEN>, TC_SMEM},
+      {(const void*)conv_tc_kernel<IN_BF16, OUT_HIDDEN>, TC_SMEM},
+      {(const void*)conv_tc_kernel<IN_BF16, OUT_FIELD>, TC_SMEM},
+      // the trainer's layers
+      {(const void*)conv_tc_kernel<IN_F32, OUT_HIDDEN>, TC_SMEM},
+      {(const void*)conv_tc_kernel<IN_BF16, OUT_F32>, TC_SMEM},
+      {(const void*)conv_tc_kernel<IN_G32, OUT_GRAD>, TC_SMEM4}};
+  for (const auto& k : ks)
+    if (cudaFuncSetAttribute(k.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.second) != cudaSuccess)
+      return HELM6_ERR_CUDA;
+  done = true;
   return HELM6_OK;
 }
 
 void cnn_prepare(const CnnNet& net, cudaStream_t s) {
-  note_launch(net.wtc ? 2 : 1);
-  prep_kernel<<<(27 * 16 * 16 + 255) / 256, 256, 0, s>>>(net.theta, net.wf, net.wb);
+  note_launch((net.wtc ? 1 : 0) + (net.wtcb ? 1 : 0));
   if (net.wtc) prep_tc_kernel<<<(NL * 27 * 256 + 255) / 256, 256, 0, s>>>(net.theta, net.wtc);
+  if (net.wtcb) prep_tcb_kernel<<<(NL * 27 * 256 + 255) / 256, 256, 0, s>>>(net.theta, net.wtcb);
 }
 
 int cnn_apply_field(const CnnNet& net, int nz, int ny, int nx, const float* t, const double* sumsq, uint16_t* act0,
                     uint16_t* act1, float out_scale, float* z, int* err, cudaStream_t s) {
   const LayerDims d = layer_dims();
   TcConvArgs a{};
+  a.nb = 1;
   a.nz = nz;
   a.ny = ny;
   a.nx = nx;
@@ -822,6 +749,7 @@ struct helm6_cnn_trainer {
   float* partial = nullptr;
   double *lpart = nullptr, *loss = nullptr;
   double* pinned = nullptr;
+  int* tcerr = nullptr;     // set by a tensor-core layer whose MMA wait timed out
   int nblk = 0, nloss = 0;
   long long step = 0;
   bool residual = false;    // loss mean|A_h y - x|^2 over interior points (else MSE)
@@ -831,36 +759,54 @@ struct helm6_cnn_trainer {
 
 namespace {
 
-int tr_forward(helm6_cnn_trainer* tr, const float* x) {
-  const LayerDims d = layer_dims();
-  ConvArgs a = vol_args(tr->nb, tr->nz, tr->ny, tr->nx);
-  cudaStream_t s = tr->stream;
-  a.in = x;
-  a.round_in = 1;
-  a.w = tr->net.wf + d.woff[0];
-  a.bias = tr->net.theta + d.boff[0];
-  a.pre = tr->pre[0];
-  a.out = tr->act[0];
-  if (launch_conv<2, 16, IN_F32, OUT_HIDDEN>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
-  a.round_in = 0;
-  for (int l = 1; l < 3; ++l) {
-    a.in = tr->act[l - 1];
-    a.w = tr->net.wf + d.woff[l];
-    a.bias = tr->net.theta + d.boff[l];
-    a.pre = tr->pre[l];
-    a.out = tr->act[l];
-    if (launch_conv<16, 16, IN_BF16, OUT_HIDDEN>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
-  }
-  a.in = tr->act[2];
-  a.w = tr->net.wf + d.woff[3];
-  a.bias = tr->net.theta + d.boff[3];
-  a.pre = nullptr;
-  a.out = tr->y;
-  if (launch_conv<16, 2, IN_BF16, OUT_F32>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
-  return HELM6_OK;
+// A tensor-core layer over the trainer's batch of images.
+TcConvArgs tr_tc_args(const helm6_cnn_trainer* tr) {
+  TcConvArgs a{};
+  a.nb = tr->nb;
+  a.nz = tr->nz;
+  a.ny = tr->ny;
+  a.nx = tr->nx;
+  a.bx = (tr->nx + BX - 1) / BX;
+  a.by = (tr->ny + BY - 1) / BY;
+  a.bz = (tr->nz + BZ - 1) / BZ;
+  a.err = tr->tcerr;
+  return a;
 }
 
-// loss, g4 = dL/dy, then every layer's weight/bias gradient into tr->grad
+unsigned tr_tc_grid(const TcConvArgs& a) { return (unsigned)((int64_t)a.bx * a.by * a.bz * a.nb); }
+
+// Forward pass on the tensor cores: BF16 input (rounded), BF16 activations, FP32
+// pre-activations kept for the backward pass.
+int tr_forward(helm6_cnn_trainer* tr, const float* x) {
+  const LayerDims d = layer_dims();
+  cudaStream_t s = tr->stream;
+  TcConvArgs a = tr_tc_args(tr);
+  const unsigned grid = tr_tc_grid(a);
+  note_launch(NL);
+  for (int l = 0; l < NL; ++l) {
+    a.w = tr->net.wtc + (size_t)l * 27 * 256;
+    a.bias = tr->net.theta + d.boff[l];
+    if (l == 0) {
+      a.in = x;
+      a.cin = 2;
+      a.pre = tr->pre[0];
+      a.out = tr->act[0];
+      conv_tc_kernel<IN_F32, OUT_HIDDEN><<<grid, 128, TC_SMEM, s>>>(a);
+    } else if (l < NL - 1) {
+      a.in = tr->act[l - 1];
+      a.pre = tr->pre[l];
+      a.out = tr->act[l];
+      conv_tc_kernel<IN_BF16, OUT_HIDDEN><<<grid, 128, TC_SMEM, s>>>(a);
+    } else {
+      a.in = tr->act[l - 1];
+      a.pre = nullptr;
+      a.out = tr->y;
+      conv_tc_kernel<IN_BF16, OUT_F32><<<grid, 128, TC_SMEM, s>>>(a);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? HELM6_OK : HELM6_ERR_CUDA;
+}
+
 int tr_backward(helm6_cnn_trainer* tr, const float* x, const float* target) {
   const LayerDims d = layer_dims();
   cudaStream_t s = tr->stream;
@@ -886,17 +832,22 @@ int tr_backward(helm6_cnn_trainer* tr, const float* x, const float* target) {
     wgrad_reduce_kernel<<<(ne + 255) / 256, 256, 0, s>>>(tr->partial, tr->nblk, d.cin[l], d.cout[l],
                                                          tr->grad + d.toff[l], tr->grad + d.boff[l]);
   };
+  // input gradients on the tensor cores (the FP32 gradient split into BF16 hi + lo), weight
+  // gradients by the SIMT reduction kernel
+  TcConvArgs t = tr_tc_args(tr);
+  const unsigned tgrid = tr_tc_grid(t);
+  t.bias = nullptr;
   // layer 4: dW from act3 and g4; g3 = (W4^T * g4) gelu'(pre3)
   a.in = tr->act[2];
   if (launch_wgrad<16, 2, IN_BF16>(a, tr->g4, tr->partial, tr->nblk, s) != cudaSuccess) return HELM6_ERR_CUDA;
   reduce(3);
-  a.in = tr->g4;
-  a.round_in = 0;
-  a.w = tr->net.wb + d.woff[3];
-  a.bias = nullptr;
-  a.pre = tr->pre[2];
-  a.out = tr->ga;
-  if (launch_conv<2, 16, IN_F32, OUT_GRAD>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+  t.in = tr->g4;
+  t.cin = 2;
+  t.w = tr->net.wtcb + (size_t)3 * 27 * 256;
+  t.pre = tr->pre[2];
+  t.out = tr->ga;
+  note_launch();
+  conv_tc_kernel<IN_G32, OUT_GRAD><<<tgrid, 128, TC_SMEM4, s>>>(t);
   // layers 3 and 2
   float* gcur = tr->ga;
   float* gnext = tr->gb;
@@ -904,11 +855,13 @@ int tr_backward(helm6_cnn_trainer* tr, const float* x, const float* target) {
     a.in = tr->act[l - 1];
     if (launch_wgrad<16, 16, IN_BF16>(a, gcur, tr->partial, tr->nblk, s) != cudaSuccess) return HELM6_ERR_CUDA;
     reduce(l);
-    a.in = gcur;
-    a.w = tr->net.wb + d.woff[l];
-    a.pre = tr->pre[l - 1];
-    a.out = gnext;
-    if (launch_conv<16, 16, IN_F32, OUT_GRAD>(a, s) != cudaSuccess) return HELM6_ERR_CUDA;
+    t.in = gcur;
+    t.cin = 16;
+    t.w = tr->net.wtcb + (size_t)l * 27 * 256;
+    t.pre = tr->pre[l - 1];
+    t.out = gnext;
+    note_launch();
+    conv_tc_kernel<IN_G32, OUT_GRAD><<<tgrid, 128, TC_SMEM4, s>>>(t);
     std::swap(gcur, gnext);
   }
   // layer 1: dW from the BF16-rounded input and g1
@@ -938,7 +891,7 @@ void helm6_cnn_trainer_destroy(helm6_cnn_trainer* tr) {
   else cudaDeviceSynchronize();
   cnn_free(tr->net);
   void* bufs[] = {tr->m, tr->v, tr->grad, tr->pre[0], tr->pre[1], tr->pre[2], tr->act[0], tr->act[1],
-                  tr->act[2], tr->y, tr->g4, tr->ga, tr->gb, tr->partial, tr->lpart, tr->loss};
+                  tr->act[2], tr->y, tr->g4, tr->ga, tr->gb, tr->partial, tr->lpart, tr->loss, tr->tcerr};
   for (void* p : bufs) cudaFree(p);
   if (tr->pinned) cudaFreeHost(tr->pinned);
   delete tr;
@@ -967,7 +920,10 @@ int helm6_cnn_trainer_create(helm6_cnn_trainer** out, int batch, int nz, int ny,
   };
   auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
   const size_t np = HELM6_CNN_NPARAMS;
-  if (cnn_alloc(tr->net) != HELM6_OK) return fail(HELM6_ERR_NOMEM);
+  if (cnn_configure() != HELM6_OK) return fail(HELM6_ERR_CUDA);
+  if (cnn_alloc(tr->net, true) != HELM6_OK) return fail(HELM6_ERR_NOMEM);
+  if (cudaMalloc((void**)&tr->tcerr, sizeof(int)) != cudaSuccess || cudaMemset(tr->tcerr, 0, sizeof(int)) != cudaSuccess)
+    return fail(HELM6_ERR_NOMEM);
   bool ok = al((void**)&tr->m, np * 4) && al((void**)&tr->v, np * 4) && al((void**)&tr->grad, np * 4) &&
             al((void**)&tr->y, npts * 8) && al((void**)&tr->g4, npts * 8) && al((void**)&tr->ga, npts * 64) &&
             al((void**)&tr->gb, npts * 64) && al((void**)&tr->partial, (size_t)tr->nblk * (6912 + 16) * 4) &&

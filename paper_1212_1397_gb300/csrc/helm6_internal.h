@@ -261,13 +261,12 @@ void launch_tri_mul(const double* T, int ldt, int k, const double* y, double* q,
 // [t][c_in][c_out] and in the input-gradient layout [26 - t][c_out][c_in].
 struct CnnNet {
   float* theta = nullptr;
-  float* wf = nullptr;
-  float* wb = nullptr;
-  uint16_t* wtc = nullptr;  // BF16 taps of every layer for the tensor-core field path
+  uint16_t* wtc = nullptr;   // BF16 taps of every layer for the tensor-core layers
+  uint16_t* wtcb = nullptr;  // the flipped, channel-transposed taps (input gradients; trainer)
 };
-int cnn_alloc(CnnNet& net);
+int cnn_alloc(CnnNet& net, bool backward = false);
 void cnn_free(CnnNet& net);
-void cnn_prepare(const CnnNet& net, cudaStream_t s);  // wf, wb from theta
+void cnn_prepare(const CnnNet& net, cudaStream_t s);  // the tensor-core taps from theta
 int cnn_configure();  // kernel attributes of the field path (before any capture)
 // z += c s N(t / s) on planar complex FP32 fields of nz*ny*nx points, s = sqrt(*sumsq / N)
 // (z unchanged when *sumsq is 0); act0/act1: scratch of 16 BF16 per point each.  The four

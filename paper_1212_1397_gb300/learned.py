@@ -181,6 +181,26 @@ def evaluate(theta, out_scale, n, k, faces, seeds, nsrc, noise, restart=30, tol=
     return res
 
 
+def time_steps(steps=50, warmup=5, batch=32, seed=5):
+    """Device time of one training step (forward, residual-form loss, backward, Adam) on
+    seeded random patches, CUDA events around `steps` steps after `warmup`."""
+    torch = _torch()
+    x = torch.from_numpy(inputs.complex_normal(seed, (batch, PATCH, PATCH, PATCH)).view(np.float64)
+                         .reshape(batch, PATCH, PATCH, PATCH, 2).astype(np.float32)).cuda()
+    with H.Trainer(batch, PATCH, PATCH, PATCH, init_theta(seed)) as tr:
+        tr.set_residual_loss(40.0, 1.0 / 129)
+        for _ in range(warmup):
+            tr.step(x, x, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            tr.step(x, x, 1e-3, want_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / max(1, steps)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -197,8 +217,14 @@ def main(argv=None):
     e.add_argument("--weights", required=True)
     e.add_argument("--seeds", type=int, default=5)
     e.add_argument("--n", type=int, default=192)
+    ts = sub.add_parser("time-step")
+    ts.add_argument("--steps", type=int, default=50)
+    ts.add_argument("--batch", type=int, default=32)
     a = ap.parse_args(argv)
-    if a.cmd == "train":
+    if a.cmd == "time-step":
+        ms = time_steps(a.steps, batch=a.batch)
+        print(json.dumps(dict(ms_per_train_step=ms, batch=a.batch, patch=PATCH, steps=a.steps)))
+    elif a.cmd == "train":
         t0 = time.time()
         fields = harvest(128, 40.0, "DDNNSS", range(100, 100 + a.seeds128), nsrc=1, noise=1e-3)
         fields += harvest(256, 80.0, "DDNNSS", range(100, 100 + a.seeds256), nsrc=8, noise=0.0)
