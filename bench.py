@@ -70,8 +70,8 @@ KERNEL_OF = {
     "ztri": "ztri_lines_kernel<8>",
     "xform_y_inv": "xform_tc_kernel",
     "xform_x_inv": "xform_tc_kernel",
-    "gs_dot": "dcgs_dot_kernel<float,{p},{tv}>",
-    "gs_update": "dcgs_update_kernel<float,{p},{tv}>",
+    "gs_dot": "dcgs_dot_kernel<float,{p},{tv}{dch}>",
+    "gs_update": "dcgs_update_kernel<float,{p},{tv}{uch}>",
     "resid64": "stencil_kernel<double,1>",
 }
 
@@ -592,7 +592,11 @@ def main():
     hbm, bf16, peak_src = peaks()
     phases = prof["phases"]
     f16 = solver.basis == H.BASIS_F16
-    kernel_of = {ph: name.format(p=4 if f16 and N % 4 == 0 else 2, tv="__half" if f16 else "float")
+    # an FP16 basis on a grid of 8k points: 8 points per thread, the reduction pass compiled
+    # for 1 to 6 vectors per warp group (by the step's count), the update 4 vectors at a time
+    p8 = f16 and N % 8 == 0
+    kernel_of = {ph: name.format(p=8 if p8 else 4 if f16 and N % 4 == 0 else 2, tv="__half" if f16 else "float",
+                                 dch=",1..6" if p8 else ",8", uch=",4" if p8 else ",8")
                  for ph, name in KERNEL_OF.items()}
     single = [p for p in phases if p in kernel_of and phases[p]["count"] > 0]
     per_kernel = {}

@@ -225,13 +225,24 @@ __device__ __forceinline__ void ldpts(const S* p, int64_t q, T* o) {
       const typename V2<T>::t v = ((const typename V2<T>::t*)p)[q];
       o[0] = v.x;
       o[1] = v.y;
-    } else {
-      static_assert(P == 4 && std::is_same<T, float>::value, "4-point loads are FP32 or FP16");
+    } else if constexpr (P == 4) {
+      static_assert(std::is_same<T, float>::value, "4-point loads are FP32 or FP16");
       const float4 v = ((const float4*)p)[q];
       o[0] = v.x;
       o[1] = v.y;
       o[2] = v.z;
       o[3] = v.w;
+    } else {
+      static_assert(P == 8 && std::is_same<T, float>::value, "8-point loads are FP32 or FP16");
+      const float4 a = ((const float4*)p)[2 * q], b = ((const float4*)p)[2 * q + 1];
+      o[0] = a.x;
+      o[1] = a.y;
+      o[2] = a.z;
+      o[3] = a.w;
+      o[4] = b.x;
+      o[5] = b.y;
+      o[6] = b.z;
+      o[7] = b.w;
     }
   } else {
     static_assert(std::is_same<S, __half>::value && std::is_same<T, float>::value, "FP16 storage, FP32 arithmetic");
@@ -261,20 +272,34 @@ __device__ __forceinline__ void stpts(S* p, int64_t q, const T* v) {
       p[q] = v[0];
     } else if constexpr (P == 2) {
       ((typename V2<T>::t*)p)[q] = typename V2<T>::t{v[0], v[1]};
-    } else {
+    } else if constexpr (P == 4) {
       ((float4*)p)[q] = float4{v[0], v[1], v[2], v[3]};
+    } else {
+      static_assert(P == 8, "stores of 1, 2, 4 or 8 points");
+      ((float4*)p)[2 * q] = float4{v[0], v[1], v[2], v[3]};
+      ((float4*)p)[2 * q + 1] = float4{v[4], v[5], v[6], v[7]};
     }
   } else {
     if constexpr (P == 1) {
       p[q] = __float2half_rn(v[0]);
     } else if constexpr (P == 2) {
       ((__half2*)p)[q] = __floats2half2_rn(v[0], v[1]);
-    } else {
+    } else if constexpr (P == 4) {
       const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
       uint2 raw;
       raw.x = *(const uint32_t*)&a;
       raw.y = *(const uint32_t*)&b;
       ((uint2*)p)[q] = raw;
+    } else {
+      static_assert(P == 8, "stores of 1, 2, 4 or 8 points");
+      const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+      const __half2 c = __floats2half2_rn(v[4], v[5]), d = __floats2half2_rn(v[6], v[7]);
+      uint4 raw;
+      raw.x = *(const uint32_t*)&a;
+      raw.y = *(const uint32_t*)&b;
+      raw.z = *(const uint32_t*)&c;
+      raw.w = *(const uint32_t*)&d;
+      ((uint4*)p)[q] = raw;
     }
   }
 }
@@ -303,6 +328,16 @@ struct PtsReg<float, 4, __half> {
   }
 };
 template <>
+struct PtsReg<float, 8, __half> {
+  uint4 r;
+  __device__ __forceinline__ void load(const __half* p, int64_t q) { r = ((const uint4*)p)[q]; }
+  __device__ __forceinline__ float get(int k) const {
+    const uint32_t w = k < 2 ? r.x : k < 4 ? r.y : k < 6 ? r.z : r.w;
+    const __half2 h = *(const __half2*)&w;
+    return (k & 1) ? __high2float(h) : __low2float(h);
+  }
+};
+template <>
 struct PtsReg<float, 2, __half> {
   __half2 r;
   __device__ __forceinline__ void load(const __half* p, int64_t q) { r = ((const __half2*)p)[q]; }
@@ -324,37 +359,39 @@ __device__ __forceinline__ T round_to(T x) {
 // Partial layout per block (ncol = 4 count + 3 doubles): s (2 count), t (2 count), a, b (2).
 // The basis is stored in TV (T, or FP16 holding vscale V_i with vscale a power of two), so
 // the s and t sums are multiplied by vinv = 1 / vscale in the block epilogue.
-// The block's warps form G = 1, 2 or 4 groups (the fewest with at most CHD basis vectors
+// The block's warps form G = 1, 2, 4 or 8 groups (the fewest with at most CH basis vectors
 // each); all groups walk the same points, each reducing its own share of the basis, so u
 // and w come from DRAM once (the other groups' loads of them hit L1) however many vectors
-// there are.  More than G * CHD vectors (restarts beyond 32) take further rounds.  At the
+// there are.  More than G * CH vectors (restarts beyond 32) take further rounds.  At the
 // end of a round every accumulator is reduced by warp shuffles and one shared-memory
 // exchange.
-template <typename T, int PTS, typename TV>
+template <typename T, int PTS, typename TV, int CH>
 __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(const TV* __restrict__ V, int64_t vs, int count,
                                                          const T* __restrict__ u, const T* __restrict__ w,
                                                          int64_t N, double* __restrict__ partial, double vinv) {
   constexpr int NW = RB / 32;
-  constexpr int NACC = 4 * CHD + 3;
+  constexpr int NACC = 4 * CH + 3;
   __shared__ T sh[NW][NACC];
   const int ncol = 4 * count + 3;
   const bool hw = (w != nullptr);
   const int64_t npts = N / PTS;
   double* out = partial + (int64_t)blockIdx.x * ncol;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int G = count <= CHD ? 1 : count <= 2 * CHD ? 2 : 4;
+  int G = 1;
+  while (G < NW && (count + G - 1) / G > CH) G *= 2;
   const int wpg = NW / G;                     // warps per group
   const int grp = warp / wpg;
   const int tig = (warp % wpg) * 32 + lane;   // thread within the group
   const int64_t tpg = (int64_t)wpg * 32;
   const int64_t stride = (int64_t)gridDim.x * tpg;
-  const int nround = count > 0 ? (count + G * CHD - 1) / (G * CHD) : 1;
+  const int nround = count > 0 ? (count + G * CH - 1) / (G * CH) : 1;
   for (int rd = 0; rd < nround; ++rd) {
-    const int rbase = rd * G * CHD;
-    const int rcount = min(G * CHD, count - rbase);
-    const int cpg = (rcount + G - 1) / G;
-    const int base = rbase + grp * cpg;
-    const int nc = max(0, min(cpg, rcount - grp * cpg));
+    const int rbase = rd * G * CH;
+    const int rcount = min(G * CH, count - rbase);
+    // group g reduces vectors [g rcount / G, (g + 1) rcount / G) of the round: shares
+    // differ by at most one, the larger ones last (group 0 also forms a and b)
+    const int base = rbase + grp * rcount / G;
+    const int nc = rbase + (grp + 1) * rcount / G - base;
     const bool own = (rd == 0 && grp == 0);   // this group also forms a and b
     T acc[NACC];
 #pragma unroll
@@ -369,9 +406,9 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
         ldpts<T, PTS, T>(w, q, wr);
         ldpts<T, PTS, T>(w + N, q, wi);
       }
-      PtsReg<T, PTS, TV> vr[CHD], vi[CHD];
+      PtsReg<T, PTS, TV> vr[CH], vi[CH];
 #pragma unroll
-      for (int c = 0; c < CHD; ++c) {
+      for (int c = 0; c < CH; ++c) {
         if (c < nc) {
           const TV* v = V + (int64_t)(base + c) * vs;
           vr[c].load(v, q);
@@ -381,13 +418,13 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
       if (own) {
 #pragma unroll
         for (int k = 0; k < PTS; ++k) {
-          acc[4 * CHD] = fmx(ur[k], ur[k], fmx(ui[k], ui[k], acc[4 * CHD]));
-          acc[4 * CHD + 1] = fmx(ur[k], wr[k], fmx(ui[k], wi[k], acc[4 * CHD + 1]));
-          acc[4 * CHD + 2] = fmx(ur[k], wi[k], fmx(-ui[k], wr[k], acc[4 * CHD + 2]));
+          acc[4 * CH] = fmx(ur[k], ur[k], fmx(ui[k], ui[k], acc[4 * CH]));
+          acc[4 * CH + 1] = fmx(ur[k], wr[k], fmx(ui[k], wi[k], acc[4 * CH + 1]));
+          acc[4 * CH + 2] = fmx(ur[k], wi[k], fmx(-ui[k], wr[k], acc[4 * CH + 2]));
         }
       }
 #pragma unroll
-      for (int c = 0; c < CHD; ++c) {
+      for (int c = 0; c < CH; ++c) {
         if (c < nc) {
 #pragma unroll
           for (int k = 0; k < PTS; ++k) {
@@ -412,13 +449,13 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
       const int gg = e / NACC, c = e - gg * NACC;
       double sum = 0.0;
       for (int ww = 0; ww < wpg; ++ww) sum += (double)sh[gg * wpg + ww][c];
-      const int gbase = rbase + gg * cpg;
-      const int gnc = max(0, min(cpg, rcount - gg * cpg));
-      if (c < 4 * CHD) {
+      const int gbase = rbase + gg * rcount / G;
+      const int gnc = rbase + (gg + 1) * rcount / G - gbase;
+      if (c < 4 * CH) {
         const int cc = c >> 2, kind = c & 3;
         if (cc < gnc) out[(kind < 2 ? 0 : 2 * count) + 2 * (gbase + cc) + (kind & 1)] = sum * vinv;
       } else if (rd == 0 && gg == 0) {
-        out[4 * count + (c - 4 * CHD)] = sum;
+        out[4 * count + (c - 4 * CH)] = sum;
       }
     }
     __syncthreads();
@@ -432,7 +469,7 @@ __global__ void __launch_bounds__(RB, sizeof(T) == 8 ? 1 : 2) dcgs_dot_kernel(co
 // receives vscale v_new rounded to FP16, and the correction of u uses that rounded vector,
 // so that u is orthogonalised against the basis as stored.  PTS points per thread; the basis
 // is read UB vectors at a time, all loads of a group issued before its FMAs.
-template <typename T, int PTS, typename TV>
+template <typename T, int PTS, typename TV, int UB = 8>
 __global__ void __launch_bounds__(RB) dcgs_update_kernel(const TV* __restrict__ V, int64_t vs, int count,
                                                          T* u, const T* __restrict__ w, TV* __restrict__ v_out,
                                                          int64_t N, const double* __restrict__ coef, double vscale) {
@@ -455,7 +492,6 @@ __global__ void __launch_bounds__(RB) dcgs_update_kernel(const TV* __restrict__ 
   const T vsc = (T)vscale, vin = (T)vinv;  // powers of two: exact in T
   const int64_t npts = N / PTS;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  constexpr int UB = 8;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npts; q += stride) {
     T ur[PTS], ui[PTS], wr[PTS], wi[PTS];
     ldpts<T, PTS, T>(u, q, ur);
@@ -959,22 +995,42 @@ int cgs_pts(int64_t N, int64_t vs) {
   return (N % 2 == 0 && vs % 2 == 0) ? 2 : 1;
 }
 
+// Vectors per warp group of the 8-point FP16 reduction pass for `count` basis vectors: the
+// fewest groups G (a power of two, at most 8) that leave at most 6 vectors to a group, and
+// the kernel instance compiled for exactly that share (measured at 256 x 258 x 258: an
+// instance sized for more vectors than it gets, or a split into more groups, is slower).
+int dot_share(int count) {
+  int G = 1;
+  while (G < 8 && (count + G - 1) / G > 6) G *= 2;
+  return std::max(1, std::min(6, (count + G - 1) / G));
+}
+
 template <typename T, typename TV>
 void launch_dcgs_dot(const TV* V, int64_t vs, int count, const T* u, const T* w, int64_t N, double* partial,
                      int nblocks, double vscale, cudaStream_t s) {
   note_launch();
   const double vinv = 1.0 / vscale;
-  const int p = cgs_pts<TV>(N, vs);
   if constexpr (std::is_same<TV, __half>::value) {
-    if (p == 4) {
-      dcgs_dot_kernel<T, 4, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
+    if (N % 8 == 0 && vs % 8 == 0) {
+      // 8 points per thread: 16-byte basis loads, twice the bytes in flight of 4 points
+      switch (dot_share(count)) {
+#define DOT8(CH)                                                                                   \
+  case CH:                                                                                         \
+    dcgs_dot_kernel<T, 8, TV, CH><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv); \
+    return;
+        DOT8(1) DOT8(2) DOT8(3) DOT8(4) DOT8(5) DOT8(6)
+#undef DOT8
+      }
+    }
+    if (cgs_pts<TV>(N, vs) == 4) {
+      dcgs_dot_kernel<T, 4, TV, CHD><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
       return;
     }
   }
-  if (p == 2)
-    dcgs_dot_kernel<T, 2, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
+  if (cgs_pts<TV>(N, vs) == 2)
+    dcgs_dot_kernel<T, 2, TV, CHD><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
   else
-    dcgs_dot_kernel<T, 1, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
+    dcgs_dot_kernel<T, 1, TV, CHD><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, N, partial, vinv);
 }
 
 // Blocks of the reduction pass: two per SM (its per-block epilogue favours few blocks).
@@ -986,6 +1042,11 @@ void launch_dcgs_update(const TV* V, int64_t vs, int count, T* u, const T* w, TV
   note_launch();
   const int p = cgs_pts<TV>(N, vs);
   if constexpr (std::is_same<TV, __half>::value) {
+    if (N % 8 == 0 && vs % 8 == 0) {
+      // 8 points per thread, the basis read 4 vectors at a time (measured best at 256 x 258 x 258)
+      dcgs_update_kernel<T, 8, TV, 4><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef, vscale);
+      return;
+    }
     if (p == 4) {
       dcgs_update_kernel<T, 4, TV><<<nblocks, RB, 0, s>>>(V, vs, count, u, w, v_out, N, coef, vscale);
       return;
