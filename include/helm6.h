@@ -329,12 +329,13 @@ int helm6_residual_noalloc(int n, double h, helm6_c64 k, const int faces[6], con
 enum { HELM6_CNN_OFF = 0,   /* detach: the direct preconditioner alone */
        HELM6_CNN_ON = 1,    /* every inner cycle uses the learned stage */
        HELM6_CNN_AUTO = 2   /* a probe: of inner cycles 0-2 only cycle 1 uses it, and only for
-                               its first 3 columns (flexible GMRES allows a different map per
+                               its first 2 columns (flexible GMRES allows a different map per
                                column); the later cycles use it on every column only if those
-                               3 columns reduced the residual estimate per column at least
-                               10 % more (in logarithm) than the first 3 columns of cycle 2
+                               2 columns reduced the residual estimate per column at least
+                               10 % more (in logarithm) than the first 2 columns of cycle 2
                                did without it; otherwise the direct preconditioner alone (the
-                               fallback).  In every mode a learned-stage cycle whose
+                               fallback), run as one device-driven graph where the context
+                               solves that way (use_graphs = 2).  In every mode a learned-stage cycle whose
                                correction is non-finite is discarded and the rest of the solve
                                falls back (helm6_stats.cnn_fallbacks) */ };
 

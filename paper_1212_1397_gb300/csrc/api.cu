@@ -644,7 +644,7 @@ int solve_fp64(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_s
 
 // MIXED: FP64 refinement around FP32 FGMRES with the FP32 preconditioner.
 // Columns of the AUTO probe (cycle 1 preconditions this many columns with the learned stage).
-constexpr int kCnnProbe = 3;
+constexpr int kCnnProbe = 2;
 
 // Whether inner cycle `cyc` of a mixed solve uses the learned stage: ON always; AUTO uses
 // it for the first kCnnProbe columns of cycle 1 only, of cycles 0-2 (cycle 0, from the
@@ -658,6 +658,9 @@ bool cnn_cycle(const helm6_ctx* c, int cyc) {
   const double l1 = std::log(std::max(c->probe_rate[1], 1e-300)), l2 = std::log(std::max(c->probe_rate[2], 1e-300));
   return l2 < 0 && l1 < 1.1 * l2;
 }
+
+bool graph_plain_ok(const helm6_ctx* c);
+int solve_mixed_graph(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st);
 
 int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_stats* st) {
   double beta;
@@ -675,6 +678,19 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
     if (!std::isfinite(beta)) return HELM6_NONFINITE;
     if (beta <= tol * normF) return HELM6_OK;
     if (iters >= maxit) return HELM6_NOT_CONVERGED;
+    if (cyc >= 3 && (cnn_failed || !cnn_cycle(c, cyc)) && graph_plain_ok(c)) {
+      // the learned stage is out for the rest of the solve (AUTO decided against it, or it
+      // failed): finish as the plain solve, one device-driven graph launch from the current U
+      helm6_stats tail;
+      std::memset(&tail, 0, sizeof(tail));
+      const int rs = solve_mixed_graph(c, normF, tol, m, maxit - iters, &tail);
+      if (st) {
+        st->iters += tail.iters;
+        st->outer += tail.outer;
+        for (int i = 1; i < tail.nhist && st->nhist < HELM6_MAX_HIST; ++i) st->hist[st->nhist++] = tail.hist[i];
+      }
+      return rs;
+    }
     launch_convert<double, float>(c->R64, c->u32, c->g.N, 1.0 / beta, c->stream);
     const double itol = std::max(inner, 0.3 * tol * normF / beta);
     int k = 0;
@@ -749,11 +765,13 @@ int solve_mixed(helm6_ctx* c, double normF, double tol, int m, int maxit, helm6_
 //   }
 // The step bodies are the kernels of the host-driven Arnoldi steps without their readbacks.
 
-// Whether a context runs its solves (and its part of a batch) as one device-driven graph.
-bool graph_solve_ok(const helm6_ctx* c) {
+// Whether a context can run the plain mixed solve (no learned stage) as one device-driven
+// graph, and whether it runs its solves (and its part of a batch) that way.
+bool graph_plain_ok(const helm6_ctx* c) {
   return c->opts.use_graphs == 2 && c->gctl && c->opts.precision == HELM6_MIXED && c->opts.method == HELM6_FGMRES &&
-         c->cnn_mode == HELM6_CNN_OFF && !c->prof_on && !c->zline_breakdown;
+         !c->prof_on && !c->zline_breakdown;
 }
+bool graph_solve_ok(const helm6_ctx* c) { return graph_plain_ok(c) && c->cnn_mode == HELM6_CNN_OFF; }
 
 // Add a conditional node (one body) to graph g after deps; *node and *body returned.
 int add_conditional(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,

@@ -310,20 +310,23 @@ __global__ void resid_loss_kernel(int nb, int nz, int ny, int nx, const float* _
 // Implicit GEMM: per 128-point tile, D[128 x 16] = sum over the 27 taps of A_t W_t^T with
 // A_t the input rows shifted by the tap's offset (K = 16 input channels) and W_t the
 // 16 x 16 taps (layers with 2 channels are zero-padded to 16).  A CTA owns a brick of
-// 30 x 8 x 4 output points; its 32 x 10 x 6 input halo sits in shared memory as two
+// 30 x 4 x 4 output points; its 32 x 6 x 6 input halo sits in shared memory as two
 // channel planes (channels 0-7 and 8-15, 16 bytes per point, points x fastest), the
 // no-swizzle K-major layout: a core matrix is 8 consecutive points of one plane (128 B),
 // the K step between the planes is the plane distance and the step between 8-row groups
 // is 128 B, so every tap's A operand is the same descriptor with its start address moved
-// by the tap offset.  The 8 tiles (4 halo rows x 32 points each: y rows 1-4 and 5-8 of
-// z planes 1-4) accumulate in 8 x 16 TMEM columns; outputs at halo columns are computed
-// and dropped.  The same kernel serves the trainer on batches of images (zero padding at
+// by the tap offset.  The 4 tiles (4 halo rows x 32 points each: y rows 1-4 of z planes
+// 1-4) accumulate in 4 x 16 TMEM columns; outputs at halo columns are computed and dropped.
+// Bricks this small (52 KB of shared memory, 64 TMEM columns) let four CTAs share an SM, so
+// that one CTA's halo loads overlap another's MMAs and epilogue (measured against 30 x 8 x 4
+// bricks, one CTA per SM).  The same kernel serves the trainer on batches of images (zero padding at
 // every image face): its forward layers (FP32 pre-activations kept) and the input gradients
 // of the backward pass, whose FP32 gradient operand is split into BF16 hi + lo copies (two
 // more channel planes; 54 MMAs per tile) so that it keeps FP32-like accuracy.
-constexpr int BX = 30, BY = 8, BZ = 4;                       // output points of a brick
+constexpr int BX = 30, BY = 4, BZ = 4;                       // output points of a brick
 constexpr int GX = BX + 2, GY = BY + 2, GZ = BZ + 2, GP = GX * GY * GZ;  // halo (GX = 32)
 constexpr int TC_TILES = BZ * BY / 4;                         // 128-point tiles of a brick
+constexpr int TC_TMEM = TC_TILES * 16 <= 32 ? 32 : TC_TILES * 16 <= 64 ? 64 : 128;  // TMEM columns
 constexpr int PLANE_B = (GP + 2) * 16;                        // one point of padding each end
 constexpr int TCW_TAP = 512;                                  // bytes of one tap's 16 x 16 BF16
 constexpr size_t TC_SMEM = 1024 + 2 * (size_t)PLANE_B + 27 * TCW_TAP + 256;
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(128));
+                 "r"(TC_TMEM));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
@@ -555,7 +558,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM));
   if (tid == 0 && *fail) atomicExch(a.err, 1);
 }
 
