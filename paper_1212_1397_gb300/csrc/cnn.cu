@@ -403,7 +403,31 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
     const double ss = *a.sumsq;
     sc = ss > 0.0 ? (float)(1.0 / sqrt(ss / (double)npts)) : 0.f;
   }
-  for (int i = tid; i < GP; i += 128) {
+  if constexpr (IN == IN_PLANAR) {
+    // the planar FP32 field: every load of the thread's halo points issued before any is used
+    constexpr int PER = (GP + 127) / 128;
+    const float* f = (const float*)a.in;
+    float re[PER], im[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = tid + 128 * k;
+      const int hx = i % GX, r = i / GX, hy = r % GY, hz = r / GY;
+      const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+      const bool ok = i < GP && gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+      const int64_t p = ok ? ((img * a.nz + gz) * a.ny + gy) * a.nx + gx : 0;
+      re[k] = ok ? f[p] : 0.f;
+      im[k] = ok ? f[npts + p] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = tid + 128 * k;
+      if (i < GP) {
+        *(uint4*)(plane0 + 16 * i) = make_uint4(pack_bf16(re[k] * sc, im[k] * sc), 0u, 0u, 0u);
+        *(uint4*)(plane1 + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+  }
+  for (int i = tid; i < GP && IN != IN_PLANAR; i += 128) {
     const int hx = i % GX, r = i / GX, hy = r % GY, hz = r / GY;
     const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
     const bool ok = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
@@ -430,11 +454,6 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(TcConvArgs a) {
         *(uint4*)(plane0 + 2 * PLANE_B + 16 * i) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         *(uint4*)(plane0 + 3 * PLANE_B + 16 * i) = make_uint4(lo[4], lo[5], lo[6], lo[7]);
       }
-    } else {
-      const float* f = (const float*)a.in;
-      const float re = ok ? f[p] * sc : 0.f, im = ok ? f[npts + p] * sc : 0.f;
-      *(uint4*)(plane0 + 16 * i) = make_uint4(pack_bf16(re, im), 0u, 0u, 0u);
-      *(uint4*)(plane1 + 16 * i) = make_uint4(0u, 0u, 0u, 0u);
     }
   }
   if (tid < NPL) {  // the padding points before and after each plane
