@@ -31,6 +31,7 @@ import numpy as np
 
 import helm6_inputs as inputs
 from . import helm6 as H
+from . import weights_path
 
 PATCH = 32
 
@@ -201,6 +202,30 @@ def time_steps(steps=50, warmup=5, batch=32, seed=5):
     return e0.elapsed_time(e1) / max(1, steps)
 
 
+def time_stage(n=256, reps=5, seed=5):
+    """Device time of one application of the direct preconditioner and of the two-stage
+    preconditioner (with the stored weights) on a seeded random field of the n^3 mixed-face
+    workload (k = 80 n / 256), CUDA events over `reps` applications after two."""
+    torch = _torch()
+    w = np.load(weights_path("stage2_kh031.npz"))
+    out = {}
+    with H.Solver(n, 80.0 * n / 256, "DDNNSS", precision=H.MIXED, method=H.FGMRES) as s:
+        s.set_cnn(w["theta"], float(w["out_scale"]), H.CNN_ON)
+        u = torch.from_numpy(inputs.complex_normal(seed, s.shape)).cuda()
+        for name, f in (("apply_Pinv_ms", s.apply_Pinv), ("apply_stage2_ms", s.apply_stage2)):
+            for _ in range(2):
+                f(u)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f(u)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = e0.elapsed_time(e1) / reps
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -217,11 +242,16 @@ def main(argv=None):
     e.add_argument("--weights", required=True)
     e.add_argument("--seeds", type=int, default=5)
     e.add_argument("--n", type=int, default=192)
+    tg = sub.add_parser("time-stage")
+    tg.add_argument("--n", type=int, default=256)
+    tg.add_argument("--reps", type=int, default=5)
     ts = sub.add_parser("time-step")
     ts.add_argument("--steps", type=int, default=50)
     ts.add_argument("--batch", type=int, default=32)
     a = ap.parse_args(argv)
-    if a.cmd == "time-step":
+    if a.cmd == "time-stage":
+        print(json.dumps(dict(n=a.n, **time_stage(a.n, a.reps))))
+    elif a.cmd == "time-step":
         ms = time_steps(a.steps, batch=a.batch)
         print(json.dumps(dict(ms_per_train_step=ms, batch=a.batch, patch=PATCH, steps=a.steps)))
     elif a.cmd == "train":
